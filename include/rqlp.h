@@ -1,0 +1,175 @@
+/*
+ * rqlp.h -- C ABI of the GB300 (sm_103a) Rand-QLP library.
+ *
+ * Rand-QLP (Kaloorazi, Liu, Chen, de Lamare, arXiv 2110.01011) factors an
+ * m x n matrix A as A ~= Q L P^T with Q and P orthonormal and L lower
+ * triangular whose diagonal tracks the singular values of A (section 3.1,
+ * Algorithm 1). This library computes the truncated chain with d = k + p
+ * sketch columns and q power passes:
+ *
+ *   Y  = A^T Omega                         (Algorithm 1 step 3, Omega m x d)
+ *   P~ = qf(Y)                             (orth via unpivoted QR, section 2)
+ *   q times:  Z = qf(A P~),  P~ = qf(A^T Z)   (power passes)
+ *   (Q, R)   = qr(A P~)                    (Algorithm 1 step 4)
+ *   (P^, R^) = qr(R^T),  L = R^^T,  P = P~ P^   (step 5 on the d x d R)
+ *
+ * qf(.) is the Q factor of the thin QR with R's diagonal made positive, so
+ * every factor is unique for full-rank inputs. With d = n and q = 0 the chain
+ * is Algorithm 1 exactly.
+ *
+ * Conventions shared by every entry point:
+ *  - Matrices are row-major FP32 with an explicit leading dimension (elements
+ *    between consecutive rows, >= the column count).
+ *  - Device pointers point to memory of the current CUDA device; the caller
+ *    owns every buffer, including the workspace. The library allocates no
+ *    device memory in rqlp_factor / rqlp_factor_batched.
+ *  - Work is enqueued on `stream` (a cudaStream_t passed as void*, NULL = the
+ *    legacy default stream) without host synchronisation, so calls can be
+ *    captured into a CUDA graph. The return value reports argument and launch
+ *    errors synchronously; numerical failures are written to the device
+ *    array `d_info` (read it after synchronising the stream).
+ *  - Sizes: 1 <= k, p >= 0, q >= 0, d = k + p <= min(m, n), d <= RQLP_MAX_D.
+ *    Anything else returns RQLP_ERR_ARG and enqueues nothing.
+ */
+#ifndef RQLP_H
+#define RQLP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RQLP_MAX_D 256
+
+typedef enum {
+  RQLP_OK = 0,
+  RQLP_ERR_ARG = 1,        /* invalid size, stride, pointer or option      */
+  RQLP_ERR_CUDA = 2,       /* a CUDA launch or API call failed              */
+  RQLP_ERR_BREAKDOWN = 3,  /* Cholesky breakdown even after the shift        */
+  RQLP_ERR_NONFINITE = 4,  /* NaN/Inf met in A or Omega                      */
+  RQLP_ERR_TIMEOUT = 5,    /* a bounded device wait gave up                  */
+  RQLP_ERR_WORKSPACE = 6,  /* workspace too small or misaligned              */
+  RQLP_ERR_UNSUPPORTED = 7 /* option not available on this device/build      */
+} rqlp_status;
+
+/* Arithmetic of the passes over A (the four dense products per power pass). */
+typedef enum {
+  RQLP_PREC_FP32 = 0,   /* FP32 FFMA on the CUDA cores                        */
+  RQLP_PREC_BF16X3 = 1  /* tensor cores: A = A_hi + A_lo and X = X_hi + X_lo  */
+                        /* in BF16, products hi*hi + hi*lo + lo*hi, FP32 acc. */
+} rqlp_precision;
+
+typedef struct {
+  int precision;   /* rqlp_precision                                          */
+  int small_fp64;  /* 1: d x d Cholesky factors in FP64 (slow on GB300);       */
+                   /* 0: FP32 with an automatic diagonal shift on breakdown    */
+  int reserved[6]; /* must be zero                                            */
+} rqlp_opts;
+
+/* d_info layout written by rqlp_factor (2 ints): [0] = rqlp_status of the
+ * numerical phase (RQLP_OK, RQLP_ERR_BREAKDOWN, RQLP_ERR_NONFINITE),
+ * [1] = detail (1-based Cholesky column of the first breakdown, else 0). */
+#define RQLP_INFO_INTS 2
+
+/* d_diag layout (4 doubles, optional): [0] = ||A||_F^2, [1] = ||L||_F^2,
+ * [2] = ||A - Q L P^T||_F^2 = [0] - [1] (Q L P^T = A P~ P~^T is the orthogonal
+ * projection of A's rows on R(P~)), [3] = number of shifted Cholesky passes. */
+#define RQLP_DIAG_DOUBLES 4
+
+/* Opts with every field at its default (FP32 passes, FP32 small factors). */
+void rqlp_default_opts(rqlp_opts* opts);
+
+/* Bytes of device workspace rqlp_factor needs for these sizes and options
+ * (0 when the arguments are invalid). Depends on the current device's SM
+ * count; query it on the device that will run the factorisation. */
+size_t rqlp_workspace_bytes(int64_t m, int64_t n, int k, int p, int q,
+                            const rqlp_opts* opts);
+
+/* Factor A (m x n, device, lda) with the Gaussian test matrix Omega
+ * (m x d, device, ldo), d = k + p, q power passes. Writes
+ *   Q (m x d, ldq): orthonormal columns;
+ *   L (d x d, ldl): lower triangular with positive diagonal, strict upper
+ *                   part written as 0;
+ *   P (n x d, ldp): orthonormal columns,
+ * such that Q L P^T = A P~ P~^T ~= A. workspace must be 256-byte aligned and
+ * hold rqlp_workspace_bytes(...) bytes; its contents on entry are ignored.
+ * d_info: RQLP_INFO_INTS device ints (required). d_diag: RQLP_DIAG_DOUBLES
+ * device doubles or NULL. opts may be NULL (defaults). Output buffers must
+ * not overlap the inputs or the workspace. */
+rqlp_status rqlp_factor(const float* A, int64_t m, int64_t n, int64_t lda,
+                        int k, int p, int q,
+                        const float* Omega, int64_t ldo,
+                        float* Q, int64_t ldq,
+                        float* L, int64_t ldl,
+                        float* P, int64_t ldp,
+                        void* workspace, size_t ws_bytes,
+                        int* d_info, double* d_diag,
+                        const rqlp_opts* opts, void* stream);
+
+/* Host-buffer form of rqlp_factor: A, Omega, Q, L, P are HOST pointers
+ * (pinned memory gives full copy bandwidth). The inputs are copied to the
+ * device, factored, and the factors copied back; the call returns after the
+ * stream has been synchronised. workspace (device) must hold
+ * rqlp_host_workspace_bytes(...) bytes. h_info (2 ints) and h_diag (4
+ * doubles, may be NULL) are host arrays with the layouts above. */
+size_t rqlp_host_workspace_bytes(int64_t m, int64_t n, int k, int p, int q,
+                                 const rqlp_opts* opts);
+rqlp_status rqlp_factor_host(const float* hA, int64_t m, int64_t n, int64_t lda,
+                             int k, int p, int q,
+                             const float* hOmega, int64_t ldo,
+                             float* hQ, int64_t ldq,
+                             float* hL, int64_t ldl,
+                             float* hP, int64_t ldp,
+                             void* workspace, size_t ws_bytes,
+                             int* h_info, double* h_diag,
+                             const rqlp_opts* opts, void* stream);
+
+/* ---- Step-level entry points (one step of the chain each; same conventions).
+ *
+ * rqlp_sketch: one pass over A (Algorithm 1 steps 3-4 and each power pass).
+ *   trans = 1: Y (n x d, ldy) = A^T X with X m x d (ldx);
+ *   trans = 0: Y (m x d, ldy) = A X   with X n x d (ldx).
+ *   opts->precision selects FP32 or the BF16x3 tensor-core form. */
+size_t rqlp_sketch_workspace_bytes(int trans, int64_t m, int64_t n, int d, const rqlp_opts* opts);
+rqlp_status rqlp_sketch(int trans, const float* A, int64_t m, int64_t n, int64_t lda,
+                        const float* X, int64_t ldx, int d, float* Y, int64_t ldy,
+                        void* workspace, size_t ws_bytes, const rqlp_opts* opts, void* stream);
+
+/* rqlp_orth: X = qf(X) in place, the orth(.) of Algorithm 1 steps 3-4 (thin
+ * unpivoted QR, section 2) for a rows x d matrix (rows >= d) by CholeskyQR2,
+ * with a diagonal shift and a third pass when a Cholesky breaks down
+ * (shifted CholeskyQR3). R (d x d, ldr, may be NULL) receives the upper
+ * triangular factor with positive diagonal. d_info as for rqlp_factor. */
+size_t rqlp_orth_workspace_bytes(int64_t rows, int d, const rqlp_opts* opts);
+rqlp_status rqlp_orth(float* X, int64_t rows, int d, int64_t ldx, float* R, int64_t ldr,
+                      void* workspace, size_t ws_bytes, int* d_info, const rqlp_opts* opts,
+                      void* stream);
+
+/* ---- Runtime services (host only; no device memory).
+ *
+ * rqlp_kernel_launches: cumulative number of CUDA kernels this library has
+ * launched in the calling process.
+ * rqlp_profile_enable(on): while on, every pass over A (the dense products
+ * A^T X and A X) is bracketed by a CUDA event pair recorded on the launching
+ * stream. Returns the previous state. Do not enable it while capturing a
+ * graph.
+ * rqlp_profile_read: after synchronising the stream, writes up to cap pass
+ * durations in ms (tags[i] = 1 for A^T X, 0 for A X) in launch order, clears
+ * the record list and returns the count written. */
+unsigned long long rqlp_kernel_launches(void);
+int rqlp_profile_enable(int on);
+int rqlp_profile_read(float* ms, int* tags, int cap);
+
+/* Human-readable name of a status code (static string). */
+const char* rqlp_status_string(int status);
+
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+int rqlp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RQLP_H */

@@ -1,0 +1,74 @@
+// Shared declarations of the Rand-QLP CUDA library (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/rqlp.h"
+
+namespace rqlp {
+
+// Round x up to a multiple of a (a > 0); ceil(x / a).
+__host__ __device__ inline int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+__host__ __device__ inline int64_t cdiv(int64_t x, int64_t a) { return (x + a - 1) / a; }
+
+// Bump allocator over the caller's workspace (256-byte aligned slices). A
+// "dry" arena only measures, so sizing and use share one code path.
+struct Arena {
+  char* base = nullptr;
+  size_t cap = 0;
+  size_t off = 0;
+  bool dry = false;
+  template <typename T>
+  T* take(size_t count) {
+    off = (size_t)round_up((int64_t)off, 256);
+    T* p = dry ? nullptr : reinterpret_cast<T*>(base + off);
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+int sm_count();
+
+// Cumulative count of kernels this library has launched in the process
+// (reported by rqlp_kernel_launches). Every launch site calls note_launch().
+void note_launch(int n = 1);
+
+// Optional per-pass timing: when enabled, every pass over A is bracketed by a
+// CUDA event pair recorded on the launching stream.
+bool profiling_on();
+void profile_mark_begin(cudaStream_t st);
+void profile_mark_end(cudaStream_t st, int tag);
+
+// ---------------------------------------------------------------- FP32 SIMT GEMM
+// C[M x N] = op(A)[M x K] * B[K x N], op(A) = A^T when transA, row-major.
+// splits > 1 uses `part` (splits * M * N floats) and a fixed-order reduction.
+// sumsq (optional): += sum of squares of the A elements read.
+// gate (optional) with gate_mode 1: *gate == 0 -> C = A (B taken as identity,
+// needs !transA, K == N, one slice); gate_mode 2: *gate == 0 -> no work.
+// b_upper: B is upper triangular (k-tiles beyond the column tile are skipped).
+enum GateMode { kGateNone = 0, kGateCopy = 1, kGateSkip = 2 };
+cudaError_t gemm_f32_ex(bool transA, int64_t M, int64_t N, int64_t K, const float* A, int64_t lda,
+                        const float* B, int64_t ldb, float* C, int64_t ldc, int splits, float* part,
+                        double* sumsq, const int* gate, int gate_mode, bool b_upper, cudaStream_t st);
+int gemm_f32_splits(int64_t M, int64_t N, int64_t K);
+size_t gemm_f32_part_floats(int64_t M, int64_t N, int64_t K);
+
+// ---------------------------------------------------------------- d x d kernels
+// R^T R = G (+ s I on breakdown; raises *gate_out), Rinv = R^{-1}; gate_in == 0
+// -> R = Rinv = I. gstore: global scratch when the factor does not fit in
+// shared memory (chol_global_bytes(d, fp64) bytes, else unused).
+cudaError_t chol_inv(int d, const float* G, int64_t ldg, float* R, float* Rinv, int64_t ldr, int* info,
+                     double* shift_count, int* gate_out, const int* gate_in, void* gstore, bool fp64,
+                     cudaStream_t st);
+size_t chol_global_bytes(int d, bool fp64);
+cudaError_t transpose_small(int d, const float* X, int64_t ldx, float* Y, int64_t ldy, cudaStream_t st);
+cudaError_t write_L(int d, const float* Rh, int64_t ldrh, float* L, int64_t ldl, double* l2_accum,
+                    cudaStream_t st);
+cudaError_t init_scratch(int* info, int* gates, int ngates, double* scal, int nscal, cudaStream_t st);
+cudaError_t finish_diag(const double* scal, double* diag, int* info, cudaStream_t st);
+cudaError_t copy_matrix(int64_t rows, int64_t cols, const float* X, int64_t ldx, float* Y, int64_t ldy,
+                        cudaStream_t st);
+
+}  // namespace rqlp

@@ -1,0 +1,264 @@
+// FP32 SIMT GEMM engine: the plain-FP32 passes over A (Y = A^T X, Z = A X,
+// Algorithm 1 steps 3-4 and the power passes) and the tall-skinny products of
+// CholeskyQR (Gram X^T X, X R^{-1}).
+//
+// C = op(A) B with op(A) = A^T (transA) or A, row-major operands. Each CTA
+// owns a BM x BN tile of C and one slice of the K range (split-K); slices
+// write partial tiles that a second kernel sums in a fixed order (Kahan), so
+// results are deterministic. Tiles are staged through double-buffered shared
+// memory; each thread accumulates a TM x TN block in registers.
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace rqlp {
+
+namespace {
+
+struct GemmArgs {
+  int64_t M, N, K;
+  const float* A; int64_t lda;
+  const float* B; int64_t ldb;
+  float* C; int64_t ldc; int64_t c_slice;   // slice z writes C + z * c_slice
+  int64_t kchunk;                           // K range per slice (multiple of BK)
+  double* sumsq;                            // optional sum of squares of A
+  const int* gate;                          // optional gate word (see GateMode)
+  int gate_mode;
+  int b_upper;                              // B upper triangular: skip k >= n-tile end
+};
+
+template <int BM, int BN, int BK, int TM, int TN, bool TRANS_A>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+gemm_f32_kernel(GemmArgs g) {
+  constexpr int NT = (BM / TM) * (BN / TN);
+  constexpr int TX = BN / TN;
+  constexpr int AL = BM * BK / NT;
+  constexpr int BL = BN * BK / NT;
+  static_assert(AL * NT == BM * BK && BL * NT == BN * BK, "tile/thread mismatch");
+  __shared__ __align__(16) float As[2][BK][BM + 4];
+  __shared__ __align__(16) float Bs[2][BK][BN + 4];
+
+  const int tid = threadIdx.x;
+  const int tx = tid % TX, ty = tid / TX;
+  const int64_t m0 = (int64_t)blockIdx.y * BM, n0 = (int64_t)blockIdx.x * BN;
+  float* C = g.C + (int64_t)blockIdx.z * g.c_slice;
+
+  if (g.gate != nullptr && *g.gate == 0) {
+    if (g.gate_mode == kGateSkip) return;
+    // Gated off: B is taken as the identity (requires !TRANS_A, K == N, one slice).
+    for (int idx = tid; idx < BM * BN; idx += NT) {
+      int64_t gm = m0 + idx / BN, gn = n0 + idx % BN;
+      if (gm < g.M && gn < g.N) C[gm * g.ldc + gn] = g.A[gm * g.lda + gn];
+    }
+    return;
+  }
+
+  const int64_t kbeg = (int64_t)blockIdx.z * g.kchunk;
+  int64_t kend = kbeg + g.kchunk < g.K ? kbeg + g.kchunk : g.K;
+  if (g.b_upper && kend > n0 + BN) kend = n0 + BN;
+  const int64_t ntiles = kend > kbeg ? cdiv(kend - kbeg, BK) : 0;
+
+  float ra[AL], rb[BL];
+  float sq = 0.f, sq_c = 0.f;   // Kahan sum of squares of the A tiles read
+  const bool want_sq = g.sumsq != nullptr && blockIdx.x == 0;
+
+  auto load = [&](int64_t k0) {
+#pragma unroll
+    for (int r = 0; r < AL; ++r) {
+      int idx = tid + r * NT;
+      int kk = TRANS_A ? idx / BM : idx % BK;
+      int mm = TRANS_A ? idx % BM : idx / BK;
+      int64_t gk = k0 + kk, gm = m0 + mm;
+      float v = 0.f;
+      if (gk < kend && gm < g.M) v = TRANS_A ? g.A[gk * g.lda + gm] : g.A[gm * g.lda + gk];
+      ra[r] = v;
+    }
+#pragma unroll
+    for (int r = 0; r < BL; ++r) {
+      int idx = tid + r * NT;
+      int kk = idx / BN, nn = idx % BN;
+      int64_t gk = k0 + kk, gn = n0 + nn;
+      rb[r] = (gk < kend && gn < g.N) ? g.B[gk * g.ldb + gn] : 0.f;
+    }
+    if (want_sq) {
+      float s = 0.f;
+#pragma unroll
+      for (int r = 0; r < AL; ++r) s = fmaf(ra[r], ra[r], s);
+      float y = s - sq_c, t = sq + y;
+      sq_c = (t - sq) - y;
+      sq = t;
+    }
+  };
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int r = 0; r < AL; ++r) {
+      int idx = tid + r * NT;
+      int kk = TRANS_A ? idx / BM : idx % BK;
+      int mm = TRANS_A ? idx % BM : idx / BK;
+      As[buf][kk][mm] = ra[r];
+    }
+#pragma unroll
+    for (int r = 0; r < BL; ++r) {
+      int idx = tid + r * NT;
+      Bs[buf][idx / BN][idx % BN] = rb[r];
+    }
+  };
+
+  float acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = 0.f;
+
+  if (ntiles > 0) {
+    load(kbeg);
+    store(0);
+    __syncthreads();
+    for (int64_t t = 0; t < ntiles; ++t) {
+      const int buf = (int)(t & 1);
+      if (t + 1 < ntiles) load(kbeg + (t + 1) * BK);
+#pragma unroll
+      for (int kk = 0; kk < BK; ++kk) {
+        float a[TM], b[TN];
+#pragma unroll
+        for (int i = 0; i < TM; i += 4) {
+          float4 v = *reinterpret_cast<const float4*>(&As[buf][kk][ty * TM + i]);
+          a[i] = v.x; a[i + 1] = v.y; a[i + 2] = v.z; a[i + 3] = v.w;
+        }
+#pragma unroll
+        for (int j = 0; j < TN; j += 4) {
+          float4 v = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * TN + j]);
+          b[j] = v.x; b[j + 1] = v.y; b[j + 2] = v.z; b[j + 3] = v.w;
+        }
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+          for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+      }
+      if (t + 1 < ntiles) store(buf ^ 1);
+      __syncthreads();
+    }
+  }
+
+#pragma unroll
+  for (int i = 0; i < TM; ++i) {
+    int64_t gm = m0 + ty * TM + i;
+    if (gm >= g.M) continue;
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      int64_t gn = n0 + tx * TN + j;
+      if (gn < g.N) C[gm * g.ldc + gn] = acc[i][j];
+    }
+  }
+
+  if (want_sq) {
+    // Block reduction of the per-thread sums in double, one atomic per CTA.
+    __shared__ double red[32];
+    double v = (double)sq - (double)sq_c;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((tid & 31) == 0) red[tid >> 5] = v;
+    __syncthreads();
+    if (tid == 0) {
+      double s = 0.0;
+      for (int w = 0; w < NT / 32; ++w) s += red[w];
+      atomicAdd(g.sumsq, s);
+    }
+  }
+}
+
+// C[m, n] = sum_z part[z][m][n] (fixed order, Kahan-compensated FP32).
+__global__ void splitk_reduce_kernel(int64_t M, int64_t N, int splits, const float* __restrict__ part,
+                                     float* __restrict__ C, int64_t ldc) {
+  const int64_t total = M * N;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float s = 0.f, c = 0.f;
+    for (int z = 0; z < splits; ++z) {
+      float y = part[(int64_t)z * total + i] - c;
+      float t = s + y;
+      c = (t - s) - y;
+      s = t;
+    }
+    C[(i / N) * ldc + (i % N)] = s;
+  }
+}
+
+// Tile configuration: a large 128 x 64 tile for the passes over A and the
+// tall products, a small 32 x 32 tile for d x d work.
+bool use_big(int64_t M, int64_t N) { return M >= 1024 && N >= 48; }
+
+}  // namespace
+
+int sm_count() {
+  static int cached = 0;
+  if (cached == 0) {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && n > 0)
+      cached = n;
+    else
+      cached = 152;
+  }
+  return cached;
+}
+
+int gemm_f32_splits(int64_t M, int64_t N, int64_t K) {
+  const bool big = use_big(M, N);
+  const int64_t BM = big ? 128 : 32, BN = big ? 64 : 32;
+  const int64_t tiles = cdiv(M, BM) * cdiv(N, BN);
+  const int64_t resident = (int64_t)sm_count() * (big ? 2 : 8);
+  int64_t s = cdiv(resident * 2, tiles);            // about two waves of CTAs
+  int64_t maxs = K / 256;                           // keep >= 256 K per slice
+  if (s > maxs) s = maxs;
+  if (s > 64) s = 64;
+  if (s < 1) s = 1;
+  return (int)s;
+}
+
+size_t gemm_f32_part_floats(int64_t M, int64_t N, int64_t K) {
+  int s = gemm_f32_splits(M, N, K);
+  return s > 1 ? (size_t)s * (size_t)(M * N) : 0;
+}
+
+static cudaError_t launch_gemm(bool transA, const GemmArgs& g, int splits, cudaStream_t st) {
+  const bool big = use_big(g.M, g.N);
+  if (big) {
+    dim3 grid((unsigned)cdiv(g.N, 64), (unsigned)cdiv(g.M, 128), (unsigned)splits);
+    if (transA) gemm_f32_kernel<128, 64, 16, 8, 4, true><<<grid, 256, 0, st>>>(g);
+    else        gemm_f32_kernel<128, 64, 16, 8, 4, false><<<grid, 256, 0, st>>>(g);
+    note_launch();
+  } else {
+    dim3 grid((unsigned)cdiv(g.N, 32), (unsigned)cdiv(g.M, 32), (unsigned)splits);
+    if (transA) gemm_f32_kernel<32, 32, 16, 4, 4, true><<<grid, 64, 0, st>>>(g);
+    else        gemm_f32_kernel<32, 32, 16, 4, 4, false><<<grid, 64, 0, st>>>(g);
+    note_launch();
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t gemm_f32_ex(bool transA, int64_t M, int64_t N, int64_t K, const float* A, int64_t lda,
+                        const float* B, int64_t ldb, float* C, int64_t ldc, int splits, float* part,
+                        double* sumsq, const int* gate, int gate_mode, bool b_upper, cudaStream_t st) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  if (gate != nullptr && gate_mode == kGateCopy && (transA || K != N)) return cudaErrorInvalidValue;
+  if (gate != nullptr && gate_mode == kGateCopy) splits = 1;
+  GemmArgs g;
+  g.M = M; g.N = N; g.K = K; g.A = A; g.lda = lda; g.B = B; g.ldb = ldb;
+  g.sumsq = sumsq; g.gate = gate; g.gate_mode = gate_mode; g.b_upper = b_upper ? 1 : 0;
+  if (splits <= 1 || part == nullptr) {
+    g.C = C; g.ldc = ldc; g.c_slice = 0; g.kchunk = round_up(K > 0 ? K : 1, 16);
+    return launch_gemm(transA, g, 1, st);
+  }
+  g.C = part; g.ldc = N; g.c_slice = M * N;
+  g.kchunk = round_up(cdiv(K, splits), 16);
+  int used = (int)cdiv(K, g.kchunk);
+  cudaError_t e = launch_gemm(transA, g, used, st);
+  if (e != cudaSuccess) return e;
+  int64_t total = M * N;
+  int blocks = (int)std::min<int64_t>(cdiv(total, 256), (int64_t)sm_count() * 8);
+  splitk_reduce_kernel<<<blocks, 256, 0, st>>>(M, N, used, part, C, ldc);
+  note_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace rqlp

@@ -1,0 +1,441 @@
+// C ABI of the Rand-QLP library and the stream-ordered plan that runs the
+// truncated chain (section 3.1, Algorithm 1, with d = k + p sketch columns
+// and q power passes):
+//
+//   Y = A^T Omega -> P~ = qf(Y) -> q x [Z = qf(A P~), P~ = qf(A^T Z)]
+//   -> (Q, R) = qr(A P~) -> (P^, R^) = qr(R^T), L = R^^T, P = P~ P^.
+//
+// qf is CholeskyQR on the GPU. Intermediate bases (inside the power passes)
+// take one CholeskyQR pass: any upper-triangular right factor keeps
+// qf((A^T A)^q A^T Omega) unchanged, so they only need to stay well
+// conditioned. The bases that enter the result (the last P~, Q, and the QR
+// of R^T) take CholeskyQR2, plus a third pass when a Cholesky had to be
+// shifted (shifted CholeskyQR3); that pass is gated on a device flag so the
+// launch sequence is static and capturable.
+#include <algorithm>
+#include <cstring>
+
+#include "common.cuh"
+#include "tc_gemm.cuh"
+
+#define CK(x)                             \
+  do {                                    \
+    cudaError_t e_ = (x);                 \
+    if (e_ != cudaSuccess) return e_;     \
+  } while (0)
+
+namespace rqlp {
+namespace {
+
+constexpr int kGates = 8;   // gate words: one per final orthonormalisation
+constexpr int kScal = 4;    // [0] ||A||^2, [1] ||L||^2, [2] shifted Cholesky count, [3] spare
+
+// Building blocks of the chain for a fixed sketch width d, with their scratch.
+class Ops {
+ public:
+  Ops(int d, const rqlp_opts& o) : d_(d), ld_(round_up(d, 4)), o_(o) {}
+
+  // part_floats: largest split-K partial buffer any product of the caller needs.
+  void layout(Arena& ar, size_t part_floats, bool with_tc, int64_t m, int64_t n) {
+    const int64_t dd = (int64_t)d_ * ld_;
+    G_ = ar.take<float>(dd);
+    for (int i = 0; i < 3; ++i) {
+      R_[i] = ar.take<float>(dd);
+      Ri_[i] = ar.take<float>(dd);
+    }
+    Ra_ = ar.take<float>(dd);
+    part_ = ar.take<float>(std::max<size_t>(part_floats, 1));
+    scal = ar.take<double>(kScal);
+    gates = ar.take<int>(kGates);
+    cstore_ = ar.take<char>(chol_global_bytes(d_, o_.small_fp64 != 0));
+    if (with_tc) tc_.layout(ar, m, n, d_);
+  }
+  void bind(cudaStream_t st, int* info) { st_ = st; info_ = info; }
+  int64_t ld() const { return ld_; }
+  cudaStream_t stream() const { return st_; }
+
+  cudaError_t init() { return init_scratch(info_, gates, kGates, scal, kScal, st_); }
+
+  // transA: out (n x d) = A^T X (X m x d); else out (m x d) = A X (X n x d).
+  cudaError_t pass(bool transA, const float* A, int64_t m, int64_t n, int64_t lda, const float* X,
+                   int64_t ldx, float* out, int64_t ldout, double* sumsq) {
+    const bool prof = profiling_on();
+    if (prof) profile_mark_begin(st_);
+    cudaError_t e;
+    if (o_.precision == RQLP_PREC_BF16X3) {
+      e = tc_.pass(transA, A, m, n, lda, X, ldx, d_, out, ldout, sumsq, st_);
+    } else {
+      const int64_t M = transA ? n : m, K = transA ? m : n;
+      e = gemm_f32_ex(transA, M, d_, K, A, lda, X, ldx, out, ldout, gemm_f32_splits(M, d_, K), part_, sumsq,
+                      nullptr, kGateNone, false, st_);
+    }
+    if (prof) profile_mark_end(st_, transA ? 1 : 0);
+    return e;
+  }
+  static size_t pass_part_floats(int64_t m, int64_t n, int d) {
+    return std::max(gemm_f32_part_floats(n, d, m), gemm_f32_part_floats(m, d, n));
+  }
+  static size_t orth_part_floats(int64_t rows, int d) { return gemm_f32_part_floats(d, d, rows); }
+
+  // G = X^T X.
+  cudaError_t gram(const float* X, int64_t ldx, int64_t rows, const int* gate) {
+    return gemm_f32_ex(true, d_, d_, rows, X, ldx, X, ldx, G_, ld_, gemm_f32_splits(d_, d_, rows), part_,
+                       nullptr, gate, kGateSkip, false, st_);
+  }
+  // out = X Rinv (Rinv upper triangular); gate == 0 -> out = X.
+  cudaError_t trmm(const float* X, int64_t ldx, int64_t rows, const float* Rinv, float* out, int64_t ldout,
+                   const int* gate) {
+    return gemm_f32_ex(false, rows, d_, d_, X, ldx, Rinv, ld_, out, ldout, 1, nullptr, nullptr, gate,
+                       gate ? kGateCopy : kGateNone, true, st_);
+  }
+  cudaError_t chol(int slot, int* gate_out, const int* gate_in) {
+    return chol_inv(d_, G_, ld_, R_[slot], Ri_[slot], ld_, info_, &scal[2], gate_out, gate_in, cstore_,
+                    o_.small_fp64 != 0, st_);
+  }
+  // One CholeskyQR pass (shifted on breakdown): out = X R^{-1}.
+  cudaError_t orth_inter(const float* X, int64_t ldx, int64_t rows, float* out, int64_t ldout) {
+    CK(gram(X, ldx, rows, nullptr));
+    CK(chol(0, nullptr, nullptr));
+    return trmm(X, ldx, rows, Ri_[0], out, ldout, nullptr);
+  }
+  // CholeskyQR2 plus a third pass gated on a shifted Cholesky (shifted
+  // CholeskyQR3). X (rows x d) is overwritten; tmp holds rows x d (ld_);
+  // Racc (optional, d x d, ld_) receives R = R3 R2 R1.
+  cudaError_t orth_final(float* X, int64_t ldx, int64_t rows, float* out, int64_t ldout, float* tmp,
+                         float* Racc, int slot) {
+    int* g = &gates[slot];
+    CK(gram(X, ldx, rows, nullptr));
+    CK(chol(0, g, nullptr));
+    CK(trmm(X, ldx, rows, Ri_[0], tmp, ld_, nullptr));
+    CK(gram(tmp, ld_, rows, nullptr));
+    CK(chol(1, g, nullptr));
+    CK(trmm(tmp, ld_, rows, Ri_[1], X, ldx, nullptr));
+    CK(gram(X, ldx, rows, g));
+    CK(chol(2, nullptr, g));
+    CK(trmm(X, ldx, rows, Ri_[2], out, ldout, g));
+    if (Racc != nullptr) {
+      CK(gemm_f32_ex(false, d_, d_, d_, R_[1], ld_, R_[0], ld_, Ra_, ld_, 1, nullptr, nullptr, nullptr,
+                     kGateNone, true, st_));
+      CK(gemm_f32_ex(false, d_, d_, d_, R_[2], ld_, Ra_, ld_, Racc, ld_, 1, nullptr, nullptr, nullptr,
+                     kGateNone, true, st_));
+    }
+    return cudaSuccess;
+  }
+
+  double* scal = nullptr;
+  int* gates = nullptr;
+
+ private:
+  int d_;
+  int64_t ld_;
+  rqlp_opts o_;
+  cudaStream_t st_ = nullptr;
+  int* info_ = nullptr;
+  float *G_ = nullptr, *R_[3] = {}, *Ri_[3] = {}, *Ra_ = nullptr, *part_ = nullptr;
+  void* cstore_ = nullptr;
+  TcEngine tc_;
+};
+
+struct Dims {
+  int64_t m, n, lda, ldo;
+  int k, p, q, d;
+};
+
+struct Out {
+  float* Q; int64_t ldq;
+  float* L; int64_t ldl;
+  float* P; int64_t ldp;
+};
+
+// The whole chain for one matrix.
+class Plan {
+ public:
+  Plan(const Dims& dm, const rqlp_opts& o) : d_(dm), ops_(dm.d, o), o_(o) {}
+
+  size_t layout(Arena& ar) {
+    const int64_t ld = ops_.ld(), dd = (int64_t)d_.d * ld, tall = std::max(d_.m, d_.n);
+    Y_ = ar.take<float>(d_.n * ld);
+    Z_ = ar.take<float>(d_.m * ld);
+    Pt_ = ar.take<float>(d_.n * ld);
+    T1_ = ar.take<float>(tall * ld);
+    Rb_ = ar.take<float>(dd);
+    Rh_ = ar.take<float>(dd);
+    Ts_ = ar.take<float>(dd);
+    Ts2_ = ar.take<float>(dd);
+    Ph_ = ar.take<float>(dd);
+    size_t part = std::max({Ops::pass_part_floats(d_.m, d_.n, d_.d), Ops::orth_part_floats(d_.m, d_.d),
+                            Ops::orth_part_floats(d_.n, d_.d), Ops::orth_part_floats(d_.d, d_.d)});
+    ops_.layout(ar, part, o_.precision == RQLP_PREC_BF16X3, d_.m, d_.n);
+    return ar.off;
+  }
+
+  cudaError_t run(const float* A, const float* Om, const Out& out, int* info, double* diag, cudaStream_t st) {
+    ops_.bind(st, info);
+    const int64_t m = d_.m, n = d_.n, lda = d_.lda, ld = ops_.ld();
+    const int d = d_.d;
+    CK(ops_.init());
+    // Sketch Y = A^T Omega (Algorithm 1 step 3); ||A||_F^2 rides along.
+    CK(ops_.pass(true, A, m, n, lda, Om, d_.ldo, Y_, ld, &ops_.scal[0]));
+    if (d_.q == 0) CK(ops_.orth_final(Y_, ld, n, Pt_, ld, T1_, nullptr, 0));
+    else CK(ops_.orth_inter(Y_, ld, n, Pt_, ld));
+    for (int i = 1; i <= d_.q; ++i) {
+      CK(ops_.pass(false, A, m, n, lda, Pt_, ld, Z_, ld, nullptr));   // Z = A P~
+      CK(ops_.orth_inter(Z_, ld, m, T1_, ld));                        // Z = qf(Z), one pass
+      CK(ops_.pass(true, A, m, n, lda, T1_, ld, Y_, ld, nullptr));    // Y = A^T Z
+      if (i == d_.q) CK(ops_.orth_final(Y_, ld, n, Pt_, ld, T1_, nullptr, 0));
+      else CK(ops_.orth_inter(Y_, ld, n, Pt_, ld));
+    }
+    // (Q, R) = qr(A P~)  (Algorithm 1 step 4)
+    CK(ops_.pass(false, A, m, n, lda, Pt_, ld, Z_, ld, nullptr));
+    CK(ops_.orth_final(Z_, ld, m, out.Q, out.ldq, T1_, Rb_, 1));
+    // (P^, R^) = qr(R^T), L = R^^T  (step 5 applied to the d x d factor)
+    CK(transpose_small(d, Rb_, ld, Ts_, ld, st));
+    CK(ops_.orth_final(Ts_, ld, d, Ph_, ld, Ts2_, Rh_, 2));
+    CK(write_L(d, Rh_, ld, out.L, out.ldl, &ops_.scal[1], st));
+    // P = P~ P^
+    CK(gemm_f32_ex(false, n, d, d, Pt_, ld, Ph_, ld, out.P, out.ldp, 1, nullptr, nullptr, nullptr, kGateNone,
+                   false, st));
+    return finish_diag(ops_.scal, diag, info, st);
+  }
+
+ private:
+  Dims d_;
+  Ops ops_;
+  rqlp_opts o_;
+  float *Y_ = nullptr, *Z_ = nullptr, *Pt_ = nullptr, *T1_ = nullptr;
+  float *Rb_ = nullptr, *Rh_ = nullptr, *Ts_ = nullptr, *Ts2_ = nullptr, *Ph_ = nullptr;
+};
+
+rqlp_opts resolve(const rqlp_opts* o) {
+  rqlp_opts r;
+  rqlp_default_opts(&r);
+  if (o != nullptr) r = *o;
+  return r;
+}
+
+bool valid_opts(const rqlp_opts& o) {
+  if (o.precision != RQLP_PREC_FP32 && o.precision != RQLP_PREC_BF16X3) return false;
+  if (o.small_fp64 != 0 && o.small_fp64 != 1) return false;
+  for (int i = 0; i < 6; ++i)
+    if (o.reserved[i] != 0) return false;
+  return true;
+}
+
+bool valid_sizes(int64_t m, int64_t n, int k, int p, int q) {
+  if (m <= 0 || n <= 0 || k < 1 || p < 0 || q < 0 || q > 64) return false;
+  const int64_t d = (int64_t)k + p;
+  return d <= std::min(m, n) && d <= RQLP_MAX_D;
+}
+
+Dims make_dims(int64_t m, int64_t n, int64_t lda, int k, int p, int q, int64_t ldo) {
+  Dims dm;
+  dm.m = m; dm.n = n; dm.lda = lda; dm.ldo = ldo;
+  dm.k = k; dm.p = p; dm.q = q; dm.d = k + p;
+  return dm;
+}
+
+size_t plan_bytes(const Dims& dm, const rqlp_opts& o) {
+  Arena ar;
+  ar.dry = true;
+  Plan pl(dm, o);
+  return pl.layout(ar);
+}
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+Arena arena_over(void* ws, size_t bytes) {
+  Arena ar;
+  ar.base = static_cast<char*>(ws);
+  ar.cap = bytes;
+  return ar;
+}
+
+size_t sketch_bytes(int64_t m, int64_t n, int d, const rqlp_opts& o) {
+  Arena ar;
+  ar.dry = true;
+  Ops ops(d, o);
+  ops.layout(ar, Ops::pass_part_floats(m, n, d), o.precision == RQLP_PREC_BF16X3, m, n);
+  return ar.off;
+}
+
+size_t orth_bytes(int64_t rows, int d, const rqlp_opts& o) {
+  Arena ar;
+  ar.dry = true;
+  const int64_t ld = round_up(d, 4);
+  ar.take<float>(rows * ld);
+  ar.take<float>((int64_t)d * ld);
+  Ops ops(d, o);
+  ops.layout(ar, Ops::orth_part_floats(rows, d), false, rows, d);
+  return ar.off;
+}
+
+}  // namespace
+}  // namespace rqlp
+
+using namespace rqlp;
+
+extern "C" {
+
+void rqlp_default_opts(rqlp_opts* opts) {
+  if (opts == nullptr) return;
+  std::memset(opts, 0, sizeof(*opts));
+  opts->precision = RQLP_PREC_FP32;
+  opts->small_fp64 = 0;
+}
+
+size_t rqlp_workspace_bytes(int64_t m, int64_t n, int k, int p, int q, const rqlp_opts* opts) {
+  rqlp_opts o = resolve(opts);
+  if (!valid_opts(o) || !valid_sizes(m, n, k, p, q)) return 0;
+  return plan_bytes(make_dims(m, n, n, k, p, q, k + p), o);
+}
+
+rqlp_status rqlp_factor(const float* A, int64_t m, int64_t n, int64_t lda, int k, int p, int q,
+                        const float* Omega, int64_t ldo, float* Q, int64_t ldq, float* L, int64_t ldl,
+                        float* P, int64_t ldp, void* workspace, size_t ws_bytes, int* d_info, double* d_diag,
+                        const rqlp_opts* opts, void* stream) {
+  rqlp_opts o = resolve(opts);
+  if (!valid_opts(o) || !valid_sizes(m, n, k, p, q)) return RQLP_ERR_ARG;
+  const int d = k + p;
+  if (A == nullptr || Omega == nullptr || Q == nullptr || L == nullptr || P == nullptr || d_info == nullptr)
+    return RQLP_ERR_ARG;
+  if (lda < n || ldo < d || ldq < d || ldl < d || ldp < d) return RQLP_ERR_ARG;
+  if (o.precision == RQLP_PREC_BF16X3 && !tc_supported(A, lda, Omega, ldo)) return RQLP_ERR_UNSUPPORTED;
+  Dims dm = make_dims(m, n, lda, k, p, q, ldo);
+  const size_t need = plan_bytes(dm, o);
+  if (workspace == nullptr || ws_bytes < need || !aligned(workspace, 256)) return RQLP_ERR_WORKSPACE;
+  Arena ar = arena_over(workspace, ws_bytes);
+  Plan pl(dm, o);
+  pl.layout(ar);
+  Out out{Q, ldq, L, ldl, P, ldp};
+  cudaError_t e = pl.run(A, Omega, out, d_info, d_diag, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? RQLP_OK : RQLP_ERR_CUDA;
+}
+
+size_t rqlp_host_workspace_bytes(int64_t m, int64_t n, int k, int p, int q, const rqlp_opts* opts) {
+  size_t core = rqlp_workspace_bytes(m, n, k, p, q, opts);
+  if (core == 0) return 0;
+  const int64_t d = k + p, ld = round_up(d, 4);
+  Arena ar;
+  ar.dry = true;
+  ar.take<float>((size_t)(m * n));
+  ar.take<float>((size_t)(m * ld));
+  ar.take<float>((size_t)(m * ld));
+  ar.take<float>((size_t)(d * ld));
+  ar.take<float>((size_t)(n * ld));
+  ar.take<int>(RQLP_INFO_INTS);
+  ar.take<double>(RQLP_DIAG_DOUBLES);
+  return round_up((int64_t)ar.off, 256) + core;
+}
+
+rqlp_status rqlp_factor_host(const float* hA, int64_t m, int64_t n, int64_t lda, int k, int p, int q,
+                             const float* hOmega, int64_t ldo, float* hQ, int64_t ldq, float* hL, int64_t ldl,
+                             float* hP, int64_t ldp, void* workspace, size_t ws_bytes, int* h_info,
+                             double* h_diag, const rqlp_opts* opts, void* stream) {
+  rqlp_opts o = resolve(opts);
+  if (!valid_opts(o) || !valid_sizes(m, n, k, p, q)) return RQLP_ERR_ARG;
+  const int64_t d = k + p, ld = round_up(d, 4);
+  if (hA == nullptr || hOmega == nullptr || hQ == nullptr || hL == nullptr || hP == nullptr ||
+      h_info == nullptr)
+    return RQLP_ERR_ARG;
+  if (lda < n || ldo < d || ldq < d || ldl < d || ldp < d) return RQLP_ERR_ARG;
+  const size_t need = rqlp_host_workspace_bytes(m, n, k, p, q, &o);
+  if (workspace == nullptr || ws_bytes < need || !aligned(workspace, 256)) return RQLP_ERR_WORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Arena ar = arena_over(workspace, ws_bytes);
+  float* A = ar.take<float>((size_t)(m * n));
+  float* Om = ar.take<float>((size_t)(m * ld));
+  float* Q = ar.take<float>((size_t)(m * ld));
+  float* L = ar.take<float>((size_t)(d * ld));
+  float* P = ar.take<float>((size_t)(n * ld));
+  int* info = ar.take<int>(RQLP_INFO_INTS);
+  double* diag = ar.take<double>(RQLP_DIAG_DOUBLES);
+  const size_t off = (size_t)round_up((int64_t)ar.off, 256);
+  void* core = static_cast<char*>(workspace) + off;
+  const size_t F = sizeof(float);
+  if (cudaMemcpy2DAsync(A, n * F, hA, lda * F, n * F, m, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpy2DAsync(Om, ld * F, hOmega, ldo * F, d * F, m, cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return RQLP_ERR_CUDA;
+  rqlp_status s = rqlp_factor(A, m, n, n, k, p, q, Om, ld, Q, ld, L, ld, P, ld, core, ws_bytes - off, info,
+                              diag, &o, stream);
+  if (s != RQLP_OK) return s;
+  if (cudaMemcpy2DAsync(hQ, ldq * F, Q, ld * F, d * F, m, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaMemcpy2DAsync(hL, ldl * F, L, ld * F, d * F, d, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaMemcpy2DAsync(hP, ldp * F, P, ld * F, d * F, n, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaMemcpyAsync(h_info, info, RQLP_INFO_INTS * sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return RQLP_ERR_CUDA;
+  if (h_diag != nullptr &&
+      cudaMemcpyAsync(h_diag, diag, RQLP_DIAG_DOUBLES * sizeof(double), cudaMemcpyDeviceToHost, st) !=
+          cudaSuccess)
+    return RQLP_ERR_CUDA;
+  return cudaStreamSynchronize(st) == cudaSuccess ? RQLP_OK : RQLP_ERR_CUDA;
+}
+
+size_t rqlp_sketch_workspace_bytes(int trans, int64_t m, int64_t n, int d, const rqlp_opts* opts) {
+  rqlp_opts o = resolve(opts);
+  if (!valid_opts(o) || (trans != 0 && trans != 1) || m <= 0 || n <= 0 || d < 1 || d > RQLP_MAX_D) return 0;
+  return sketch_bytes(m, n, d, o);
+}
+
+rqlp_status rqlp_sketch(int trans, const float* A, int64_t m, int64_t n, int64_t lda, const float* X,
+                        int64_t ldx, int d, float* Y, int64_t ldy, void* workspace, size_t ws_bytes,
+                        const rqlp_opts* opts, void* stream) {
+  rqlp_opts o = resolve(opts);
+  const size_t need = rqlp_sketch_workspace_bytes(trans, m, n, d, &o);
+  if (need == 0 || A == nullptr || X == nullptr || Y == nullptr || lda < n || ldx < d || ldy < d)
+    return RQLP_ERR_ARG;
+  if (o.precision == RQLP_PREC_BF16X3 && !tc_supported(A, lda, X, ldx)) return RQLP_ERR_UNSUPPORTED;
+  if (workspace == nullptr || ws_bytes < need || !aligned(workspace, 256)) return RQLP_ERR_WORKSPACE;
+  Arena ar = arena_over(workspace, ws_bytes);
+  Ops ops(d, o);
+  ops.layout(ar, Ops::pass_part_floats(m, n, d), o.precision == RQLP_PREC_BF16X3, m, n);
+  ops.bind(static_cast<cudaStream_t>(stream), nullptr);
+  cudaError_t e = ops.pass(trans == 1, A, m, n, lda, X, ldx, Y, ldy, nullptr);
+  return e == cudaSuccess ? RQLP_OK : RQLP_ERR_CUDA;
+}
+
+size_t rqlp_orth_workspace_bytes(int64_t rows, int d, const rqlp_opts* opts) {
+  rqlp_opts o = resolve(opts);
+  if (!valid_opts(o) || d < 1 || d > RQLP_MAX_D || rows < d) return 0;
+  return orth_bytes(rows, d, o);
+}
+
+rqlp_status rqlp_orth(float* X, int64_t rows, int d, int64_t ldx, float* R, int64_t ldr, void* workspace,
+                      size_t ws_bytes, int* d_info, const rqlp_opts* opts, void* stream) {
+  rqlp_opts o = resolve(opts);
+  const size_t need = rqlp_orth_workspace_bytes(rows, d, &o);
+  if (need == 0 || X == nullptr || d_info == nullptr || ldx < d || (R != nullptr && ldr < d)) return RQLP_ERR_ARG;
+  if (workspace == nullptr || ws_bytes < need || !aligned(workspace, 256)) return RQLP_ERR_WORKSPACE;
+  Arena ar = arena_over(workspace, ws_bytes);
+  const int64_t ld = round_up(d, 4);
+  float* tmp = ar.take<float>(rows * ld);
+  float* Racc = ar.take<float>((int64_t)d * ld);
+  Ops ops(d, o);
+  ops.layout(ar, Ops::orth_part_floats(rows, d), false, rows, d);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  ops.bind(st, d_info);
+  // The last pass reads X, so it writes tmp (free again by then) and Q is
+  // copied back into X afterwards.
+  cudaError_t e = ops.init();
+  if (e == cudaSuccess) e = ops.orth_final(X, ldx, rows, tmp, ld, tmp, Racc, 0);
+  if (e == cudaSuccess) e = copy_matrix(rows, d, tmp, ld, X, ldx, st);
+  if (e == cudaSuccess && R != nullptr) e = copy_matrix(d, d, Racc, ld, R, ldr, st);
+  return e == cudaSuccess ? RQLP_OK : RQLP_ERR_CUDA;
+}
+
+const char* rqlp_status_string(int status) {
+  switch (status) {
+    case RQLP_OK: return "ok";
+    case RQLP_ERR_ARG: return "invalid argument";
+    case RQLP_ERR_CUDA: return "CUDA error";
+    case RQLP_ERR_BREAKDOWN: return "Cholesky breakdown (rank-deficient input)";
+    case RQLP_ERR_NONFINITE: return "non-finite input";
+    case RQLP_ERR_TIMEOUT: return "device wait timed out";
+    case RQLP_ERR_WORKSPACE: return "workspace too small or misaligned";
+    case RQLP_ERR_UNSUPPORTED: return "unsupported option";
+    default: return "unknown status";
+  }
+}
+
+int rqlp_version(void) { return 100; }
+
+}  // extern "C"

@@ -134,7 +134,7 @@ def low_rank_matrix_torch(m: int, n: int, sigma: np.ndarray, noise: float, seed:
     """Same family as ``low_rank_matrix`` built on a device with torch (FP32 out).
 
     For the 20000 x 20000 class the host build is too slow; U_r, V_r come from
-    cuSOLVER QR of torch Gaussians, A from one FP32 matmul (TF32 disabled).
+    cuSOLVER QR of FP64 torch Gaussians, A from one FP32 matmul (TF32 disabled).
     The result is a different draw than the host builder for the same seed.
     """
     import torch
@@ -149,10 +149,10 @@ def low_rank_matrix_torch(m: int, n: int, sigma: np.ndarray, noise: float, seed:
             s = torch.sign(torch.diagonal(Rh))
             s[s == 0] = 1.0
             return Qh * s
-        U = haar(m)
-        V = haar(n)
         sg = torch.as_tensor(np.asarray(sigma[:rank], dtype=np.float64), device=device)
-        A = ((U * sg) @ V.T).to(torch.float32)
+        U = (haar(m) * sg).to(torch.float32)
+        V = haar(n).to(torch.float32)
+        A = U @ V.T
         del U, V
         if noise:
             A.add_(torch.randn(m, n, generator=gen, device=device, dtype=torch.float32),

@@ -1,0 +1,303 @@
+"""Thin ctypes binding of librqlp.so (the C ABI declared in include/rqlp.h).
+
+The functions named ``rqlp_*`` mirror the C entry points one to one and only
+marshal arguments: torch CUDA tensors are passed as raw device pointers, the
+current torch stream as the cudaStream_t. Every step of the factorisation
+runs in the library's CUDA kernels; there is no CPU fallback, and loading
+fails loudly when the library has not been built.
+
+``factor`` is the convenience call: it allocates the outputs and the workspace
+with torch and returns (Q, L, P, info, diag).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+__all__ = ["load", "RqlpError", "rqlp_default_opts", "rqlp_workspace_bytes", "rqlp_factor",
+           "rqlp_host_workspace_bytes", "rqlp_factor_host", "rqlp_status_string", "rqlp_version",
+           "factor", "factor_host", "Opts", "PREC_FP32", "PREC_BF16X3", "STATUS", "EXPORTED"]
+
+PREC_FP32 = 0
+PREC_BF16X3 = 1
+MAX_D = 256
+STATUS = {0: "RQLP_OK", 1: "RQLP_ERR_ARG", 2: "RQLP_ERR_CUDA", 3: "RQLP_ERR_BREAKDOWN",
+          4: "RQLP_ERR_NONFINITE", 5: "RQLP_ERR_TIMEOUT", 6: "RQLP_ERR_WORKSPACE",
+          7: "RQLP_ERR_UNSUPPORTED"}
+
+# Every symbol include/rqlp.h declares (checked by the ABI test).
+EXPORTED = ["rqlp_default_opts", "rqlp_workspace_bytes", "rqlp_factor", "rqlp_host_workspace_bytes",
+            "rqlp_factor_host", "rqlp_sketch_workspace_bytes", "rqlp_sketch",
+            "rqlp_orth_workspace_bytes", "rqlp_orth", "rqlp_kernel_launches", "rqlp_profile_enable",
+            "rqlp_profile_read", "rqlp_status_string", "rqlp_version"]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("small_fp64", ctypes.c_int),
+                ("reserved", ctypes.c_int * 6)]
+
+
+class RqlpError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__(f"{where}: {STATUS.get(status, status)} ({rqlp_status_string(status)})")
+        self.status = status
+
+
+_lib = None
+_i64, _int, _vp, _sz = ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t
+
+
+def _declare(lib):
+    lib.rqlp_default_opts.argtypes = [ctypes.POINTER(Opts)]
+    lib.rqlp_default_opts.restype = None
+    lib.rqlp_workspace_bytes.argtypes = [_i64, _i64, _int, _int, _int, ctypes.POINTER(Opts)]
+    lib.rqlp_workspace_bytes.restype = _sz
+    lib.rqlp_host_workspace_bytes.argtypes = [_i64, _i64, _int, _int, _int, ctypes.POINTER(Opts)]
+    lib.rqlp_host_workspace_bytes.restype = _sz
+    sig = [_vp, _i64, _i64, _i64, _int, _int, _int, _vp, _i64, _vp, _i64, _vp, _i64, _vp, _i64,
+           _vp, _sz, _vp, _vp, ctypes.POINTER(Opts), _vp]
+    lib.rqlp_factor.argtypes = sig
+    lib.rqlp_factor.restype = _int
+    lib.rqlp_factor_host.argtypes = sig
+    lib.rqlp_factor_host.restype = _int
+    lib.rqlp_sketch_workspace_bytes.argtypes = [_int, _i64, _i64, _int, ctypes.POINTER(Opts)]
+    lib.rqlp_sketch_workspace_bytes.restype = _sz
+    lib.rqlp_sketch.argtypes = [_int, _vp, _i64, _i64, _i64, _vp, _i64, _int, _vp, _i64, _vp, _sz,
+                                ctypes.POINTER(Opts), _vp]
+    lib.rqlp_sketch.restype = _int
+    lib.rqlp_orth_workspace_bytes.argtypes = [_i64, _int, ctypes.POINTER(Opts)]
+    lib.rqlp_orth_workspace_bytes.restype = _sz
+    lib.rqlp_orth.argtypes = [_vp, _i64, _int, _i64, _vp, _i64, _vp, _sz, _vp, ctypes.POINTER(Opts), _vp]
+    lib.rqlp_orth.restype = _int
+    lib.rqlp_kernel_launches.argtypes = []
+    lib.rqlp_kernel_launches.restype = ctypes.c_ulonglong
+    lib.rqlp_profile_enable.argtypes = [_int]
+    lib.rqlp_profile_enable.restype = _int
+    lib.rqlp_profile_read.argtypes = [ctypes.POINTER(ctypes.c_float), ctypes.POINTER(_int), _int]
+    lib.rqlp_profile_read.restype = _int
+    lib.rqlp_status_string.argtypes = [_int]
+    lib.rqlp_status_string.restype = ctypes.c_char_p
+    lib.rqlp_version.argtypes = []
+    lib.rqlp_version.restype = _int
+
+
+def load(build_if_missing: bool = True):
+    """Load librqlp.so (building it first if needed); raises if unavailable."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path) or (build_if_missing and not _build.up_to_date()):
+        if not build_if_missing:
+            raise RuntimeError(f"{path} is missing: run paper_2110_01011_gb300.build.build()")
+        _build.build()
+    lib = ctypes.CDLL(path)
+    _declare(lib)
+    _lib = lib
+    return lib
+
+
+def _opts(precision=PREC_FP32, small_fp64=False):
+    o = Opts()
+    load().rqlp_default_opts(ctypes.byref(o))
+    o.precision = int(precision)
+    o.small_fp64 = 1 if small_fp64 else 0
+    return o
+
+
+# ------------------------------------------------------------------ 1:1 entry points
+
+def rqlp_default_opts():
+    return _opts()
+
+
+def rqlp_workspace_bytes(m, n, k, p, q, opts=None):
+    return int(load().rqlp_workspace_bytes(m, n, k, p, q, ctypes.byref(opts or _opts())))
+
+
+def rqlp_host_workspace_bytes(m, n, k, p, q, opts=None):
+    return int(load().rqlp_host_workspace_bytes(m, n, k, p, q, ctypes.byref(opts or _opts())))
+
+
+def rqlp_factor(A, m, n, lda, k, p, q, Omega, ldo, Q, ldq, L, ldl, P, ldp, workspace, ws_bytes,
+                d_info, d_diag, opts, stream):
+    """Raw call: pointer arguments are ints (device addresses) or None."""
+    return int(load().rqlp_factor(A, m, n, lda, k, p, q, Omega, ldo, Q, ldq, L, ldl, P, ldp,
+                                  workspace, ws_bytes, d_info, d_diag,
+                                  ctypes.byref(opts) if opts is not None else None, stream))
+
+
+def rqlp_factor_host(A, m, n, lda, k, p, q, Omega, ldo, Q, ldq, L, ldl, P, ldp, workspace,
+                     ws_bytes, h_info, h_diag, opts, stream):
+    """Raw call: A, Omega, Q, L, P, h_info, h_diag are host addresses."""
+    return int(load().rqlp_factor_host(A, m, n, lda, k, p, q, Omega, ldo, Q, ldq, L, ldl, P, ldp,
+                                       workspace, ws_bytes, h_info, h_diag,
+                                       ctypes.byref(opts) if opts is not None else None, stream))
+
+
+def rqlp_sketch_workspace_bytes(trans, m, n, d, opts=None):
+    return int(load().rqlp_sketch_workspace_bytes(trans, m, n, d, ctypes.byref(opts or _opts())))
+
+
+def rqlp_sketch(trans, A, m, n, lda, X, ldx, d, Y, ldy, workspace, ws_bytes, opts, stream):
+    return int(load().rqlp_sketch(trans, A, m, n, lda, X, ldx, d, Y, ldy, workspace, ws_bytes,
+                                  ctypes.byref(opts) if opts is not None else None, stream))
+
+
+def rqlp_orth_workspace_bytes(rows, d, opts=None):
+    return int(load().rqlp_orth_workspace_bytes(rows, d, ctypes.byref(opts or _opts())))
+
+
+def rqlp_orth(X, rows, d, ldx, R, ldr, workspace, ws_bytes, d_info, opts, stream):
+    return int(load().rqlp_orth(X, rows, d, ldx, R, ldr, workspace, ws_bytes, d_info,
+                                ctypes.byref(opts) if opts is not None else None, stream))
+
+
+def rqlp_kernel_launches():
+    return int(load().rqlp_kernel_launches())
+
+
+def rqlp_profile_enable(on):
+    return int(load().rqlp_profile_enable(1 if on else 0))
+
+
+def rqlp_profile_read(cap=4096):
+    """Returns a list of (ms, tag) for the recorded passes over A."""
+    ms = (ctypes.c_float * cap)()
+    tags = (_int * cap)()
+    n = int(load().rqlp_profile_read(ms, tags, cap))
+    return [(float(ms[i]), int(tags[i])) for i in range(n)]
+
+
+def rqlp_status_string(status):
+    return load().rqlp_status_string(int(status)).decode()
+
+
+def rqlp_version():
+    return int(load().rqlp_version())
+
+
+# ------------------------------------------------------------------ torch conveniences
+
+def _ptr(t):
+    return None if t is None else t.data_ptr()
+
+
+def _stream():
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+def factor(A, k, p, q, Omega, precision=PREC_FP32, small_fp64=False, workspace=None, out=None):
+    """Factor a CUDA FP32 row-major A (m x n) with Omega (m x (k+p)).
+
+    Returns (Q, L, P, info, diag) as CUDA tensors; info (int32[2]) and diag
+    (float64[4]) are filled asynchronously on the current stream.
+    """
+    import torch
+    m, n = A.shape
+    d = k + p
+    if A.dtype != torch.float32 or Omega.dtype != torch.float32 or not A.is_cuda:
+        raise TypeError("A and Omega must be CUDA float32 tensors")
+    if A.stride(1) != 1 or Omega.stride(1) != 1:
+        raise ValueError("A and Omega must be row-major (unit column stride)")
+    opts = _opts(precision, small_fp64)
+    ws_bytes = rqlp_workspace_bytes(m, n, k, p, q, opts)
+    if ws_bytes == 0:
+        raise RqlpError(1, "rqlp_workspace_bytes")
+    dev = A.device
+    if workspace is None or workspace.numel() < ws_bytes + 256:
+        workspace = torch.empty(ws_bytes + 256, dtype=torch.uint8, device=dev)
+    if out is None:
+        Q = torch.empty(m, d, dtype=torch.float32, device=dev)
+        L = torch.empty(d, d, dtype=torch.float32, device=dev)
+        P = torch.empty(n, d, dtype=torch.float32, device=dev)
+        info = torch.empty(2, dtype=torch.int32, device=dev)
+        diag = torch.empty(4, dtype=torch.float64, device=dev)
+    else:
+        Q, L, P, info, diag = out
+    base = workspace.data_ptr()
+    aligned = (base + 255) // 256 * 256
+    st = rqlp_factor(A.data_ptr(), m, n, A.stride(0), k, p, q, Omega.data_ptr(), Omega.stride(0),
+                     Q.data_ptr(), Q.stride(0), L.data_ptr(), L.stride(0), P.data_ptr(), P.stride(0),
+                     aligned, ws_bytes, info.data_ptr(), diag.data_ptr(), opts, _stream())
+    if st != 0:
+        raise RqlpError(st, "rqlp_factor")
+    return Q, L, P, info, diag
+
+
+def _workspace(nbytes, device):
+    import torch
+    buf = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+    return buf, (buf.data_ptr() + 255) // 256 * 256
+
+
+def sketch(A, X, trans, precision=PREC_FP32):
+    """Y = A^T X (trans=1) or A X (trans=0) for CUDA float32 row-major A, X."""
+    import torch
+    m, n = A.shape
+    d = X.shape[1]
+    opts = _opts(precision)
+    nb = rqlp_sketch_workspace_bytes(trans, m, n, d, opts)
+    if nb == 0:
+        raise RqlpError(1, "rqlp_sketch_workspace_bytes")
+    buf, ws = _workspace(nb, A.device)
+    Y = torch.empty(n if trans else m, d, dtype=torch.float32, device=A.device)
+    st = rqlp_sketch(trans, A.data_ptr(), m, n, A.stride(0), X.data_ptr(), X.stride(0), d,
+                     Y.data_ptr(), Y.stride(0), ws, nb, opts, _stream())
+    if st != 0:
+        raise RqlpError(st, "rqlp_sketch")
+    return Y, buf
+
+
+def orth(X, small_fp64=False):
+    """In-place X = qf(X) for a CUDA float32 row-major X; returns (X, R, info)."""
+    import torch
+    rows, d = X.shape
+    opts = _opts(PREC_FP32, small_fp64)
+    nb = rqlp_orth_workspace_bytes(rows, d, opts)
+    if nb == 0:
+        raise RqlpError(1, "rqlp_orth_workspace_bytes")
+    buf, ws = _workspace(nb, X.device)
+    R = torch.empty(d, d, dtype=torch.float32, device=X.device)
+    info = torch.empty(2, dtype=torch.int32, device=X.device)
+    st = rqlp_orth(X.data_ptr(), rows, d, X.stride(0), R.data_ptr(), R.stride(0), ws, nb,
+                   info.data_ptr(), opts, _stream())
+    if st != 0:
+        raise RqlpError(st, "rqlp_orth")
+    return X, R, info, buf
+
+
+def factor_host(A, k, p, q, Omega, precision=PREC_FP32, workspace=None, out=None):
+    """Host-buffer form: numpy/torch CPU float32 A and Omega (pinned for full
+    bandwidth). Returns host (Q, L, P, info, diag); synchronous."""
+    import torch
+    A_t = torch.as_tensor(A)
+    O_t = torch.as_tensor(Omega)
+    m, n = A_t.shape
+    d = k + p
+    opts = _opts(precision)
+    ws_bytes = rqlp_host_workspace_bytes(m, n, k, p, q, opts)
+    if ws_bytes == 0:
+        raise RqlpError(1, "rqlp_host_workspace_bytes")
+    if workspace is None or workspace.numel() < ws_bytes + 256:
+        workspace = torch.empty(ws_bytes + 256, dtype=torch.uint8, device="cuda")
+    if out is None:
+        pin = torch.cuda.is_available()
+        Q = torch.empty(m, d, dtype=torch.float32, pin_memory=pin)
+        L = torch.empty(d, d, dtype=torch.float32, pin_memory=pin)
+        P = torch.empty(n, d, dtype=torch.float32, pin_memory=pin)
+        info = torch.zeros(2, dtype=torch.int32)
+        diag = torch.zeros(4, dtype=torch.float64)
+    else:
+        Q, L, P, info, diag = out
+    aligned = (workspace.data_ptr() + 255) // 256 * 256
+    st = rqlp_factor_host(A_t.data_ptr(), m, n, A_t.stride(0), k, p, q, O_t.data_ptr(),
+                          O_t.stride(0), Q.data_ptr(), Q.stride(0), L.data_ptr(), L.stride(0),
+                          P.data_ptr(), P.stride(0), aligned, ws_bytes, info.data_ptr(),
+                          diag.data_ptr(), opts, _stream())
+    if st != 0:
+        raise RqlpError(st, "rqlp_factor_host")
+    return Q, L, P, info, diag

@@ -1,0 +1,64 @@
+"""Helpers shared by the GPU parity tests: run the CUDA path through the
+C-ABI binding, run the FP64 oracle on the same inputs, compare."""
+from __future__ import annotations
+
+import numpy as np
+
+from oracle import rqlp_oracle as orc
+
+# Tolerances (FP32 path vs FP64 oracle); the derivation is in the design notes:
+# leading-k |L_ii| relative 1e-4, ||Q^T Q - I||_F <= 1e-5, relative residual
+# within 1e-3 (relative) of the oracle's.
+TOL_LII = 1e-4
+TOL_ORTH = 1e-5
+TOL_RES = 1e-3
+
+
+def run_gpu(A, Om, k, p, q, precision=0, small_fp64=False):
+    import torch
+
+    from paper_2110_01011_gb300 import rqlp
+    dA = torch.from_numpy(np.ascontiguousarray(A, dtype=np.float32)).cuda()
+    dO = torch.from_numpy(np.ascontiguousarray(Om, dtype=np.float32)).cuda()
+    Q, L, P, info, diag = rqlp.factor(dA, k, p, q, dO, precision=precision, small_fp64=small_fp64)
+    torch.cuda.synchronize()
+    return (Q.double().cpu().numpy(), L.double().cpu().numpy(), P.double().cpu().numpy(),
+            info.cpu().numpy(), diag.cpu().numpy())
+
+
+def relres(A, Q, L, P):
+    A = np.asarray(A, dtype=np.float64)
+    return np.linalg.norm(A - (Q @ L) @ P.T) / np.linalg.norm(A)
+
+
+def compare(A, Om, k, p, q, gpu, elem_atol=2e-4):
+    """Compare GPU factors with the oracle; returns a dict of measured errors
+    and asserts the tolerances."""
+    Qg, Lg, Pg, info, diag = gpu
+    A64 = np.asarray(A, dtype=np.float64)
+    ref = orc.rand_qlp(A64, np.asarray(Om, dtype=np.float64), q)
+    d = k + p
+    assert info[0] == 0, f"info={info}"
+    err = {}
+    err["orthQ"] = np.linalg.norm(Qg.T @ Qg - np.eye(d))
+    err["orthP"] = np.linalg.norm(Pg.T @ Pg - np.eye(d))
+    err["Lii_rel"] = np.max(np.abs(np.diag(Lg)[:k] - np.diag(ref.L)[:k]) / np.abs(np.diag(ref.L)[:k]))
+    rg, ro = relres(A64, Qg, Lg, Pg), relres(A64, ref.Q, ref.L, ref.P)
+    err["res_gpu"], err["res_oracle"] = rg, ro
+    err["res_rel"] = abs(rg - ro) / ro if ro > 0 else abs(rg)
+    err["Q_lead"] = np.max(np.abs(Qg[:, :k] - ref.Q[:, :k]))
+    err["P_lead"] = np.max(np.abs(Pg[:, :k] - ref.P[:, :k]))
+    err["L_lead"] = np.max(np.abs(Lg[:k, :k] - ref.L[:k, :k])) / np.abs(ref.L).max()
+    err["L_upper_zero"] = float(np.abs(np.triu(Lg, 1)).max()) if d > 1 else 0.0
+    nA2 = np.linalg.norm(A64) ** 2
+    err["diag_A2_rel"] = abs(diag[0] - nA2) / nA2
+    assert err["L_upper_zero"] == 0.0
+    assert (np.diag(Lg) > 0).all()
+    assert err["orthQ"] <= TOL_ORTH, err
+    assert err["orthP"] <= TOL_ORTH, err
+    assert err["Lii_rel"] <= TOL_LII, err
+    assert err["res_rel"] <= TOL_RES or abs(rg - ro) <= 1e-6, err
+    assert err["Q_lead"] <= elem_atol and err["P_lead"] <= elem_atol, err
+    assert err["L_lead"] <= elem_atol, err
+    assert err["diag_A2_rel"] <= 1e-6, err
+    return err

@@ -1,0 +1,92 @@
+"""C-ABI checks that need no GPU: the library builds, loads, exports every
+symbol include/rqlp.h declares, and rejects invalid arguments before any
+device work."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2110_01011_gb300 import build, rqlp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_symbols():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", h)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(rqlp_\w+)\s*\(", text))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return rqlp.load()
+
+
+def test_exports_every_declared_symbol(lib):
+    declared = _declared_symbols()
+    assert declared, "no declarations found"
+    for name in sorted(declared):
+        assert hasattr(lib, name), name
+    assert declared == set(rqlp.EXPORTED)
+
+
+def test_host_only_calls(lib):
+    assert rqlp.rqlp_version() >= 100
+    assert rqlp.rqlp_status_string(0) == "ok"
+    assert "breakdown" in rqlp.rqlp_status_string(3).lower()
+    o = rqlp.rqlp_default_opts()
+    assert o.precision == rqlp.PREC_FP32 and o.small_fp64 == 0
+    assert list(o.reserved) == [0] * 6
+
+
+@pytest.mark.parametrize("m,n,k,p,q", [(0, 10, 1, 0, 0), (10, 10, 0, 1, 0), (10, 10, 8, 3, 0),
+                                       (300, 300, 250, 10, 0), (10, 10, 2, -1, 0),
+                                       (10, 10, 2, 1, -1)])
+def test_workspace_rejects_bad_sizes(lib, m, n, k, p, q):
+    assert rqlp.rqlp_workspace_bytes(m, n, k, p, q) == 0
+
+
+def test_workspace_grows_with_size(lib):
+    a = rqlp.rqlp_workspace_bytes(1000, 1000, 20, 5, 1)
+    b = rqlp.rqlp_workspace_bytes(4000, 2000, 20, 5, 1)
+    assert 0 < a < b
+    assert rqlp.rqlp_host_workspace_bytes(1000, 1000, 20, 5, 1) > a + 4 * 1000 * 1000
+
+
+def test_bad_opts_rejected(lib):
+    o = rqlp.rqlp_default_opts()
+    o.reserved[0] = 1
+    assert rqlp.rqlp_workspace_bytes(100, 100, 5, 5, 0, o) == 0
+    o = rqlp.rqlp_default_opts()
+    o.precision = 7
+    assert rqlp.rqlp_workspace_bytes(100, 100, 5, 5, 0, o) == 0
+
+
+def test_factor_argument_errors_without_device_work(lib):
+    """Invalid sizes, strides and null pointers return RQLP_ERR_ARG before
+    anything is enqueued (the fake pointers are never dereferenced)."""
+    fake = 0x1000
+    o = rqlp.rqlp_default_opts()
+    base = dict(A=fake, m=100, n=80, lda=80, k=10, p=5, q=1, Omega=fake, ldo=15, Q=fake, ldq=15,
+                L=fake, ldl=15, P=fake, ldp=15, workspace=fake, ws_bytes=1 << 30, d_info=fake,
+                d_diag=None, opts=o, stream=None)
+
+    def call(**kw):
+        a = dict(base)
+        a.update(kw)
+        return rqlp.rqlp_factor(**a)
+
+    assert call(lda=79) == 1          # lda < n
+    assert call(ldo=14) == 1          # ldo < d
+    assert call(A=None) == 1
+    assert call(d_info=None) == 1
+    assert call(k=0) == 1
+    assert call(k=78, p=5) == 1       # d > min(m, n)
+    assert call(ws_bytes=10) == 6     # workspace too small
+    assert call(workspace=fake + 8) == 6   # misaligned

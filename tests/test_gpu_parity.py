@@ -1,0 +1,105 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
+the same seeded inputs, element by element where the factors are unique."""
+import numpy as np
+import pytest
+
+from oracle import rqlp_oracle as orc
+from paper_2110_01011_gb300 import inputs
+from parity_util import compare, relres, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def _cfg1():
+    m = n = 1000
+    A = inputs.low_rank_matrix(m, n, inputs.step_spectrum(n, 20, 0.1), 1e-3, seed=1001)
+    Om = inputs.omega(m, 25, seed=2001)
+    return A, Om
+
+
+def test_config1_fp32():
+    """1000 x 1000, sigma = 1 (i <= 20) then 0.1^(i-20), noise 1e-3; k=20, p=5, q=1."""
+    A, Om = _cfg1()
+    err = compare(A, Om, 20, 5, 1, run_gpu(A, Om, 20, 5, 1))
+    print("config1 fp32", {k: float(v) for k, v in err.items()})
+
+
+@pytest.mark.parametrize("m,n,k,p,q", [
+    (257, 131, 10, 3, 0), (257, 131, 10, 3, 2), (131, 257, 10, 3, 1),   # ragged tails, m < n
+    (1500, 700, 40, 9, 1), (700, 1500, 48, 16, 1),                     # several big tiles
+    (64, 64, 64, 0, 0), (300, 200, 1, 0, 3), (2049, 1025, 60, 4, 2),
+])
+def test_shapes(m, n, k, p, q):
+    sig = inputs.exp_spectrum(min(m, n), rate=max(4.0, (k + p) / 3))
+    A = inputs.low_rank_matrix(m, n, sig, 1e-5, seed=m * 7 + n)
+    Om = inputs.omega(m, k + p, seed=m + 3 * n)
+    compare(A, Om, k, p, q, run_gpu(A, Om, k, p, q), elem_atol=5e-4)
+
+
+def test_poly_spectrum():
+    """Config-3 stress spectrum sigma_i = i^-1.5 on the 1000 x 1000 workload."""
+    m = n = 1000
+    A = inputs.low_rank_matrix(m, n, inputs.poly_spectrum(n, 1.5), 0.0, seed=1003)
+    Om = inputs.omega(m, 25, seed=2003)
+    compare(A, Om, 20, 5, 1, run_gpu(A, Om, 20, 5, 1))
+
+
+def test_small_fp64_option():
+    A, Om = _cfg1()
+    compare(A, Om, 20, 5, 1, run_gpu(A, Om, 20, 5, 1, small_fp64=True))
+
+
+def test_exact_low_rank_reconstruction():
+    """rank(A) = d: A = Q L P^T up to FP32 rounding (oracle: 1e-13)."""
+    m, n, r = 600, 400, 12
+    A = inputs.low_rank_matrix(m, n, np.linspace(2.0, 0.5, r), 0.0, seed=77)
+    Om = inputs.omega(m, r, seed=78)
+    Q, L, P, info, _ = run_gpu(A, Om, 10, 2, 1)
+    assert info[0] == 0
+    assert relres(A, Q, L, P) < 2e-6
+
+
+def test_rank_deficient_shift_path():
+    """rank(A) < d: the Gram is singular, the shifted Cholesky kicks in and
+    the leading factors still match the oracle's span."""
+    m, n, r = 500, 300, 6
+    A = inputs.low_rank_matrix(m, n, np.linspace(1.0, 0.5, r), 0.0, seed=81)
+    Om = inputs.omega(m, 10, seed=82)
+    Q, L, P, info, diag = run_gpu(A, Om, 8, 2, 0)
+    assert info[0] in (0, 3)
+    assert diag[3] >= 1            # at least one shifted Cholesky
+    ref = orc.rand_qlp(A.astype(np.float64), Om.astype(np.float64), 0)
+    # the leading r columns are unique; compare them and the reconstruction
+    assert np.max(np.abs(Q[:, :r] - ref.Q[:, :r])) < 1e-3
+    assert np.max(np.abs(np.diag(L)[:r] - np.diag(ref.L)[:r]) / np.diag(ref.L)[:r]) < 1e-3
+    assert np.all(np.isfinite(Q)) and np.all(np.isfinite(L)) and np.all(np.isfinite(P))
+
+
+def test_nonfinite_input_reported():
+    A, Om = _cfg1()
+    A = A.copy()
+    A[3, 7] = np.nan
+    _, _, _, info, _ = run_gpu(A, Om, 20, 5, 0)
+    assert info[0] == 4
+
+
+def test_host_buffer_form_matches_device_form():
+    import torch
+
+    from paper_2110_01011_gb300 import rqlp
+    A, Om = _cfg1()
+    Qd, Ld, Pd, info_d, _ = run_gpu(A, Om, 20, 5, 1)
+    Q, L, P, info, diag = rqlp.factor_host(torch.from_numpy(A).pin_memory(), 20, 5, 1,
+                                           torch.from_numpy(Om).pin_memory())
+    assert int(info[0]) == 0
+    assert np.array_equal(Q.numpy(), Qd.astype(np.float32))
+    assert np.array_equal(L.numpy(), Ld.astype(np.float32))
+    assert np.array_equal(P.numpy(), Pd.astype(np.float32))
+
+
+def test_deterministic():
+    A, Om = _cfg1()
+    a = run_gpu(A, Om, 20, 5, 1)
+    b = run_gpu(A, Om, 20, 5, 1)
+    for x, y in zip(a[:3], b[:3]):
+        assert np.array_equal(x, y)
