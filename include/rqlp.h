@@ -126,6 +126,37 @@ rqlp_status rqlp_factor_host(const float* hA, int64_t m, int64_t n, int64_t lda,
                              int* h_info, double* h_diag,
                              const rqlp_opts* opts, void* stream);
 
+/* ---- Factorisation without any allocation (the paper has no counterpart;
+ * this serves callers of the library, not the method).
+ *
+ * Some callers cannot allocate device memory: code inside a framework or host
+ * application whose own pool owns every byte of device memory, code with a
+ * fixed device-memory budget, and code on paths where the implicit device
+ * synchronisation of cudaMalloc is not acceptable. rqlp_factor_noalloc is
+ * rqlp_factor without the workspace argument: its scratch is one array of
+ * RQLP_NOALLOC_SCRATCH_BYTES bytes in device memory that belongs to the
+ * library (every GPU that loads the library holds it until the process
+ * exits). It calls no cudaMalloc, cudaFree or allocating library routine.
+ *  - Problems with rqlp_workspace_bytes(...) > RQLP_NOALLOC_SCRATCH_BYTES
+ *    return RQLP_ERR_WORKSPACE and enqueue nothing (16 MiB covers, e.g.,
+ *    4096 x 4096 with d = 69 and q = 1).
+ *  - All calls on a device share the array, which keeps the last call's
+ *    contents; each call clears what must start at zero in its first kernel.
+ *    Calls whose GPU work overlaps (two streams without an ordering) race on
+ *    the array: order them on one stream or with events.
+ *  - The first call on a device looks up the array's device address while
+ *    that device is current; make that first call before any stream capture.
+ * Other arguments, outputs and errors are as for rqlp_factor. */
+#define RQLP_NOALLOC_SCRATCH_BYTES (16u << 20)
+rqlp_status rqlp_factor_noalloc(const float* A, int64_t m, int64_t n, int64_t lda,
+                                int k, int p, int q,
+                                const float* Omega, int64_t ldo,
+                                float* Q, int64_t ldq,
+                                float* L, int64_t ldl,
+                                float* P, int64_t ldp,
+                                int* d_info, double* d_diag,
+                                const rqlp_opts* opts, void* stream);
+
 /* ---- Step-level entry points (one step of the chain each; same conventions).
  *
  * rqlp_sketch: one pass over A (Algorithm 1 steps 3-4 and each power pass).

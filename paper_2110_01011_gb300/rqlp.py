@@ -29,7 +29,7 @@ STATUS = {0: "RQLP_OK", 1: "RQLP_ERR_ARG", 2: "RQLP_ERR_CUDA", 3: "RQLP_ERR_BREA
 
 # Every symbol include/rqlp.h declares (checked by the ABI test).
 EXPORTED = ["rqlp_default_opts", "rqlp_workspace_bytes", "rqlp_factor", "rqlp_host_workspace_bytes",
-            "rqlp_factor_host", "rqlp_sketch_workspace_bytes", "rqlp_sketch",
+            "rqlp_factor_host", "rqlp_factor_noalloc", "rqlp_sketch_workspace_bytes", "rqlp_sketch",
             "rqlp_orth_workspace_bytes", "rqlp_orth", "rqlp_kernel_launches", "rqlp_profile_enable",
             "rqlp_profile_read", "rqlp_status_string", "rqlp_version"]
 
@@ -62,6 +62,9 @@ def _declare(lib):
     lib.rqlp_factor.restype = _int
     lib.rqlp_factor_host.argtypes = sig
     lib.rqlp_factor_host.restype = _int
+    lib.rqlp_factor_noalloc.argtypes = [_vp, _i64, _i64, _i64, _int, _int, _int, _vp, _i64, _vp, _i64,
+                                         _vp, _i64, _vp, _i64, _vp, _vp, ctypes.POINTER(Opts), _vp]
+    lib.rqlp_factor_noalloc.restype = _int
     lib.rqlp_sketch_workspace_bytes.argtypes = [_int, _i64, _i64, _int, ctypes.POINTER(Opts)]
     lib.rqlp_sketch_workspace_bytes.restype = _sz
     lib.rqlp_sketch.argtypes = [_int, _vp, _i64, _i64, _i64, _vp, _i64, _int, _vp, _i64, _vp, _sz,
@@ -135,6 +138,17 @@ def rqlp_factor_host(A, m, n, lda, k, p, q, Omega, ldo, Q, ldq, L, ldl, P, ldp, 
     return int(load().rqlp_factor_host(A, m, n, lda, k, p, q, Omega, ldo, Q, ldq, L, ldl, P, ldp,
                                        workspace, ws_bytes, h_info, h_diag,
                                        ctypes.byref(opts) if opts is not None else None, stream))
+
+
+def rqlp_factor_noalloc(A, m, n, lda, k, p, q, Omega, ldo, Q, ldq, L, ldl, P, ldp, d_info, d_diag,
+                        opts, stream):
+    """Raw call of the allocation-free factorisation (library-owned scratch)."""
+    return int(load().rqlp_factor_noalloc(A, m, n, lda, k, p, q, Omega, ldo, Q, ldq, L, ldl, P, ldp,
+                                          d_info, d_diag,
+                                          ctypes.byref(opts) if opts is not None else None, stream))
+
+
+NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
 def rqlp_sketch_workspace_bytes(trans, m, n, d, opts=None):
