@@ -54,7 +54,10 @@ class Ops {
   int64_t ld() const { return ld_; }
   cudaStream_t stream() const { return st_; }
 
-  cudaError_t init() { return init_scratch(info_, gates, kGates, scal, kScal, st_); }
+  cudaError_t init() {
+    tc_.reset();
+    return init_scratch(info_, gates, kGates, scal, kScal, st_);
+  }
 
   // transA: out (n x d) = A^T X (X m x d); else out (m x d) = A X (X n x d).
   cudaError_t pass(bool transA, const float* A, int64_t m, int64_t n, int64_t lda, const float* X,
@@ -63,7 +66,7 @@ class Ops {
     if (prof) profile_mark_begin(st_);
     cudaError_t e;
     if (o_.precision == RQLP_PREC_BF16X3) {
-      e = tc_.pass(transA, A, m, n, lda, X, ldx, d_, out, ldout, sumsq, st_);
+      e = tc_.pass(transA, A, m, n, lda, X, ldx, d_, out, ldout, sumsq, info_, st_);
     } else {
       const int64_t M = transA ? n : m, K = transA ? m : n;
       e = gemm_f32_ex(transA, M, d_, K, A, lda, X, ldx, out, ldout, gemm_f32_splits(M, d_, K), part_, sumsq,

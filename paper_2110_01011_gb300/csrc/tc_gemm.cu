@@ -1,16 +1,503 @@
-// Tensor-core passes over A (BF16 split precision). Not yet available: the
-// entry points report the option as unsupported.
+// Tensor-core passes over A in BF16 split precision (tcgen05 / TMEM / TMA).
+//
+// Each pass computes out = op(A) X with op(A) = A^T (Y = A^T X, the sketch
+// and the A^T-half of a power pass) or A (Z = A X, the projection). A and X
+// are split into BF16 high and low parts, A = A_hi + A_lo, X = X_hi + X_lo,
+// and the product is accumulated in FP32 in tensor memory as
+//     A_hi X_hi + A_hi X_lo + A_lo X_hi
+// (the dropped A_lo X_lo term is below 2^-16 relative). When X has no low
+// part (a BF16-exact Omega) the middle product is skipped.
+//
+// Data flow per factorisation: split_a_kernel writes A_hi, A_lo once (and
+// ||A||_F^2); prep_x_kernel writes X_hi^T, X_lo^T (d x K, K-major) before
+// every pass; tc_pass_kernel streams A tiles through shared memory with TMA
+// and issues tcgen05.mma from one thread; tc_fixup_kernel adds the partial
+// tiles of stream-K in a fixed order.
+//
+// tc_pass_kernel is persistent: one CTA per SM, the (tile, k-block) units of
+// the whole pass split evenly over the CTAs (stream-K), so the 157 M-tiles of
+// a 20000-row pass load all 152 SMs equally. Warp roles: warps 0-3 drain the
+// accumulator from TMEM (each warp its 32 lanes), warp 4 issues TMA loads,
+// warp 5 allocates TMEM and issues the MMAs. Two accumulator buffers let the
+// next segment's MMAs run while the epilogue drains the previous one. Every
+// wait is bounded; a timeout is reported in the status word and the kernel
+// drains what it started and frees its TMEM before returning.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <mutex>
+
 #include "tc_gemm.cuh"
+#include "tc_ptx.cuh"
 
 namespace rqlp {
+namespace {
 
-bool tc_supported(const float*, int64_t, const float*, int64_t) { return false; }
+using bf16 = __nv_bfloat16;
 
-void TcEngine::layout(Arena&, int64_t, int64_t, int) {}
+constexpr int BM = 128;              // MMA M: output rows per tile (TMEM lanes)
+constexpr int BK = 32;               // K per pipeline stage (64 bytes of BF16)
+constexpr int kThreads = 192;        // 6 warps
+constexpr int kMaxStages = 8;
+constexpr long long kWaitLimit = 4000000000LL;   // cycles (~2 s) before a wait gives up
+constexpr uint32_t kABytes = BM * BK * 2;        // one BF16 A tile (8 KB)
 
-cudaError_t TcEngine::pass(bool, const float*, int64_t, int64_t, int64_t, const float*, int64_t, int, float*,
-                           int64_t, double*, cudaStream_t) {
-  return cudaErrorNotSupported;
+struct TcArgs {
+  int M, K, d, npad, kblocks, tiles, G, stages;
+  long long units;
+  float* out;
+  long long ldo;
+  float* part;               // 2 * G slots of BM x npad floats
+  const int* xlo_nonzero;    // 1 when X has a nonzero low part
+  int* info;                 // status word (may be null)
+  uint32_t idesc, stage_bytes, tmem_cols;
+};
+
+__host__ __device__ inline long long unit_begin(int c, long long units, int G) {
+  return (long long)c * units / G;
+}
+// The CTA whose unit range holds unit u (empty ranges never match).
+__host__ __device__ inline int unit_owner(long long u, long long units, int G) {
+  return (int)(((u + 1) * G + units - 1) / units) - 1;
+}
+
+__device__ void post_timeout(int* info) {
+  if (info != nullptr && atomicCAS(info, 0, RQLP_ERR_TIMEOUT) == 0) info[1] = 0;
+}
+
+template <bool MN_A>
+__global__ void __launch_bounds__(kThreads, 1)
+tc_pass_kernel(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUtensorMap tmAlo,
+               const __grid_constant__ CUtensorMap tmXhi, const __grid_constant__ CUtensorMap tmXlo,
+               const TcArgs a) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int S = a.stages;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)S * a.stage_bytes);
+  uint64_t* empty = full + S;
+  uint64_t* accf = empty + S;
+  uint64_t* acce = accf + 2;
+  uint64_t* done = acce + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int cta = blockIdx.x;
+  const long long u0 = unit_begin(cta, a.units, a.G), u1 = unit_begin(cta + 1, a.units, a.G);
+  if (u0 >= u1) return;   // no work for this CTA (uniform)
+  const int KB = a.kblocks;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&accf[b], 1);
+      tc::mbar_init(&acce[b], 4 * 32);
+    }
+    tc::mbar_init(done, 1);
+    tc::fence_barrier_init();
+  }
+  if (warp == 5) {
+    tc::tmem_alloc(tmem_slot, a.tmem_cols);
+    tc::tmem_relinquish();
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  const int products = (*a.xlo_nonzero) ? 3 : 2;
+  const uint32_t xbytes = (uint32_t)a.npad * BK * 2;
+
+  if (warp == 4 && lane == 0) {
+    // ------------------------------------------------ TMA producer
+    tc::prefetch_tmap(&tmAhi);
+    tc::prefetch_tmap(&tmAlo);
+    tc::prefetch_tmap(&tmXhi);
+    tc::prefetch_tmap(&tmXlo);
+    long long issued = 0;
+    bool ok = true;
+    for (long long u = u0; u < u1; ++u, ++issued) {
+      const int stage = (int)(issued % S);
+      const uint32_t par = (uint32_t)((issued / S) & 1);
+      if (!tc::mbar_wait(&empty[stage], par ^ 1u, kWaitLimit)) { ok = false; break; }
+      const int t = (int)(u / KB), kb = (int)(u % KB);
+      unsigned char* base = smem + (size_t)stage * a.stage_bytes;
+      tc::mbar_expect_tx(&full[stage], 2 * kABytes + (products == 3 ? 2u : 1u) * xbytes);
+      if (MN_A) {
+        tc::tma_load_2d(base, &tmAhi, &full[stage], t * BM, kb * BK);
+        tc::tma_load_2d(base + kABytes / 2, &tmAhi, &full[stage], t * BM + 64, kb * BK);
+        tc::tma_load_2d(base + kABytes, &tmAlo, &full[stage], t * BM, kb * BK);
+        tc::tma_load_2d(base + kABytes + kABytes / 2, &tmAlo, &full[stage], t * BM + 64, kb * BK);
+      } else {
+        tc::tma_load_2d(base, &tmAhi, &full[stage], kb * BK, t * BM);
+        tc::tma_load_2d(base + kABytes, &tmAlo, &full[stage], kb * BK, t * BM);
+      }
+      tc::tma_load_2d(base + 2 * kABytes, &tmXhi, &full[stage], kb * BK, 0);
+      if (products == 3) tc::tma_load_2d(base + 2 * kABytes + xbytes, &tmXlo, &full[stage], kb * BK, 0);
+    }
+    if (!ok) post_timeout(a.info);
+    // Drain: every load this thread started has landed before the CTA exits.
+    for (long long i = issued > S ? issued - S : 0; i < issued; ++i)
+      if (!tc::mbar_wait(&full[i % S], (uint32_t)((i / S) & 1), kWaitLimit)) post_timeout(a.info);
+  } else if (warp == 5 && lane == 0) {
+    // ------------------------------------------------ MMA issuer
+    long long consumed = 0;
+    int seg = 0;
+    bool ok = true;
+    long long u = u0;
+    while (u < u1 && ok) {
+      const int t = (int)(u / KB);
+      const long long seg_begin = u, seg_end = std::min(u1, (long long)(t + 1) * KB);
+      const int ab = seg & 1;
+      if (!tc::mbar_wait(&acce[ab], (uint32_t)(((seg >> 1) & 1) ^ 1), kWaitLimit)) { ok = false; break; }
+      tc::tc_fence_after();
+      const uint32_t d_tmem = tmem_base + (uint32_t)(ab * a.npad);
+      for (; u < seg_end; ++u, ++consumed) {
+        const int stage = (int)(consumed % S);
+        if (!tc::mbar_wait(&full[stage], (uint32_t)((consumed / S) & 1), kWaitLimit)) { ok = false; break; }
+        tc::tc_fence_after();
+        const uint32_t base = tc::smem_u32(smem + (size_t)stage * a.stage_bytes);
+        const uint32_t ahi = base, alo = base + kABytes, xhi = base + 2 * kABytes, xlo = xhi + xbytes;
+#pragma unroll
+        for (int ks = 0; ks < BK / 16; ++ks) {
+          uint64_t dah, dal;
+          if (MN_A) {   // MN-major, 128B swizzle: 16 k-rows = two 1024-byte atoms
+            dah = tc::smem_desc(ahi + ks * 2048, kABytes / 2, 1024, tc::kSwizzle128);
+            dal = tc::smem_desc(alo + ks * 2048, kABytes / 2, 1024, tc::kSwizzle128);
+          } else {      // K-major, 64B swizzle: 16 k-columns = 32 bytes into the row
+            dah = tc::smem_desc(ahi + ks * 32, 16, 512, tc::kSwizzle64);
+            dal = tc::smem_desc(alo + ks * 32, 16, 512, tc::kSwizzle64);
+          }
+          const uint64_t dxh = tc::smem_desc(xhi + ks * 32, 16, 512, tc::kSwizzle64);
+          const uint64_t dxl = tc::smem_desc(xlo + ks * 32, 16, 512, tc::kSwizzle64);
+          const uint32_t acc = (u > seg_begin || ks > 0) ? 1u : 0u;
+          tc::mma_bf16(d_tmem, dah, dxh, a.idesc, acc);
+          if (products == 3) tc::mma_bf16(d_tmem, dah, dxl, a.idesc, 1u);
+          tc::mma_bf16(d_tmem, dal, dxh, a.idesc, 1u);
+        }
+        tc::mma_commit(&empty[stage]);
+      }
+      if (!ok) break;
+      tc::mma_commit(&accf[ab]);
+      ++seg;
+    }
+    if (!ok) post_timeout(a.info);
+    tc::mma_commit(done);   // no MMA in flight at teardown
+    if (!tc::mbar_wait(done, 0, kWaitLimit)) post_timeout(a.info);
+  } else if (warp < 4) {
+    // ------------------------------------------------ epilogue: TMEM -> global
+    const int row = warp * 32 + lane;
+    int seg = 0;
+    long long u = u0;
+    while (u < u1) {
+      const int t = (int)(u / KB);
+      const long long seg_begin = u, seg_end = std::min(u1, (long long)(t + 1) * KB);
+      const bool whole = seg_begin == (long long)t * KB && seg_end == (long long)(t + 1) * KB;
+      const int ab = seg & 1;
+      int ok = 1;
+      if (lane == 0) ok = tc::mbar_wait(&accf[ab], (uint32_t)((seg >> 1) & 1), kWaitLimit) ? 1 : 0;
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) {
+        if (lane == 0) post_timeout(a.info);
+        break;
+      }
+      tc::tc_fence_after();
+      const uint32_t taddr = tmem_base + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ab * a.npad);
+      const long long gm = (long long)t * BM + row;
+      float* dst;
+      int ncols;
+      if (whole) {
+        dst = a.out + gm * a.ldo;
+        ncols = gm < a.M ? a.d : 0;
+      } else {
+        const int slot = seg == 0 ? 2 * cta : 2 * cta + 1;
+        dst = a.part + ((long long)slot * BM + row) * a.npad;
+        ncols = a.npad;
+      }
+      for (int c0 = 0; c0 < a.npad; c0 += 16) {
+        float v[16];
+        tc::tmem_ld16(taddr + (uint32_t)c0, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+          if (c0 + i < ncols) dst[c0 + i] = v[i];
+      }
+      tc::tc_fence_before();
+      tc::mbar_arrive(&acce[ab]);
+      u = seg_end;
+      ++seg;
+    }
+  }
+
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  if (warp == 5) tc::tmem_dealloc(tmem_base, a.tmem_cols);
+}
+
+// Sum the stream-K partial tiles of every tile split across CTAs, in CTA order.
+__global__ void tc_fixup_kernel(const TcArgs a) {
+  const int t = blockIdx.x;
+  const long long ub = (long long)t * a.kblocks, ue = ub + a.kblocks;
+  const int clo = unit_owner(ub, a.units, a.G), chi = unit_owner(ue - 1, a.units, a.G);
+  if (clo == chi) return;   // one CTA held the whole tile and wrote it directly
+  for (int e = threadIdx.x; e < BM * a.d; e += blockDim.x) {
+    const int r = e / a.d, col = e % a.d;
+    const long long gm = (long long)t * BM + r;
+    if (gm >= a.M) continue;
+    float s = 0.f;
+    for (int c = clo; c <= chi; ++c) {
+      const long long cb = unit_begin(c, a.units, a.G);
+      if (cb == unit_begin(c + 1, a.units, a.G)) continue;
+      const int slot = (cb / a.kblocks == t) ? 2 * c : 2 * c + 1;
+      s += a.part[((long long)slot * BM + r) * a.npad + col];
+    }
+    a.out[gm * a.ldo + col] = s;
+  }
+}
+
+// A (m x n FP32) -> A_hi, A_lo (BF16, ld ldb, padding columns zero) and ||A||_F^2.
+__global__ void split_a_kernel(const float* __restrict__ A, long long m, long long n, long long lda, bool vec,
+                               bf16* __restrict__ hi, bf16* __restrict__ lo, long long ldb, double* sumsq) {
+  const long long cpr = ldb / 8, total = m * cpr;
+  float s = 0.f, comp = 0.f;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long r = idx / cpr, c0 = (idx % cpr) * 8;
+    const float* src = A + r * lda + c0;
+    float x[8];
+    if (vec && c0 + 8 <= n) {
+      const float4 p = *reinterpret_cast<const float4*>(src);
+      const float4 q = *reinterpret_cast<const float4*>(src + 4);
+      x[0] = p.x; x[1] = p.y; x[2] = p.z; x[3] = p.w; x[4] = q.x; x[5] = q.y; x[6] = q.z; x[7] = q.w;
+    } else {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) x[i] = (c0 + i < n) ? src[i] : 0.f;
+    }
+    __align__(16) bf16 h[8];
+    __align__(16) bf16 l[8];
+    float ss = 0.f;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      h[i] = __float2bfloat16_rn(x[i]);
+      l[i] = __float2bfloat16_rn(x[i] - __bfloat162float(h[i]));
+      ss = fmaf(x[i], x[i], ss);
+    }
+    *reinterpret_cast<uint4*>(hi + r * ldb + c0) = *reinterpret_cast<const uint4*>(h);
+    *reinterpret_cast<uint4*>(lo + r * ldb + c0) = *reinterpret_cast<const uint4*>(l);
+    const float y = ss - comp, tt = s + y;
+    comp = (tt - s) - y;
+    s = tt;
+  }
+  if (sumsq == nullptr) return;
+  __shared__ double red[32];
+  double v = (double)s - (double)comp;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    atomicAdd(sumsq, t);
+  }
+}
+
+// X (rows x d FP32) -> X_hi^T, X_lo^T (d x ldk BF16, K-major); flags a nonzero low part.
+__global__ void prep_x_kernel(const float* __restrict__ X, long long rows, int d, long long ldx,
+                              bf16* __restrict__ th, bf16* __restrict__ tl, long long ldk, int* nonzero_lo) {
+  __shared__ float tile[32][33];
+  const long long r0 = (long long)blockIdx.x * 32;
+  const int c0 = blockIdx.y * 32;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const long long r = r0 + i;
+    const int c = c0 + threadIdx.x;
+    tile[i][threadIdx.x] = (r < rows && c < d) ? X[r * ldx + c] : 0.f;
+  }
+  __syncthreads();
+  bool any = false;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int c = c0 + i;
+    const long long r = r0 + threadIdx.x;
+    if (c < d && r < ldk) {
+      const float x = tile[threadIdx.x][i];
+      const bf16 h = __float2bfloat16_rn(x);
+      const bf16 l = __float2bfloat16_rn(x - __bfloat162float(h));
+      th[(long long)c * ldk + r] = h;
+      tl[(long long)c * ldk + r] = l;
+      any |= __bfloat162float(l) != 0.f;
+    }
+  }
+  if (__any_sync(0xffffffffu, any) && threadIdx.x == 0) atomicOr(nonzero_lo, 1);
+}
+
+// ---------------------------------------------------------------- host side
+using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeFn encode_fn() {
+  static EncodeFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeFn>(p);
+  });
+  return fn;
+}
+
+// 2-D BF16 tensor map: dims {inner, outer}, row pitch in elements, box {bi, bo}.
+bool make_map(CUtensorMap* map, const void* base, long long inner, long long outer, long long pitch, int bi,
+              int bo, CUtensorMapSwizzle sw) {
+  EncodeFn fn = encode_fn();
+  if (fn == nullptr) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
+  cuuint64_t strides[1] = {(cuuint64_t)(pitch * 2)};
+  cuuint32_t box[2] = {(cuuint32_t)bi, (cuuint32_t)bo};
+  cuuint32_t es[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int npad_of(int d) { return (int)round_up(std::max(d, 16), 16); }
+uint32_t tmem_cols_of(int npad) {
+  uint32_t need = 2u * (uint32_t)npad, c = 32;
+  while (c < need) c <<= 1;
+  return c;
+}
+uint32_t stage_bytes_of(int npad) { return 2 * kABytes + 2u * (uint32_t)npad * BK * 2; }
+
+size_t smem_optin_tc() {
+  static size_t v = 0;
+  if (v == 0) {
+    int dev = 0, x = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&x, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess && x > 0)
+      v = (size_t)x;
+    else
+      v = 227 * 1024;
+  }
+  return v;
+}
+
+int stages_of(int npad) {
+  const size_t avail = smem_optin_tc() - 1024 - 256;
+  int s = (int)(avail / stage_bytes_of(npad));
+  return std::max(2, std::min(kMaxStages, s));
+}
+
+template <bool MN_A>
+cudaError_t launch_pass(const CUtensorMap& ah, const CUtensorMap& al, const CUtensorMap& xh,
+                        const CUtensorMap& xl, const TcArgs& a, cudaStream_t st) {
+  const size_t smem = (size_t)a.stages * a.stage_bytes + 1024 + 256;
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(tc_pass_kernel<MN_A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(smem_optin_tc()));
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  tc_pass_kernel<MN_A><<<a.G, kThreads, smem, st>>>(ah, al, xh, xl, a);
+  note_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool tc_supported(const float* A, int64_t lda, const float* Omega, int64_t ldo) {
+  (void)A; (void)lda; (void)Omega; (void)ldo;
+  int dev = 0, major = 0, minor = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess)
+    return false;
+  return major == 10 && minor == 3 && encode_fn() != nullptr;
+}
+
+void TcEngine::layout(Arena& ar, int64_t m, int64_t n, int d) {
+  m_ = m;
+  n_ = n;
+  d_ = d;
+  npad_ = npad_of(d);
+  ldb_ = round_up(n, 8);
+  ldk_ = round_up(std::max(m, n), 8);
+  G_ = sm_count();
+  Ahi_ = ar.take<uint16_t>((size_t)(m * ldb_));
+  Alo_ = ar.take<uint16_t>((size_t)(m * ldb_));
+  Xhi_ = ar.take<uint16_t>((size_t)d * ldk_);
+  Xlo_ = ar.take<uint16_t>((size_t)d * ldk_);
+  part_ = ar.take<float>((size_t)2 * G_ * BM * npad_);
+  flag_ = ar.take<int>(4);
+}
+
+cudaError_t TcEngine::pass(bool transA, const float* A, int64_t m, int64_t n, int64_t lda, const float* X,
+                           int64_t ldx, int d, float* out, int64_t ldout, double* sumsq, int* info,
+                           cudaStream_t st) {
+  if (m != m_ || n != n_ || d != d_) return cudaErrorInvalidValue;
+  cudaError_t e;
+  if (split_of_ != A) {
+    const bool vec = (reinterpret_cast<uintptr_t>(A) % 16 == 0) && (lda % 4 == 0);
+    const long long total = m * (ldb_ / 8);
+    const int blocks = (int)std::min<long long>(cdiv(total, 256), (long long)G_ * 8);
+    split_a_kernel<<<blocks, 256, 0, st>>>(A, m, n, lda, vec, reinterpret_cast<bf16*>(Ahi_),
+                                           reinterpret_cast<bf16*>(Alo_), ldb_, sumsq);
+    note_launch();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    split_of_ = A;
+    sumsq = nullptr;
+  }
+  if (sumsq != nullptr) return cudaErrorInvalidValue;   // ||A||^2 comes with the split only
+  const long long K = transA ? m : n, M = transA ? n : m;
+  if ((e = cudaMemsetAsync(flag_, 0, sizeof(int), st)) != cudaSuccess) return e;
+  {
+    dim3 grid((unsigned)cdiv(round_up(K, 8), 32), (unsigned)cdiv(d, 32));
+    prep_x_kernel<<<grid, dim3(32, 8), 0, st>>>(X, K, d, ldx, reinterpret_cast<bf16*>(Xhi_),
+                                                 reinterpret_cast<bf16*>(Xlo_), round_up(K, 8), flag_);
+    note_launch();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  CUtensorMap ah, al, xh, xl;
+  const long long ldk = round_up(K, 8);
+  bool ok;
+  if (transA) {   // op(A) = A^T: MN-major tiles, box 64 (j) x 32 (i), 128B swizzle
+    ok = make_map(&ah, Ahi_, n, m, ldb_, 64, BK, CU_TENSOR_MAP_SWIZZLE_128B) &&
+         make_map(&al, Alo_, n, m, ldb_, 64, BK, CU_TENSOR_MAP_SWIZZLE_128B);
+  } else {        // op(A) = A: K-major tiles, box 32 (j) x 128 (i), 64B swizzle
+    ok = make_map(&ah, Ahi_, n, m, ldb_, BK, BM, CU_TENSOR_MAP_SWIZZLE_64B) &&
+         make_map(&al, Alo_, n, m, ldb_, BK, BM, CU_TENSOR_MAP_SWIZZLE_64B);
+  }
+  ok = ok && make_map(&xh, Xhi_, K, d, ldk, BK, npad_, CU_TENSOR_MAP_SWIZZLE_64B) &&
+       make_map(&xl, Xlo_, K, d, ldk, BK, npad_, CU_TENSOR_MAP_SWIZZLE_64B);
+  if (!ok) return cudaErrorInvalidValue;
+
+  TcArgs a;
+  a.M = (int)M;
+  a.K = (int)K;
+  a.d = d;
+  a.npad = npad_;
+  a.kblocks = (int)cdiv(K, BK);
+  a.tiles = (int)cdiv(M, BM);
+  a.units = (long long)a.tiles * a.kblocks;
+  a.G = (int)std::min<long long>(G_, a.units);
+  a.stages = stages_of(npad_);
+  a.out = out;
+  a.ldo = ldout;
+  a.part = part_;
+  a.xlo_nonzero = flag_;
+  a.info = info;
+  a.idesc = tc::idesc_bf16(BM, npad_, transA, false);
+  a.stage_bytes = stage_bytes_of(npad_);
+  a.tmem_cols = tmem_cols_of(npad_);
+  e = transA ? launch_pass<true>(ah, al, xh, xl, a, st) : launch_pass<false>(ah, al, xh, xl, a, st);
+  if (e != cudaSuccess) return e;
+  tc_fixup_kernel<<<a.tiles, 256, 0, st>>>(a);
+  note_launch();
+  return cudaGetLastError();
 }
 
 }  // namespace rqlp

@@ -17,7 +17,7 @@ workloads of this library):
 
 Haar-distributed orthonormal factors are the Q factor of a Gaussian matrix
 with the column signs fixed by sign(diag(R)) (Mezzadri 2007); that QR is a
-LAPACK call (numpy) or cuSOLVER call (torch), never this library's code.
+LAPACK call (numpy), never this library's code.
 """
 from __future__ import annotations
 
@@ -61,8 +61,18 @@ def omega(m: int, d: int, seed: int, bf16_exact: bool = False) -> np.ndarray:
 
 
 def haar_columns(n: int, r: int, g: np.random.Generator) -> np.ndarray:
-    """n x r matrix with Haar-distributed orthonormal columns (FP64)."""
+    """n x r matrix with Haar-distributed orthonormal columns (FP64).
+
+    The Q factor (positive-diagonal R) of an n x r Gaussian. Large tall draws
+    (n >= 4 r, n r >= 4e6) are well conditioned (kappa <= ~3), so Q comes from
+    the Cholesky factor of G^T G (LAPACK potrf + trsm) instead of a slower
+    Householder QR; both give the same Q up to rounding.
+    """
     G = g.standard_normal((n, r))
+    if n >= 4 * r and n * r >= 4_000_000:
+        import scipy.linalg as sla
+        Rc = np.linalg.cholesky(G.T @ G).T
+        return sla.solve_triangular(Rc, G.T, trans="T", lower=False).T
     Qh, Rh = np.linalg.qr(G)
     s = np.sign(np.diag(Rh))
     s[s == 0] = 1.0
@@ -131,30 +141,27 @@ def low_rank_matrix(m: int, n: int, sigma: np.ndarray, noise: float, seed: int,
 
 def low_rank_matrix_torch(m: int, n: int, sigma: np.ndarray, noise: float, seed: int,
                           rank: int, device="cuda"):
-    """Same family as ``low_rank_matrix`` built on a device with torch (FP32 out).
+    """Same family as ``low_rank_matrix`` assembled on a device (FP32 out).
 
-    For the 20000 x 20000 class the host build is too slow; U_r, V_r come from
-    cuSOLVER QR of FP64 torch Gaussians, A from one FP32 matmul (TF32 disabled).
-    The result is a different draw than the host builder for the same seed.
+    For the 20000 x 20000 class the host product is too slow: U_r and V_r are
+    drawn on the host (Philox, LAPACK QR) and the product U_r diag(sigma) V_r^T
+    is one FP32 matmul on the device (TF32 disabled); the Gaussian noise is
+    drawn by torch's seeded device generator.
     """
     import torch
-    gen = torch.Generator(device=device)
-    gen.manual_seed(int(seed))
+    g = rng(seed)
+    U = haar_columns(m, rank, g) * np.asarray(sigma[:rank], dtype=np.float64)
+    V = haar_columns(n, rank, g)
     prev = torch.backends.cuda.matmul.allow_tf32
     torch.backends.cuda.matmul.allow_tf32 = False
     try:
-        def haar(rows):
-            G = torch.randn(rows, rank, generator=gen, device=device, dtype=torch.float64)
-            Qh, Rh = torch.linalg.qr(G)
-            s = torch.sign(torch.diagonal(Rh))
-            s[s == 0] = 1.0
-            return Qh * s
-        sg = torch.as_tensor(np.asarray(sigma[:rank], dtype=np.float64), device=device)
-        U = (haar(m) * sg).to(torch.float32)
-        V = haar(n).to(torch.float32)
-        A = U @ V.T
-        del U, V
+        Ud = torch.from_numpy(U.astype(np.float32)).to(device)
+        Vd = torch.from_numpy(V.astype(np.float32)).to(device)
+        A = Ud @ Vd.T
+        del Ud, Vd
         if noise:
+            gen = torch.Generator(device=device)
+            gen.manual_seed(int(seed))
             A.add_(torch.randn(m, n, generator=gen, device=device, dtype=torch.float32),
                    alpha=noise / math.sqrt(n))
         return A.contiguous()

@@ -31,7 +31,13 @@ def relres(A, Q, L, P):
     return np.linalg.norm(A - (Q @ L) @ P.T) / np.linalg.norm(A)
 
 
-def compare(A, Om, k, p, q, gpu, elem_atol=2e-4):
+# Absolute floor for the relative residual when the oracle's is at rounding
+# level (rank(A) <= d): a few units of the pass arithmetic's roundoff
+# (FP32 6e-8; BF16x3 keeps ~16 bits per operand, ~1.5e-5).
+RES_FLOOR = {0: 1e-6, 1: 2e-5}
+
+
+def compare(A, Om, k, p, q, gpu, elem_atol=2e-4, precision=0):
     """Compare GPU factors with the oracle; returns a dict of measured errors
     and asserts the tolerances."""
     Qg, Lg, Pg, info, diag = gpu
@@ -57,7 +63,7 @@ def compare(A, Om, k, p, q, gpu, elem_atol=2e-4):
     assert err["orthQ"] <= TOL_ORTH, err
     assert err["orthP"] <= TOL_ORTH, err
     assert err["Lii_rel"] <= TOL_LII, err
-    assert err["res_rel"] <= TOL_RES or abs(rg - ro) <= 1e-6, err
+    assert err["res_rel"] <= TOL_RES or abs(rg - ro) <= RES_FLOOR[precision], err
     assert err["Q_lead"] <= elem_atol and err["P_lead"] <= elem_atol, err
     assert err["L_lead"] <= elem_atol, err
     assert err["diag_A2_rel"] <= 1e-6, err

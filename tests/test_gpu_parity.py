@@ -17,11 +17,12 @@ def _cfg1():
     return A, Om
 
 
-def test_config1_fp32():
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp32", "bf16x3"])
+def test_config1(prec):
     """1000 x 1000, sigma = 1 (i <= 20) then 0.1^(i-20), noise 1e-3; k=20, p=5, q=1."""
     A, Om = _cfg1()
-    err = compare(A, Om, 20, 5, 1, run_gpu(A, Om, 20, 5, 1))
-    print("config1 fp32", {k: float(v) for k, v in err.items()})
+    err = compare(A, Om, 20, 5, 1, run_gpu(A, Om, 20, 5, 1, precision=prec), precision=prec)
+    print("config1", ["fp32", "bf16x3"][prec], {k: float(v) for k, v in err.items()})
 
 
 @pytest.mark.parametrize("m,n,k,p,q", [
@@ -29,19 +30,22 @@ def test_config1_fp32():
     (1500, 700, 40, 9, 1), (700, 1500, 48, 16, 1),                     # several big tiles
     (64, 64, 64, 0, 0), (300, 200, 1, 0, 3), (2049, 1025, 60, 4, 2),
 ])
-def test_shapes(m, n, k, p, q):
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp32", "bf16x3"])
+def test_shapes(m, n, k, p, q, prec):
     sig = inputs.exp_spectrum(min(m, n), rate=max(4.0, (k + p) / 3))
     A = inputs.low_rank_matrix(m, n, sig, 1e-5, seed=m * 7 + n)
     Om = inputs.omega(m, k + p, seed=m + 3 * n)
-    compare(A, Om, k, p, q, run_gpu(A, Om, k, p, q), elem_atol=5e-4)
+    compare(A, Om, k, p, q, run_gpu(A, Om, k, p, q, precision=prec), elem_atol=5e-4, precision=prec)
 
 
-def test_poly_spectrum():
-    """Config-3 stress spectrum sigma_i = i^-1.5 on the 1000 x 1000 workload."""
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp32", "bf16x3"])
+def test_poly_spectrum(prec):
+    """Stress spectrum sigma_i = i^-1.5 on the 1000 x 1000 workload (split form too)."""
     m = n = 1000
     A = inputs.low_rank_matrix(m, n, inputs.poly_spectrum(n, 1.5), 0.0, seed=1003)
     Om = inputs.omega(m, 25, seed=2003)
-    compare(A, Om, 20, 5, 1, run_gpu(A, Om, 20, 5, 1))
+    err = compare(A, Om, 20, 5, 1, run_gpu(A, Om, 20, 5, 1, precision=prec), precision=prec)
+    print("poly", ["fp32", "bf16x3"][prec], {k: float(v) for k, v in err.items()})
 
 
 def test_small_fp64_option():
