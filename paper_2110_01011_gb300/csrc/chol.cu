@@ -1,0 +1,382 @@
+// Cholesky factor and inverse of the d x d Gram matrix of CholeskyQR, in one
+// CTA: G = L L^T (R = L^T, upper, positive diagonal) and W = L^{-1}
+// (R^{-1} = W^T).
+//
+// Blocked right-looking elimination on the augmented matrix [G | I] with
+// 16-column panels:
+//   (1) one warp factors the 16 x 16 diagonal block (row per lane, shuffles)
+//       and inverts it (column per lane): L_JJ, D = L_JJ^{-1};
+//   (2) panel L_IJ = G_IJ D^T for the rows below, and the block row of W:
+//       W_J,: = D X_J,: (X = the eliminated identity, W_JJ = D);
+//   (3) trailing updates G_II -= L_IJ L_IJ^T (lower part) and
+//       X_I,: -= L_IJ W_J,: for the rows below.
+// Step (3) runs as warp tasks of 8 x 128 outputs with the panel operands in
+// transposed shared-memory buffers (row values broadcast, column values one
+// vector per lane). L lives in the lower triangle of one square buffer and
+// W^T in its strict upper triangle (W's diagonal in a side array).
+//
+// A pivot that is not clearly positive restarts the elimination on G + s I
+// (shifted CholeskyQR, Fukaya et al. 2020) and raises the caller's gate flag;
+// a second breakdown reports RQLP_ERR_BREAKDOWN and writes identities.
+#include <algorithm>
+#include <cmath>
+
+#include "common.cuh"
+
+namespace rqlp {
+namespace {
+
+constexpr int NB = 16;
+constexpr int kMaxD = RQLP_MAX_D;
+constexpr int kThreads = 512;
+
+template <typename T> struct Vec4;
+template <> struct Vec4<float> { using type = float4; };
+template <> struct Vec4<double> { using type = double4_32a; };
+
+template <typename T>
+__device__ __forceinline__ void ld4(const T* p, T* v) {
+  const typename Vec4<T>::type q = *reinterpret_cast<const typename Vec4<T>::type*>(p);
+  v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+template <typename T>
+__device__ __forceinline__ void st4(T* p, const T* v) {
+  typename Vec4<T>::type q;
+  q.x = v[0]; q.y = v[1]; q.z = v[2]; q.w = v[3];
+  *reinterpret_cast<typename Vec4<T>::type*>(p) = q;
+}
+
+template <typename T> struct Eps;
+template <> struct Eps<float> { static constexpr float u = 5.9604645e-8f; };
+template <> struct Eps<double> { static constexpr double u = 1.1102230246251565e-16; };
+
+// Row pitch of the square buffer: a multiple of 4 elements (16-byte rows) and
+// 4 banks off a multiple of 32, so consecutive rows start in different banks.
+__host__ __device__ inline int lds_of(int d) { return (int)round_up(d, 32) + 4; }
+__host__ __device__ inline int ptld_of(int d) { return (int)round_up(d, 8); }
+
+__device__ void post_error(int* info, int code, int detail) {
+  if (info != nullptr && atomicCAS(info, 0, code) == 0) info[1] = detail;
+}
+
+__device__ void write_identity(int d, float* R, float* Rinv, int64_t ldr) {
+  for (int e = threadIdx.x; e < d * d; e += blockDim.x) {
+    const int i = e / d, l = e % d;
+    const float v = i == l ? 1.f : 0.f;
+    R[i * ldr + l] = v;
+    Rinv[i * ldr + l] = v;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+chol_blocked_kernel(int d, const float* __restrict__ G, int64_t ldg, float* __restrict__ R, float* __restrict__ Rinv,
+                    int64_t ldr, int* info, double* shift_count, int* gate_out, const int* gate_in, T* gS) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int LDS = lds_of(d), PTLD = ptld_of(d);
+  T* dyn = reinterpret_cast<T*>(smem_raw);
+  T* S = gS != nullptr ? gS : dyn;
+  T* PT = gS != nullptr ? dyn : dyn + (size_t)d * LDS;
+  T* WT = PT + NB * PTLD;
+  __shared__ T gdiag[kMaxD], wdiag[kMaxD];
+  __shared__ T Lb[NB][NB + 1], Dinv[NB][NB + 1], rdiag[NB];
+  __shared__ T s_red[32];
+  __shared__ int s_fail;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+
+  if (gate_in != nullptr && *gate_in == 0) {   // pass not needed: R = R^{-1} = I
+    write_identity(d, R, Rinv, ldr);
+    return;
+  }
+
+  T tr = 0;
+  for (int i = tid; i < d; i += blockDim.x) tr += (T)G[(int64_t)i * ldg + i];
+  for (int o = 16; o > 0; o >>= 1) tr += __shfl_down_sync(0xffffffffu, tr, o);
+  if (lane == 0) s_red[warp] = tr;
+  __syncthreads();
+  T trace = 0;
+  for (int w = 0; w < nwarps; ++w) trace += s_red[w];
+  if (!isfinite(trace)) {
+    if (tid == 0) post_error(info, RQLP_ERR_NONFINITE, 0);
+    write_identity(d, R, Rinv, ldr);
+    return;
+  }
+  const T shift = (T)(100.0 * d) * Eps<T>::u * trace;
+  const T rel_tol = (T)64 * Eps<T>::u;
+
+  int fail = -1;
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    const T sh = attempt == 0 ? (T)0 : shift;
+    for (int e = tid; e < d * d; e += blockDim.x) {
+      const int i = e / d, j = e % d;
+      T v = 0;
+      if (j <= i) v = (T)G[(int64_t)i * ldg + j] + (i == j ? sh : (T)0);
+      S[(size_t)i * LDS + j] = v;
+    }
+    for (int i = tid; i < d; i += blockDim.x) gdiag[i] = (T)G[(int64_t)i * ldg + i] + sh;
+    __syncthreads();
+    fail = -1;
+    for (int j0 = 0; j0 < d; j0 += NB) {
+      const int jb = min(NB, d - j0);
+      // (1) diagonal block: Cholesky (lane = row) and inverse (lane = column).
+      if (warp == 0) {
+        T a[NB];
+#pragma unroll
+        for (int k = 0; k < NB; ++k) a[k] = (lane < jb && k <= lane) ? S[(size_t)(j0 + lane) * LDS + j0 + k] : (T)0;
+        int f = -1;
+#pragma unroll
+        for (int k = 0; k < NB; ++k) {
+          if (k < jb && f < 0) {
+            const T piv = __shfl_sync(0xffffffffu, a[k], k);
+            if (!(piv > rel_tol * gdiag[j0 + k]) || !isfinite(piv)) {
+              f = j0 + k;
+            } else {
+              const T lkk = sqrt(piv), rl = (T)1 / lkk;
+              if (lane == k) a[k] = lkk;
+              else if (lane > k) a[k] *= rl;
+              const T lik = a[k];
+#pragma unroll
+              for (int j = k + 1; j < NB; ++j) {
+                const T ljk = __shfl_sync(0xffffffffu, lik, j);
+                if (j < jb && lane >= j) a[j] -= lik * ljk;
+              }
+            }
+          }
+        }
+        if (f < 0) {
+#pragma unroll
+          for (int k = 0; k < NB; ++k) {
+            if (lane < jb && k <= lane) {
+              Lb[lane][k] = a[k];
+              S[(size_t)(j0 + lane) * LDS + j0 + k] = a[k];
+            }
+            if (lane == k && k < jb) rdiag[k] = (T)1 / a[k];
+          }
+          __syncwarp();
+          const int c = lane;
+          T x[NB];
+#pragma unroll
+          for (int i = 0; i < NB; ++i) {
+            T v = 0;
+            if (c < jb && i < jb) {
+              if (i == c) {
+                v = rdiag[c];
+              } else if (i > c) {
+                T s = 0;
+#pragma unroll
+                for (int t = 0; t < NB; ++t)
+                  if (t >= c && t < i) s += Lb[i][t] * x[t];
+                v = -s * rdiag[i];
+              }
+            }
+            x[i] = v;
+          }
+#pragma unroll
+          for (int i = 0; i < NB; ++i)
+            if (c < jb && i < jb) Dinv[i][c] = x[i];
+        }
+        if (lane == 0) s_fail = f;
+      }
+      __syncthreads();
+      if (s_fail >= 0) {
+        fail = s_fail;
+        break;
+      }
+      const int jn = j0 + jb, Nt = d - jn;
+      // (2) panel rows below the block, block row of W, and W's diagonal block.
+      for (int idx = tid; idx < Nt + jn; idx += blockDim.x) {
+        if (idx < Nt) {
+          const int i = jn + idx;
+          T v[NB], o[NB];
+#pragma unroll
+          for (int k = 0; k < NB; k += 4) ld4(&S[(size_t)i * LDS + j0 + k], &v[k]);
+#pragma unroll
+          for (int c = 0; c < NB; ++c) {
+            T s2 = 0;
+#pragma unroll
+            for (int k = 0; k <= c; ++k) s2 += v[k] * Dinv[c][k];
+            o[c] = s2;
+            PT[c * PTLD + i] = s2;
+          }
+#pragma unroll
+          for (int k = 0; k < NB; k += 4) st4(&S[(size_t)i * LDS + j0 + k], &o[k]);
+        } else {
+          const int c = idx - Nt;
+          if (c < j0) {
+            T w[NB];
+            if (jb == NB) {
+#pragma unroll
+              for (int k = 0; k < NB; k += 4) ld4(&S[(size_t)c * LDS + j0 + k], &w[k]);
+            } else {
+#pragma unroll
+              for (int k = 0; k < NB; ++k) w[k] = k < jb ? S[(size_t)c * LDS + j0 + k] : (T)0;
+            }
+#pragma unroll
+            for (int r = 0; r < NB; ++r) {
+              if (r < jb) {
+                T s2 = 0;
+#pragma unroll
+                for (int k = 0; k <= r; ++k) s2 += Dinv[r][k] * w[k];
+                S[(size_t)c * LDS + j0 + r] = s2;
+                WT[r * PTLD + c] = s2;
+              }
+            }
+          } else {
+            const int cc = c - j0;
+            wdiag[c] = Dinv[cc][cc];
+#pragma unroll
+            for (int r = 0; r < NB; ++r) {
+              if (r < jb) {
+                const T wv = r >= cc ? Dinv[r][cc] : (T)0;
+                if (r > cc) S[(size_t)c * LDS + j0 + r] = wv;
+                WT[r * PTLD + c] = wv;
+              }
+            }
+          }
+        }
+      }
+      __syncthreads();
+      // (3) trailing updates as 8 x 128 warp tasks.
+      if (Nt > 0) {
+        const int ra = (Nt + 7) / 8, rb = (jn + 7) / 8, nc = (Nt + 127) / 128;
+        const int tasks = (ra + rb) * nc;
+        for (int task = warp; task < tasks; task += nwarps) {
+          const int strip = task / nc, cs = task % nc;
+          const bool lower = strip < ra;
+          const int r0 = lower ? jn + strip * 8 : (strip - ra) * 8;
+          const int rlim = lower ? d : jn;
+          if (lower && jn + cs * 128 > r0 + 7) continue;   // strip above the diagonal
+          const int c0 = jn + cs * 128 + 4 * lane;
+          const T* Ar = lower ? PT : WT;
+          T acc[8][4];
+#pragma unroll
+          for (int rr = 0; rr < 8; ++rr)
+#pragma unroll
+            for (int cc = 0; cc < 4; ++cc) acc[rr][cc] = 0;
+          const bool cvalid = c0 < d;   // c0 + 4 <= PTLD whenever c0 < d
+#pragma unroll
+          for (int k = 0; k < NB; ++k) {
+            T av[8], bv[4];
+            ld4(&Ar[k * PTLD + r0], &av[0]);
+            ld4(&Ar[k * PTLD + r0 + 4], &av[4]);
+#pragma unroll
+            for (int rr = 0; rr < 8; ++rr)
+              if (r0 + rr >= rlim) av[rr] = 0;
+            if (cvalid) {
+              ld4(&PT[k * PTLD + c0], bv);
+#pragma unroll
+              for (int cc = 0; cc < 4; ++cc)
+                if (c0 + cc >= d) bv[cc] = 0;
+            } else {
+              bv[0] = bv[1] = bv[2] = bv[3] = 0;
+            }
+#pragma unroll
+            for (int rr = 0; rr < 8; ++rr)
+#pragma unroll
+              for (int cc = 0; cc < 4; ++cc) acc[rr][cc] += av[rr] * bv[cc];
+          }
+          if (cvalid) {
+#pragma unroll
+            for (int rr = 0; rr < 8; ++rr) {
+              const int r = r0 + rr;
+              if (r >= rlim) continue;
+              T* dst = &S[(size_t)r * LDS + c0];
+              if (c0 + 3 < d && (!lower || c0 + 3 <= r)) {
+                T cur[4];
+                ld4(dst, cur);
+#pragma unroll
+                for (int cc = 0; cc < 4; ++cc) cur[cc] -= acc[rr][cc];
+                st4(dst, cur);
+              } else {
+#pragma unroll
+                for (int cc = 0; cc < 4; ++cc) {
+                  const int col = c0 + cc;
+                  if (col < d && (!lower || col <= r)) dst[cc] -= acc[rr][cc];
+                }
+              }
+            }
+          }
+        }
+      }
+      __syncthreads();
+    }
+    if (fail < 0) break;
+    __syncthreads();
+    if (attempt == 0 && tid == 0) {
+      if (gate_out != nullptr) *gate_out = 1;
+      if (shift_count != nullptr) atomicAdd(shift_count, 1.0);
+    }
+  }
+
+  if (fail >= 0) {
+    if (tid == 0) post_error(info, RQLP_ERR_BREAKDOWN, fail + 1);
+    write_identity(d, R, Rinv, ldr);
+    return;
+  }
+  // R = L^T (upper); R^{-1} = W^T: strict upper part from S, diagonal from wdiag.
+  for (int e = tid; e < d * d; e += blockDim.x) {
+    const int i = e / d, l = e % d;
+    R[i * ldr + l] = l >= i ? (float)S[(size_t)l * LDS + i] : 0.f;
+    Rinv[i * ldr + l] = l > i ? (float)S[(size_t)i * LDS + l] : (l == i ? (float)wdiag[i] : 0.f);
+  }
+}
+
+size_t smem_optin_chol() {
+  static size_t v = 0;
+  if (v == 0) {
+    int dev = 0, x = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&x, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess && x > 0)
+      v = (size_t)x;
+    else
+      v = 227 * 1024;
+  }
+  return v;
+}
+
+template <typename T>
+size_t square_bytes(int d) { return (size_t)d * lds_of(d) * sizeof(T); }
+template <typename T>
+size_t panel_bytes(int d) { return (size_t)2 * NB * ptld_of(d) * sizeof(T); }
+template <typename T>
+size_t static_bytes() { return (2 * kMaxD + 2 * NB * (NB + 1) + NB + 32) * sizeof(T) + 64; }
+template <typename T>
+bool square_in_smem(int d) {
+  return square_bytes<T>(d) + panel_bytes<T>(d) + static_bytes<T>() <= smem_optin_chol();
+}
+
+template <typename T>
+cudaError_t launch(int d, const float* G, int64_t ldg, float* R, float* Rinv, int64_t ldr, int* info,
+                   double* shift_count, int* gate_out, const int* gate_in, void* gstore, cudaStream_t st) {
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(chol_blocked_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(smem_optin_chol() - static_bytes<T>()));
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  const bool in_smem = square_in_smem<T>(d);
+  if (!in_smem && gstore == nullptr) return cudaErrorInvalidValue;
+  const size_t dyn = panel_bytes<T>(d) + (in_smem ? square_bytes<T>(d) : 0);
+  chol_blocked_kernel<T><<<1, kThreads, dyn, st>>>(d, G, ldg, R, Rinv, ldr, info, shift_count, gate_out, gate_in,
+                                                    in_smem ? nullptr : reinterpret_cast<T*>(gstore));
+  note_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t chol_global_bytes(int d, bool fp64) {
+  if (fp64) return square_in_smem<double>(d) ? 0 : square_bytes<double>(d);
+  return square_in_smem<float>(d) ? 0 : square_bytes<float>(d);
+}
+
+cudaError_t chol_inv(int d, const float* G, int64_t ldg, float* R, float* Rinv, int64_t ldr, int* info,
+                     double* shift_count, int* gate_out, const int* gate_in, void* gstore, bool fp64,
+                     cudaStream_t st) {
+  if (fp64) return launch<double>(d, G, ldg, R, Rinv, ldr, info, shift_count, gate_out, gate_in, gstore, st);
+  return launch<float>(d, G, ldg, R, Rinv, ldr, info, shift_count, gate_out, gate_in, gstore, st);
+}
+
+}  // namespace rqlp

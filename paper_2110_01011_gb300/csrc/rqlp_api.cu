@@ -52,7 +52,6 @@ class Ops {
   }
   void bind(cudaStream_t st, int* info) { st_ = st; info_ = info; }
   int64_t ld() const { return ld_; }
-  cudaStream_t stream() const { return st_; }
 
   cudaError_t init() {
     tc_.reset();

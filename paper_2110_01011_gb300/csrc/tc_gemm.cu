@@ -11,8 +11,10 @@
 // Data flow per factorisation: split_a_kernel writes A_hi, A_lo once (and
 // ||A||_F^2); prep_x_kernel writes X_hi^T, X_lo^T (d x K, K-major) before
 // every pass; tc_pass_kernel streams A tiles through shared memory with TMA
-// and issues tcgen05.mma from one thread; tc_fixup_kernel adds the partial
-// tiles of stream-K in a fixed order.
+// and issues tcgen05.mma from one thread. A tile whose K range is split over
+// several CTAs (stream-K) is finished by the CTA that arrives last on the
+// tile's counter: it adds the published partial tiles in CTA order
+// (deterministic) and resets the counter; no CTA ever waits for another.
 //
 // tc_pass_kernel is persistent: one CTA per SM, the (tile, k-block) units of
 // the whole pass split evenly over the CTAs (stream-K), so the 157 M-tiles of
@@ -42,6 +44,7 @@ constexpr int kThreads = 192;        // 6 warps
 constexpr int kMaxStages = 8;
 constexpr long long kWaitLimit = 4000000000LL;   // cycles (~2 s) before a wait gives up
 constexpr uint32_t kABytes = BM * BK * 2;        // one BF16 A tile (8 KB)
+constexpr int kMaxSlots = 16;                    // partial tiles summed from a cached slot list
 
 struct TcArgs {
   int M, K, d, npad, kblocks, tiles, G, stages;
@@ -49,6 +52,7 @@ struct TcArgs {
   float* out;
   long long ldo;
   float* part;               // 2 * G slots of BM x npad floats
+  int* tile_cnt;             // per-tile arrival counters (zero between passes)
   const int* xlo_nonzero;    // 1 when X has a nonzero low part
   int* info;                 // status word (may be null)
   uint32_t idesc, stage_bytes, tmem_cols;
@@ -81,6 +85,11 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant_
   uint64_t* acce = accf + 2;
   uint64_t* done = acce + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  int* last_flag = reinterpret_cast<int*>(tmem_slot + 1);
+  int* last_lo = last_flag + 1;
+  int* epi_ok = last_lo + 2;
+  int* nslots = epi_ok + 1;
+  int* slots = nslots + 1;   // kMaxSlots entries
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int cta = blockIdx.x;
@@ -197,11 +206,11 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant_
       const long long seg_begin = u, seg_end = std::min(u1, (long long)(t + 1) * KB);
       const bool whole = seg_begin == (long long)t * KB && seg_end == (long long)(t + 1) * KB;
       const int ab = seg & 1;
-      int ok = 1;
-      if (lane == 0) ok = tc::mbar_wait(&accf[ab], (uint32_t)((seg >> 1) & 1), kWaitLimit) ? 1 : 0;
-      ok = __shfl_sync(0xffffffffu, ok, 0);
-      if (!ok) {
-        if (lane == 0) post_timeout(a.info);
+      // One thread waits; the verdict is shared so the four warps stay in step.
+      if (threadIdx.x == 0) *epi_ok = tc::mbar_wait(&accf[ab], (uint32_t)((seg >> 1) & 1), kWaitLimit) ? 1 : 0;
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      if (*epi_ok == 0) {
+        if (threadIdx.x == 0) post_timeout(a.info);
         break;
       }
       tc::tc_fence_after();
@@ -226,6 +235,70 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant_
       }
       tc::tc_fence_before();
       tc::mbar_arrive(&acce[ab]);
+      if (!whole) {
+        // Publish the partial tile; the last CTA to arrive on the tile sums them.
+        __threadfence();
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+        if (threadIdx.x == 0) {
+          // Slots of this tile's contributors in CTA order (the fixed summation order).
+          const long long ub = (long long)t * KB, ue = ub + KB;
+          const int clo = unit_owner(ub, a.units, a.G), chi = unit_owner(ue - 1, a.units, a.G);
+          int n = 0;
+          for (int c = clo; c <= chi; ++c) {
+            const long long cb = unit_begin(c, a.units, a.G);
+            if (cb == unit_begin(c + 1, a.units, a.G)) continue;
+            if (n < kMaxSlots) slots[n] = (cb / KB == t) ? 2 * c : 2 * c + 1;
+            ++n;
+          }
+          const int old = atomicAdd(&a.tile_cnt[t], 1);
+          *last_flag = (old == n - 1) ? 1 : 0;
+          *nslots = n;
+          last_lo[0] = clo;
+          last_lo[1] = chi;
+        }
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+        if (*last_flag) {
+          __threadfence();
+          if (gm < a.M) {
+            float* o = a.out + gm * a.ldo;
+            const int n = *nslots;
+            for (int c0 = 0; c0 < a.d; c0 += 16) {
+              float acc[16];
+#pragma unroll
+              for (int i = 0; i < 16; ++i) acc[i] = 0.f;
+              if (n <= kMaxSlots) {
+                for (int s2 = 0; s2 < n; ++s2) {
+                  const float4* src =
+                      reinterpret_cast<const float4*>(a.part + ((long long)slots[s2] * BM + row) * a.npad + c0);
+#pragma unroll
+                  for (int q = 0; q < 4; ++q) {
+                    const float4 v = __ldcg(src + q);
+                    acc[4 * q] += v.x; acc[4 * q + 1] += v.y; acc[4 * q + 2] += v.z; acc[4 * q + 3] += v.w;
+                  }
+                }
+              } else {   // many contributors (tiny problems): recompute the slots
+                for (int c = last_lo[0]; c <= last_lo[1]; ++c) {
+                  const long long cb = unit_begin(c, a.units, a.G);
+                  if (cb == unit_begin(c + 1, a.units, a.G)) continue;
+                  const int slot = (cb / KB == t) ? 2 * c : 2 * c + 1;
+                  const float4* src =
+                      reinterpret_cast<const float4*>(a.part + ((long long)slot * BM + row) * a.npad + c0);
+#pragma unroll
+                  for (int q = 0; q < 4; ++q) {
+                    const float4 v = __ldcg(src + q);
+                    acc[4 * q] += v.x; acc[4 * q + 1] += v.y; acc[4 * q + 2] += v.z; acc[4 * q + 3] += v.w;
+                  }
+                }
+              }
+#pragma unroll
+              for (int i = 0; i < 16; ++i)
+                if (c0 + i < a.d) o[c0 + i] = acc[i];
+            }
+          }
+          if (threadIdx.x == 0) a.tile_cnt[t] = 0;
+        }
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+      }
       u = seg_end;
       ++seg;
     }
@@ -235,27 +308,6 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant_
   __syncthreads();
   tc::tc_fence_after();
   if (warp == 5) tc::tmem_dealloc(tmem_base, a.tmem_cols);
-}
-
-// Sum the stream-K partial tiles of every tile split across CTAs, in CTA order.
-__global__ void tc_fixup_kernel(const TcArgs a) {
-  const int t = blockIdx.x;
-  const long long ub = (long long)t * a.kblocks, ue = ub + a.kblocks;
-  const int clo = unit_owner(ub, a.units, a.G), chi = unit_owner(ue - 1, a.units, a.G);
-  if (clo == chi) return;   // one CTA held the whole tile and wrote it directly
-  for (int e = threadIdx.x; e < BM * a.d; e += blockDim.x) {
-    const int r = e / a.d, col = e % a.d;
-    const long long gm = (long long)t * BM + r;
-    if (gm >= a.M) continue;
-    float s = 0.f;
-    for (int c = clo; c <= chi; ++c) {
-      const long long cb = unit_begin(c, a.units, a.G);
-      if (cb == unit_begin(c + 1, a.units, a.G)) continue;
-      const int slot = (cb / a.kblocks == t) ? 2 * c : 2 * c + 1;
-      s += a.part[((long long)slot * BM + r) * a.npad + col];
-    }
-    a.out[gm * a.ldo + col] = s;
-  }
 }
 
 // A (m x n FP32) -> A_hi, A_lo (BF16, ld ldb, padding columns zero) and ||A||_F^2.
@@ -343,7 +395,8 @@ EncodeFn encode_fn() {
   std::call_once(once, [] {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
       fn = reinterpret_cast<EncodeFn>(p);
   });
@@ -386,7 +439,7 @@ size_t smem_optin_tc() {
 }
 
 int stages_of(int npad) {
-  const size_t avail = smem_optin_tc() - 1024 - 256;
+  const size_t avail = smem_optin_tc() - 1024 - 512;
   int s = (int)(avail / stage_bytes_of(npad));
   return std::max(2, std::min(kMaxStages, s));
 }
@@ -394,7 +447,7 @@ int stages_of(int npad) {
 template <bool MN_A>
 cudaError_t launch_pass(const CUtensorMap& ah, const CUtensorMap& al, const CUtensorMap& xh,
                         const CUtensorMap& xl, const TcArgs& a, cudaStream_t st) {
-  const size_t smem = (size_t)a.stages * a.stage_bytes + 1024 + 256;
+  const size_t smem = (size_t)a.stages * a.stage_bytes + 1024 + 512;
   static bool configured = false;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(tc_pass_kernel<MN_A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -433,6 +486,7 @@ void TcEngine::layout(Arena& ar, int64_t m, int64_t n, int d) {
   Xlo_ = ar.take<uint16_t>((size_t)d * ldk_);
   part_ = ar.take<float>((size_t)2 * G_ * BM * npad_);
   flag_ = ar.take<int>(4);
+  cnt_ = ar.take<int>((size_t)cdiv(std::max(m, n), BM));
 }
 
 cudaError_t TcEngine::pass(bool transA, const float* A, int64_t m, int64_t n, int64_t lda, const float* X,
@@ -450,6 +504,8 @@ cudaError_t TcEngine::pass(bool transA, const float* A, int64_t m, int64_t n, in
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     split_of_ = A;
     sumsq = nullptr;
+    // Tile counters start at zero; each pass's last arrivals reset them.
+    if ((e = cudaMemsetAsync(cnt_, 0, sizeof(int) * cdiv(std::max(m, n), BM), st)) != cudaSuccess) return e;
   }
   if (sumsq != nullptr) return cudaErrorInvalidValue;   // ||A||^2 comes with the split only
   const long long K = transA ? m : n, M = transA ? n : m;
@@ -488,16 +544,13 @@ cudaError_t TcEngine::pass(bool transA, const float* A, int64_t m, int64_t n, in
   a.out = out;
   a.ldo = ldout;
   a.part = part_;
+  a.tile_cnt = cnt_;
   a.xlo_nonzero = flag_;
   a.info = info;
   a.idesc = tc::idesc_bf16(BM, npad_, transA, false);
   a.stage_bytes = stage_bytes_of(npad_);
   a.tmem_cols = tmem_cols_of(npad_);
-  e = transA ? launch_pass<true>(ah, al, xh, xl, a, st) : launch_pass<false>(ah, al, xh, xl, a, st);
-  if (e != cudaSuccess) return e;
-  tc_fixup_kernel<<<a.tiles, 256, 0, st>>>(a);
-  note_launch();
-  return cudaGetLastError();
+  return transA ? launch_pass<true>(ah, al, xh, xl, a, st) : launch_pass<false>(ah, al, xh, xl, a, st);
 }
 
 }  // namespace rqlp

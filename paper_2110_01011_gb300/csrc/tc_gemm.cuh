@@ -27,6 +27,7 @@ class TcEngine {
   uint16_t *Ahi_ = nullptr, *Alo_ = nullptr, *Xhi_ = nullptr, *Xlo_ = nullptr;
   float* part_ = nullptr;
   int* flag_ = nullptr;
+  int* cnt_ = nullptr;
   const float* split_of_ = nullptr;
 };
 
