@@ -10,9 +10,9 @@
 //       W_J,: = D X_J,: (X = the eliminated identity, W_JJ = D);
 //   (3) trailing updates G_II -= L_IJ L_IJ^T (lower part) and
 //       X_I,: -= L_IJ W_J,: for the rows below.
-// Step (3) runs as warp tasks of 8 x 128 outputs with the panel operands in
-// transposed shared-memory buffers (row values broadcast, column values one
-// vector per lane). L lives in the lower triangle of one square buffer and
+// Step (3) runs as warp tasks of 16 x 64 outputs with the panel operands in
+// transposed shared-memory buffers (row values broadcast, two column values
+// per lane). L lives in the lower triangle of one square buffer and
 // W^T in its strict upper triangle (W's diagonal in a side array).
 //
 // A pivot that is not clearly positive restarts the elimination on G + s I
@@ -53,7 +53,7 @@ template <> struct Eps<double> { static constexpr double u = 1.1102230246251565e
 // Row pitch of the square buffer: a multiple of 4 elements (16-byte rows) and
 // 4 banks off a multiple of 32, so consecutive rows start in different banks.
 __host__ __device__ inline int lds_of(int d) { return (int)round_up(d, 32) + 4; }
-__host__ __device__ inline int ptld_of(int d) { return (int)round_up(d, 8); }
+__host__ __device__ inline int ptld_of(int d) { return (int)round_up(d, 16); }
 
 __device__ void post_error(int* info, int code, int detail) {
   if (info != nullptr && atomicCAS(info, 0, code) == 0) info[1] = detail;
@@ -132,9 +132,11 @@ chol_blocked_kernel(int d, const float* __restrict__ G, int64_t ldg, float* __re
             if (!(piv > rel_tol * gdiag[j0 + k]) || !isfinite(piv)) {
               f = j0 + k;
             } else {
-              const T lkk = sqrt(piv), rl = (T)1 / lkk;
+              // One reciprocal square root gives both 1/L_kk and L_kk = piv / sqrt(piv).
+              const T rl = rsqrt(piv), lkk = piv * rl;
               if (lane == k) a[k] = lkk;
               else if (lane > k) a[k] *= rl;
+              if (lane == 0) rdiag[k] = rl;
               const T lik = a[k];
 #pragma unroll
               for (int j = k + 1; j < NB; ++j) {
@@ -151,7 +153,6 @@ chol_blocked_kernel(int d, const float* __restrict__ G, int64_t ldg, float* __re
               Lb[lane][k] = a[k];
               S[(size_t)(j0 + lane) * LDS + j0 + k] = a[k];
             }
-            if (lane == k && k < jb) rdiag[k] = (T)1 / a[k];
           }
           __syncwarp();
           const int c = lane;
@@ -163,11 +164,11 @@ chol_blocked_kernel(int d, const float* __restrict__ G, int64_t ldg, float* __re
               if (i == c) {
                 v = rdiag[c];
               } else if (i > c) {
-                T s = 0;
+                T s2 = 0;
 #pragma unroll
                 for (int t = 0; t < NB; ++t)
-                  if (t >= c && t < i) s += Lb[i][t] * x[t];
-                v = -s * rdiag[i];
+                  if (t >= c && t < i) s2 += Lb[i][t] * x[t];
+                v = -s2 * rdiag[i];
               }
             }
             x[i] = v;
@@ -237,65 +238,42 @@ chol_blocked_kernel(int d, const float* __restrict__ G, int64_t ldg, float* __re
         }
       }
       __syncthreads();
-      // (3) trailing updates as 8 x 128 warp tasks.
+      // (3) trailing updates as 16 x 64 warp tasks: each lane owns two columns
+      // (one PT value each), 16 row values are broadcast from PT / WT.
       if (Nt > 0) {
-        const int ra = (Nt + 7) / 8, rb = (jn + 7) / 8, nc = (Nt + 127) / 128;
+        const int ra = (Nt + 15) / 16, rb = (jn + 15) / 16, nc = (Nt + 63) / 64;
         const int tasks = (ra + rb) * nc;
         for (int task = warp; task < tasks; task += nwarps) {
           const int strip = task / nc, cs = task % nc;
           const bool lower = strip < ra;
-          const int r0 = lower ? jn + strip * 8 : (strip - ra) * 8;
+          const int r0 = lower ? jn + strip * 16 : (strip - ra) * 16;
           const int rlim = lower ? d : jn;
-          if (lower && jn + cs * 128 > r0 + 7) continue;   // strip above the diagonal
-          const int c0 = jn + cs * 128 + 4 * lane;
+          const int cbase = jn + cs * 64;
+          if (lower && cbase > r0 + 15) continue;   // tile above the diagonal
+          const int col0 = cbase + lane, col1 = col0 + 32;
           const T* Ar = lower ? PT : WT;
-          T acc[8][4];
+          T acc0[16], acc1[16];
 #pragma unroll
-          for (int rr = 0; rr < 8; ++rr)
-#pragma unroll
-            for (int cc = 0; cc < 4; ++cc) acc[rr][cc] = 0;
-          const bool cvalid = c0 < d;   // c0 + 4 <= PTLD whenever c0 < d
+          for (int rr = 0; rr < 16; ++rr) acc0[rr] = acc1[rr] = 0;
 #pragma unroll
           for (int k = 0; k < NB; ++k) {
-            T av[8], bv[4];
-            ld4(&Ar[k * PTLD + r0], &av[0]);
-            ld4(&Ar[k * PTLD + r0 + 4], &av[4]);
+            T av[16];
 #pragma unroll
-            for (int rr = 0; rr < 8; ++rr)
-              if (r0 + rr >= rlim) av[rr] = 0;
-            if (cvalid) {
-              ld4(&PT[k * PTLD + c0], bv);
+            for (int q = 0; q < 16; q += 4) ld4(&Ar[k * PTLD + r0 + q], &av[q]);
+            const T b0 = col0 < d ? PT[k * PTLD + col0] : (T)0;
+            const T b1 = col1 < d ? PT[k * PTLD + col1] : (T)0;
 #pragma unroll
-              for (int cc = 0; cc < 4; ++cc)
-                if (c0 + cc >= d) bv[cc] = 0;
-            } else {
-              bv[0] = bv[1] = bv[2] = bv[3] = 0;
+            for (int rr = 0; rr < 16; ++rr) {
+              acc0[rr] += av[rr] * b0;
+              acc1[rr] += av[rr] * b1;
             }
-#pragma unroll
-            for (int rr = 0; rr < 8; ++rr)
-#pragma unroll
-              for (int cc = 0; cc < 4; ++cc) acc[rr][cc] += av[rr] * bv[cc];
           }
-          if (cvalid) {
 #pragma unroll
-            for (int rr = 0; rr < 8; ++rr) {
-              const int r = r0 + rr;
-              if (r >= rlim) continue;
-              T* dst = &S[(size_t)r * LDS + c0];
-              if (c0 + 3 < d && (!lower || c0 + 3 <= r)) {
-                T cur[4];
-                ld4(dst, cur);
-#pragma unroll
-                for (int cc = 0; cc < 4; ++cc) cur[cc] -= acc[rr][cc];
-                st4(dst, cur);
-              } else {
-#pragma unroll
-                for (int cc = 0; cc < 4; ++cc) {
-                  const int col = c0 + cc;
-                  if (col < d && (!lower || col <= r)) dst[cc] -= acc[rr][cc];
-                }
-              }
-            }
+          for (int rr = 0; rr < 16; ++rr) {
+            const int r = r0 + rr;
+            if (r >= rlim) continue;
+            if (col0 < d && (!lower || col0 <= r)) S[(size_t)r * LDS + col0] -= acc0[rr];
+            if (col1 < d && (!lower || col1 <= r)) S[(size_t)r * LDS + col1] -= acc1[rr];
           }
         }
       }

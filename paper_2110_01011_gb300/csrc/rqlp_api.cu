@@ -48,13 +48,19 @@ class Ops {
     scal = ar.take<double>(kScal);
     gates = ar.take<int>(kGates);
     cstore_ = ar.take<char>(chol_global_bytes(d_, o_.small_fp64 != 0));
-    if (with_tc) tc_.layout(ar, m, n, d_);
+    if (with_tc) {
+      tc_.layout(ar, m, n, d_, std::max(m, n), false);
+      // Tall d-column operands of CholeskyQR: Gram and X R^{-1} on the tensor cores.
+      tcs_.layout(ar, std::max(m, n), d_, d_, d_, true);
+    }
+    tc_on_ = with_tc;
   }
   void bind(cudaStream_t st, int* info) { st_ = st; info_ = info; }
   int64_t ld() const { return ld_; }
 
   cudaError_t init() {
     tc_.reset();
+    tcs_.reset();
     return init_scratch(info_, gates, kGates, scal, kScal, st_);
   }
 
@@ -94,8 +100,19 @@ class Ops {
     return chol_inv(d_, G_, ld_, R_[slot], Ri_[slot], ld_, info_, &scal[2], gate_out, gate_in, cstore_,
                     o_.small_fp64 != 0, st_);
   }
+  // One CholeskyQR pass (shifted on breakdown) with the BF16x3 tensor-core
+  // Gram and product: out = X R^{-1}; gate_out raised if the Cholesky shifted.
+  cudaError_t tc_cqr(const float* X, int64_t ldx, int64_t rows, float* out, int64_t ldout, int slot,
+                     int* gate_out) {
+    tcs_.reset();
+    CK(tcs_.split(X, rows, d_, ldx, nullptr, st_));
+    CK(tcs_.gram(G_, ld_, info_, st_));
+    CK(chol(slot, gate_out, nullptr));
+    return tcs_.pass(false, X, rows, d_, ldx, Ri_[slot], ld_, d_, out, ldout, nullptr, info_, st_);
+  }
   // One CholeskyQR pass (shifted on breakdown): out = X R^{-1}.
   cudaError_t orth_inter(const float* X, int64_t ldx, int64_t rows, float* out, int64_t ldout) {
+    if (tc_on_ && rows > (int64_t)d_) return tc_cqr(X, ldx, rows, out, ldout, 0, nullptr);
     CK(gram(X, ldx, rows, nullptr));
     CK(chol(0, nullptr, nullptr));
     return trmm(X, ldx, rows, Ri_[0], out, ldout, nullptr);
@@ -106,9 +123,15 @@ class Ops {
   cudaError_t orth_final(float* X, int64_t ldx, int64_t rows, float* out, int64_t ldout, float* tmp,
                          float* Racc, int slot) {
     int* g = &gates[slot];
-    CK(gram(X, ldx, rows, nullptr));
-    CK(chol(0, g, nullptr));
-    CK(trmm(X, ldx, rows, Ri_[0], tmp, ld_, nullptr));
+    if (tc_on_ && rows > (int64_t)d_) {
+      // First pass on the tensor cores (it only has to leave X well conditioned);
+      // the second pass, which sets the orthogonality, stays in FP32.
+      CK(tc_cqr(X, ldx, rows, tmp, ld_, 0, g));
+    } else {
+      CK(gram(X, ldx, rows, nullptr));
+      CK(chol(0, g, nullptr));
+      CK(trmm(X, ldx, rows, Ri_[0], tmp, ld_, nullptr));
+    }
     CK(gram(tmp, ld_, rows, nullptr));
     CK(chol(1, g, nullptr));
     CK(trmm(tmp, ld_, rows, Ri_[1], X, ldx, nullptr));
@@ -135,7 +158,8 @@ class Ops {
   int* info_ = nullptr;
   float *G_ = nullptr, *R_[3] = {}, *Ri_[3] = {}, *Ra_ = nullptr, *part_ = nullptr;
   void* cstore_ = nullptr;
-  TcEngine tc_;
+  TcEngine tc_, tcs_;
+  bool tc_on_ = false;
 };
 
 struct Dims {

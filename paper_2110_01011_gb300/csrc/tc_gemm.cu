@@ -48,6 +48,8 @@ constexpr int kMaxSlots = 16;                    // partial tiles summed from a 
 
 struct TcArgs {
   int M, K, d, npad, kblocks, tiles, G, stages;
+  int tpc;                   // > 0: whole tiles per CTA (no split tiles); 0: stream-K
+  int vec_out;               // out rows are 16-byte aligned (float4 stores)
   long long units;
   float* out;
   long long ldo;
@@ -60,6 +62,13 @@ struct TcArgs {
 
 __host__ __device__ inline long long unit_begin(int c, long long units, int G) {
   return (long long)c * units / G;
+}
+// First unit of CTA c: stream-K (even split of all units) or, with tpc > 0,
+// whole tiles (tpc tiles of kblocks units each per CTA).
+__device__ inline long long cta_begin(const int c, const long long units, const int G, const int tpc,
+                                      const int tiles, const int kblocks) {
+  if (tpc > 0) return (long long)min(c * tpc, tiles) * kblocks;
+  return unit_begin(c, units, G);
 }
 // The CTA whose unit range holds unit u (empty ranges never match).
 __host__ __device__ inline int unit_owner(long long u, long long units, int G) {
@@ -93,7 +102,8 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant_
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int cta = blockIdx.x;
-  const long long u0 = unit_begin(cta, a.units, a.G), u1 = unit_begin(cta + 1, a.units, a.G);
+  const long long u0 = cta_begin(cta, a.units, a.G, a.tpc, a.tiles, a.kblocks);
+  const long long u1 = cta_begin(cta + 1, a.units, a.G, a.tpc, a.tiles, a.kblocks);
   if (u0 >= u1) return;   // no work for this CTA (uniform)
   const int KB = a.kblocks;
 
@@ -226,12 +236,19 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant_
         dst = a.part + ((long long)slot * BM + row) * a.npad;
         ncols = a.npad;
       }
+      const bool vec = whole ? (a.vec_out != 0) : true;   // partial slots are 64-byte aligned
       for (int c0 = 0; c0 < a.npad; c0 += 16) {
         float v[16];
         tc::tmem_ld16(taddr + (uint32_t)c0, v);
+        if (vec && c0 + 16 <= ncols) {
+          float4* d4 = reinterpret_cast<float4*>(dst + c0);
 #pragma unroll
-        for (int i = 0; i < 16; ++i)
-          if (c0 + i < ncols) dst[c0 + i] = v[i];
+          for (int q = 0; q < 4; ++q) d4[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        } else {
+#pragma unroll
+          for (int i = 0; i < 16; ++i)
+            if (c0 + i < ncols) dst[c0 + i] = v[i];
+        }
       }
       tc::tc_fence_before();
       tc::mbar_arrive(&acce[ab]);
@@ -310,6 +327,150 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant_
   if (warp == 5) tc::tmem_dealloc(tmem_base, a.tmem_cols);
 }
 
+// Gram matrix of a split tall matrix on the tensor cores: G = X^T X for
+// X = X_hi + X_lo (rows x cols, cols <= 256), products hi^T hi + hi^T lo +
+// lo^T hi in FP32. CTA c takes an even share of the rows; each stage holds
+// one 32-row chunk of X as 64-column MN-major boxes (128B swizzle), which
+// serves as the A operand (X^T, one or two 128-row tiles of G, one TMEM
+// accumulator each) and as the B operand (X, N = round16(cols)). Each CTA
+// writes its partial G to its own slot; tc_gram_reduce_kernel adds the slots
+// in CTA order.
+struct GramArgs {
+  int rows, cols, npad, kblocks, G, stages, mtiles, nbox;
+  float* part;               // G slots of (mtiles * 128) x npad floats
+  int* info;
+  uint32_t idesc, stage_bytes, tmem_cols;
+};
+
+__global__ void __launch_bounds__(kThreads, 1)
+tc_gram_kernel(const __grid_constant__ CUtensorMap tmHi, const __grid_constant__ CUtensorMap tmLo,
+               const GramArgs a) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int S = a.stages;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)S * a.stage_bytes);
+  uint64_t* empty = full + S;
+  uint64_t* accf = empty + S;
+  uint64_t* done = accf + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  int* epi_ok = reinterpret_cast<int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int cta = blockIdx.x;
+  const long long kb0 = unit_begin(cta, a.kblocks, a.G), kb1 = unit_begin(cta + 1, a.kblocks, a.G);
+  const uint32_t half = (uint32_t)a.nbox * 4096u;   // bytes of one (hi or lo) chunk
+
+  if (threadIdx.x == 0) {
+    for (int s2 = 0; s2 < S; ++s2) {
+      tc::mbar_init(&full[s2], 1);
+      tc::mbar_init(&empty[s2], 1);
+    }
+    tc::mbar_init(accf, 1);
+    tc::mbar_init(done, 1);
+    tc::fence_barrier_init();
+  }
+  if (warp == 5) {
+    tc::tmem_alloc(tmem_slot, a.tmem_cols);
+    tc::tmem_relinquish();
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 4 && lane == 0) {
+    tc::prefetch_tmap(&tmHi);
+    tc::prefetch_tmap(&tmLo);
+    long long issued = 0;
+    bool ok = true;
+    for (long long kb = kb0; kb < kb1; ++kb, ++issued) {
+      const int stage = (int)(issued % S);
+      if (!tc::mbar_wait(&empty[stage], (uint32_t)((issued / S) & 1) ^ 1u, kWaitLimit)) { ok = false; break; }
+      unsigned char* base = smem + (size_t)stage * a.stage_bytes;
+      tc::mbar_expect_tx(&full[stage], 2 * half);
+      for (int b = 0; b < a.nbox; ++b) {
+        tc::tma_load_2d(base + b * 4096, &tmHi, &full[stage], b * 64, (int)(kb * BK));
+        tc::tma_load_2d(base + half + b * 4096, &tmLo, &full[stage], b * 64, (int)(kb * BK));
+      }
+    }
+    if (!ok) post_timeout(a.info);
+    for (long long i = issued > S ? issued - S : 0; i < issued; ++i)
+      if (!tc::mbar_wait(&full[i % S], (uint32_t)((i / S) & 1), kWaitLimit)) post_timeout(a.info);
+  } else if (warp == 5 && lane == 0) {
+    long long consumed = 0;
+    bool ok = true;
+    for (long long kb = kb0; kb < kb1; ++kb, ++consumed) {
+      const int stage = (int)(consumed % S);
+      if (!tc::mbar_wait(&full[stage], (uint32_t)((consumed / S) & 1), kWaitLimit)) { ok = false; break; }
+      tc::tc_fence_after();
+      const uint32_t hi = tc::smem_u32(smem + (size_t)stage * a.stage_bytes), lo = hi + half;
+#pragma unroll
+      for (int ks = 0; ks < BK / 16; ++ks) {
+        const uint32_t koff = ks * 2048;
+        const uint64_t bh = tc::smem_desc(hi + koff, 4096, 1024, tc::kSwizzle128);
+        const uint64_t bl = tc::smem_desc(lo + koff, 4096, 1024, tc::kSwizzle128);
+        for (int mt = 0; mt < a.mtiles; ++mt) {
+          const uint64_t ah = tc::smem_desc(hi + mt * 8192 + koff, 4096, 1024, tc::kSwizzle128);
+          const uint64_t al = tc::smem_desc(lo + mt * 8192 + koff, 4096, 1024, tc::kSwizzle128);
+          const uint32_t d_tmem = tmem_base + (uint32_t)(mt * a.npad);
+          const uint32_t acc = (kb > kb0 || ks > 0) ? 1u : 0u;
+          tc::mma_bf16(d_tmem, ah, bh, a.idesc, acc);
+          tc::mma_bf16(d_tmem, ah, bl, a.idesc, 1u);
+          tc::mma_bf16(d_tmem, al, bh, a.idesc, 1u);
+        }
+      }
+      tc::mma_commit(&empty[stage]);
+    }
+    if (!ok) post_timeout(a.info);
+    tc::mma_commit(accf);
+    tc::mma_commit(done);
+    if (!tc::mbar_wait(done, 0, kWaitLimit)) post_timeout(a.info);
+  } else if (warp < 4) {
+    if (threadIdx.x == 0) *epi_ok = tc::mbar_wait(accf, 0, kWaitLimit) ? 1 : 0;
+    asm volatile("bar.sync 1, 128;" ::: "memory");
+    if (*epi_ok == 0) {
+      if (threadIdx.x == 0) post_timeout(a.info);
+    } else {
+      tc::tc_fence_after();
+      const int row = warp * 32 + lane;
+      for (int mt = 0; mt < a.mtiles; ++mt) {
+        const uint32_t taddr = tmem_base + ((uint32_t)(warp * 32) << 16) + (uint32_t)(mt * a.npad);
+        float* dst = a.part + ((long long)cta * a.mtiles * BM + mt * BM + row) * a.npad;
+        for (int c0 = 0; c0 < a.npad; c0 += 16) {
+          float v[16];
+          tc::tmem_ld16(taddr + (uint32_t)c0, v);
+          float4* d4 = reinterpret_cast<float4*>(dst + c0);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) d4[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        }
+      }
+    }
+  }
+
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  if (warp == 5) tc::tmem_dealloc(tmem_base, a.tmem_cols);
+}
+
+// G[i][j] = sum over CTA slots of part (fixed order, Kahan-compensated FP32).
+__global__ void tc_gram_reduce_kernel(const float* __restrict__ part, int G, int mtiles, int npad, int cols,
+                                      float* __restrict__ out, long long ldo) {
+  const long long slot = (long long)mtiles * BM * npad;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < cols * cols; e += gridDim.x * blockDim.x) {
+    const int i = e / cols, j = e % cols;
+    const float* p = part + (long long)i * npad + j;
+    float s = 0.f, c = 0.f;
+    for (int z = 0; z < G; ++z) {
+      const float y = __ldcg(p + z * slot) - c, t = s + y;
+      c = (t - s) - y;
+      s = t;
+    }
+    out[(long long)i * ldo + j] = s;
+  }
+}
+
 // A (m x n FP32) -> A_hi, A_lo (BF16, ld ldb, padding columns zero) and ||A||_F^2.
 __global__ void split_a_kernel(const float* __restrict__ A, long long m, long long n, long long lda, bool vec,
                                bf16* __restrict__ hi, bf16* __restrict__ lo, long long ldb, double* sumsq) {
@@ -381,7 +542,9 @@ __global__ void prep_x_kernel(const float* __restrict__ X, long long rows, int d
       any |= __bfloat162float(l) != 0.f;
     }
   }
-  if (__any_sync(0xffffffffu, any) && threadIdx.x == 0) atomicOr(nonzero_lo, 1);
+  // One vote per block, and none once another block has raised the flag.
+  if (__syncthreads_or(any) && threadIdx.x == 0 && threadIdx.y == 0 && *(volatile int*)nonzero_lo == 0)
+    atomicOr(nonzero_lo, 1);
 }
 
 // ---------------------------------------------------------------- host side
@@ -472,43 +635,60 @@ bool tc_supported(const float* A, int64_t lda, const float* Omega, int64_t ldo) 
   return major == 10 && minor == 3 && encode_fn() != nullptr;
 }
 
-void TcEngine::layout(Arena& ar, int64_t m, int64_t n, int d) {
-  m_ = m;
-  n_ = n;
-  d_ = d;
-  npad_ = npad_of(d);
-  ldb_ = round_up(n, 8);
-  ldk_ = round_up(std::max(m, n), 8);
+constexpr int kGramMaxCtas = 64;
+
+void TcEngine::layout(Arena& ar, int64_t rows_cap, int64_t cols_cap, int d_cap, int64_t k_cap, bool gram) {
+  rows_cap_ = rows_cap;
+  cols_cap_ = cols_cap;
+  d_cap_ = d_cap;
+  k_cap_ = k_cap;
+  ldb_ = round_up(cols_cap, 8);
   G_ = sm_count();
-  Ahi_ = ar.take<uint16_t>((size_t)(m * ldb_));
-  Alo_ = ar.take<uint16_t>((size_t)(m * ldb_));
-  Xhi_ = ar.take<uint16_t>((size_t)d * ldk_);
-  Xlo_ = ar.take<uint16_t>((size_t)d * ldk_);
-  part_ = ar.take<float>((size_t)2 * G_ * BM * npad_);
+  const int npad = npad_of(d_cap);
+  Ahi_ = ar.take<uint16_t>((size_t)(rows_cap * ldb_));
+  Alo_ = ar.take<uint16_t>((size_t)(rows_cap * ldb_));
+  Xhi_ = ar.take<uint16_t>((size_t)d_cap * round_up(k_cap, 8));
+  Xlo_ = ar.take<uint16_t>((size_t)d_cap * round_up(k_cap, 8));
+  part_ = ar.take<float>((size_t)2 * G_ * BM * npad);
   flag_ = ar.take<int>(4);
-  cnt_ = ar.take<int>((size_t)cdiv(std::max(m, n), BM));
+  cnt_ = ar.take<int>((size_t)cdiv(std::max(rows_cap, cols_cap), BM));
+  if (gram) {
+    const int gp = npad_of((int)cols_cap);
+    gpart_ = ar.take<float>((size_t)kGramMaxCtas * cdiv(cols_cap, BM) * BM * gp);
+  }
+}
+
+cudaError_t TcEngine::split(const float* A, int64_t rows, int64_t cols, int64_t lda, double* sumsq,
+                            cudaStream_t st) {
+  if (rows > rows_cap_ || cols > cols_cap_) return cudaErrorInvalidValue;
+  const bool vec = (reinterpret_cast<uintptr_t>(A) % 16 == 0) && (lda % 4 == 0);
+  const long long total = rows * (ldb_ / 8);
+  const int blocks = (int)std::min<long long>(cdiv(total, 256), (long long)G_ * 8);
+  split_a_kernel<<<blocks, 256, 0, st>>>(A, rows, cols, lda, vec, reinterpret_cast<bf16*>(Ahi_),
+                                         reinterpret_cast<bf16*>(Alo_), ldb_, sumsq);
+  note_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  split_of_ = A;
+  m_ = rows;
+  n_ = cols;
+  // Tile counters start at zero; each pass's last arrivals reset them.
+  return cudaMemsetAsync(cnt_, 0, sizeof(int) * cdiv(std::max(rows_cap_, cols_cap_), BM), st);
 }
 
 cudaError_t TcEngine::pass(bool transA, const float* A, int64_t m, int64_t n, int64_t lda, const float* X,
                            int64_t ldx, int d, float* out, int64_t ldout, double* sumsq, int* info,
                            cudaStream_t st) {
-  if (m != m_ || n != n_ || d != d_) return cudaErrorInvalidValue;
+  if (d > d_cap_) return cudaErrorInvalidValue;
   cudaError_t e;
-  if (split_of_ != A) {
-    const bool vec = (reinterpret_cast<uintptr_t>(A) % 16 == 0) && (lda % 4 == 0);
-    const long long total = m * (ldb_ / 8);
-    const int blocks = (int)std::min<long long>(cdiv(total, 256), (long long)G_ * 8);
-    split_a_kernel<<<blocks, 256, 0, st>>>(A, m, n, lda, vec, reinterpret_cast<bf16*>(Ahi_),
-                                           reinterpret_cast<bf16*>(Alo_), ldb_, sumsq);
-    note_launch();
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    split_of_ = A;
-    sumsq = nullptr;
-    // Tile counters start at zero; each pass's last arrivals reset them.
-    if ((e = cudaMemsetAsync(cnt_, 0, sizeof(int) * cdiv(std::max(m, n), BM), st)) != cudaSuccess) return e;
+  if (split_of_ != A || m != m_ || n != n_) {
+    if ((e = split(A, m, n, lda, sumsq, st)) != cudaSuccess) return e;
+  } else if (sumsq != nullptr) {
+    return cudaErrorInvalidValue;   // ||A||^2 comes with the split only
   }
-  if (sumsq != nullptr) return cudaErrorInvalidValue;   // ||A||^2 comes with the split only
+  const int npad_ = npad_of(d);
   const long long K = transA ? m : n, M = transA ? n : m;
+  if (K > k_cap_) return cudaErrorInvalidValue;
   if ((e = cudaMemsetAsync(flag_, 0, sizeof(int), st)) != cudaSuccess) return e;
   {
     dim3 grid((unsigned)cdiv(round_up(K, 8), 32), (unsigned)cdiv(d, 32));
@@ -540,6 +720,14 @@ cudaError_t TcEngine::pass(bool transA, const float* A, int64_t m, int64_t n, in
   a.tiles = (int)cdiv(M, BM);
   a.units = (long long)a.tiles * a.kblocks;
   a.G = (int)std::min<long long>(G_, a.units);
+  // Short K (e.g. X R^{-1} with K = d): split tiles would cost more in the
+  // epilogue than they save, so give each CTA whole tiles.
+  a.tpc = 0;
+  if (a.kblocks <= 16) {
+    a.tpc = (int)cdiv(a.tiles, G_);
+    a.G = (int)cdiv(a.tiles, a.tpc);
+  }
+  a.vec_out = ((reinterpret_cast<uintptr_t>(out) % 16) == 0 && ldout % 4 == 0) ? 1 : 0;
   a.stages = stages_of(npad_);
   a.out = out;
   a.ldo = ldout;
@@ -551,6 +739,51 @@ cudaError_t TcEngine::pass(bool transA, const float* A, int64_t m, int64_t n, in
   a.stage_bytes = stage_bytes_of(npad_);
   a.tmem_cols = tmem_cols_of(npad_);
   return transA ? launch_pass<true>(ah, al, xh, xl, a, st) : launch_pass<false>(ah, al, xh, xl, a, st);
+}
+
+cudaError_t TcEngine::gram(float* Gout, int64_t ldg, int* info, cudaStream_t st) {
+  if (split_of_ == nullptr || n_ > 256) return cudaErrorInvalidValue;
+  const int cols = (int)n_;
+  const int npad = npad_of(cols);
+  const int mtiles = (int)cdiv(cols, BM);
+  GramArgs a;
+  a.rows = (int)m_;
+  a.cols = cols;
+  a.npad = npad;
+  a.kblocks = (int)cdiv(m_, BK);
+  a.G = std::max(1, std::min({a.kblocks / 8, kGramMaxCtas, G_}));
+  a.mtiles = mtiles;
+  a.nbox = std::max((int)cdiv(npad, 64), 2 * mtiles);
+  a.stage_bytes = 2u * (uint32_t)a.nbox * 4096u;
+  a.stages = std::max(2, std::min(kMaxStages, (int)((smem_optin_tc() - 1024 - 512) / a.stage_bytes)));
+  a.part = gpart_;
+  a.info = info;
+  a.idesc = tc::idesc_bf16(BM, npad, true, true);
+  {
+    uint32_t need = (uint32_t)(mtiles * npad), c = 32;
+    while (c < need) c <<= 1;
+    a.tmem_cols = c;
+  }
+  CUtensorMap hi, lo;
+  if (!make_map(&hi, Ahi_, cols, m_, ldb_, 64, BK, CU_TENSOR_MAP_SWIZZLE_128B) ||
+      !make_map(&lo, Alo_, cols, m_, ldb_, 64, BK, CU_TENSOR_MAP_SWIZZLE_128B))
+    return cudaErrorInvalidValue;
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(tc_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem_optin_tc());
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  const size_t smem = (size_t)a.stages * a.stage_bytes + 1024 + 512;
+  tc_gram_kernel<<<a.G, kThreads, smem, st>>>(hi, lo, a);
+  note_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int blocks = std::max(1, std::min(G_ * 2, (cols * cols + 255) / 256));
+  tc_gram_reduce_kernel<<<blocks, 256, 0, st>>>(gpart_, a.G, mtiles, npad, cols, Gout, ldg);
+  note_launch();
+  return cudaGetLastError();
 }
 
 }  // namespace rqlp
