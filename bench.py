@@ -8,6 +8,7 @@ C ABI with A resident in HBM. value = GB/s of A streamed by the 2q + 2
 passes over A (aggregate over ranks), ms_per_step = time to factor.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|bf16x3|auto]
+  (auto = the BF16-split tensor-core form; the plain FP32 form is timed beside it)
   python bench.py --impl reference      # the FP64 CPU oracle on a bounded sample
 
 For N > 1 (torchrun) every rank factors its own replica (the path does not
@@ -49,6 +50,7 @@ def parse():
     ap.add_argument("--q", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare", action="store_true", help="skip timing the plain FP32 form")
     ap.add_argument("--sample", type=int, default=0,
                     help="rows/cols of the oracle's sample block (0 = default for the workload)")
     return ap.parse_args()
@@ -121,20 +123,26 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ oracle baseline
 
-def oracle_sample(a, S):
-    """The FP64 oracle on the leading S x S block of the workload's A (same
-    generator and seed) with the matching Omega rows; returns (GB/s, s, cores)."""
+def oracle_inputs(a, S, A=None):
+    """The leading S x S block of the workload's A (same generator and seed)
+    and the matching Omega rows, in float64 on the host."""
     import numpy as np
     import torch
 
-    from oracle import rqlp_oracle as orc
     from paper_2110_01011_gb300 import inputs
-    sig = inputs.exp_spectrum(1000, 50.0)
-    dev = "cuda" if torch.cuda.is_available() else "cpu"
-    A = inputs.low_rank_matrix_torch(a.m, a.n, sig, 1e-6, seed=1002, rank=1000, device=dev)
+    if A is None:
+        sig = inputs.exp_spectrum(1000, 50.0)
+        dev = "cuda" if torch.cuda.is_available() else "cpu"
+        A = inputs.low_rank_matrix_torch(a.m, a.n, sig, 1e-6, seed=1002, rank=1000, device=dev)
     As = A[:S, :S].double().cpu().numpy()
-    del A
     Om = inputs.omega(a.m, a.k + a.p, seed=2002)[:S].astype(np.float64)
+    return As, Om
+
+
+def oracle_time(a, As, Om):
+    """One run of the FP64 oracle chain on the sample; returns (GB/s, s, cores)."""
+    from oracle import rqlp_oracle as orc
+    S = As.shape[0]
     t0 = time.perf_counter()
     orc.rand_qlp(As, Om, a.q)
     dt = time.perf_counter() - t0
@@ -148,9 +156,10 @@ def run_reference(a):
     if rank != 0:
         return
     S = a.sample or 2000
+    As, Om = oracle_inputs(a, S)
     vals = []
     for i in range(a.warmup + a.steps):
-        gbs, dt, cores = oracle_sample(a, S)
+        gbs, dt, cores = oracle_time(a, As, Om)
         if i >= a.warmup:
             vals.append((gbs, dt))
     gbs = statistics.median(v[0] for v in vals)
@@ -206,9 +215,8 @@ def main():
     dev = torch.device("cuda", local)
     lib = rqlp.load()
     del lib
-    prec = {"fp32": rqlp.PREC_FP32, "bf16x3": rqlp.PREC_BF16X3}.get(a.precision)
-    if prec is None:
-        prec = rqlp.PREC_FP32
+    # The headline form is the BF16-split tensor-core path; FP32 is timed beside it.
+    prec = {"fp32": rqlp.PREC_FP32, "bf16x3": rqlp.PREC_BF16X3}.get(a.precision, rqlp.PREC_BF16X3)
     d = a.k + a.p
 
     def barrier():
@@ -274,16 +282,50 @@ def main():
         roof = {"bound": "alu", "achieved": flops / (pass_ms * 1e-3) / 1e12, "peak": peak,
                 "unit": "TFLOP/s", "peak_source": f"derived: {nsm} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz"}
     else:
+        # The split form's algorithm is three BF16 products per pass (A_hi X_hi +
+        # A_hi X_lo + A_lo X_hi); the pass timed is a power-pass / projection one.
         peak = peaks.get("bf16_tflops_sustained", 1683.0)
         mma_flops = 3 * flops
         roof = {"bound": "tensor", "achieved": mma_flops / (pass_ms * 1e-3) / 1e12, "peak": peak,
-                "unit": "TFLOP/s", "peak_source": "MEASURED_PEAKS bf16_tflops_sustained (of measured)"}
+                "unit": "TFLOP/s", "flops_per_launch": mma_flops,
+                "peak_source": "MEASURED_PEAKS bf16_tflops_sustained (of measured)"}
     roof["frac"] = roof["achieved"] / roof["peak"]
+    roof.setdefault("flops_per_launch", flops)
     roof["traffic"] = traffic_for(f"{kname}_{'fp32' if prec == 0 else 'bf16x3'}", sha)
     roof["kernel"] = kname
     roof["launch_ms"] = pass_ms
     roof["hbm_gbs"] = a.m * a.n * 4 / (pass_ms * 1e-3) / 1e9
     roof["hbm_frac_of_measured"] = roof["hbm_gbs"] / peaks.get("hbm_gbs", 6761.6)
+
+    # Accuracy of the timed form (Q L P^T = A P~ P~^T, so the residual follows from
+    # ||A||_F^2 - ||L||_F^2) and the plain-FP32 form timed on the same inputs.
+    dg = diag.cpu().tolist()
+    relres = (max(dg[2], 0.0) / dg[0]) ** 0.5 if dg[0] > 0 else float("nan")
+    compare = {"form": "fp32" if prec == rqlp.PREC_FP32 else "bf16x3", "rel_residual": relres}
+    if prec != rqlp.PREC_FP32 and not a.no_compare:
+        out32 = (torch.empty_like(Q), torch.empty_like(L), torch.empty_like(P), torch.empty_like(info),
+                 torch.empty_like(diag))
+        ws32 = torch.empty(rqlp.rqlp_workspace_bytes(a.m, a.n, a.k, a.p, a.q, rqlp._opts(rqlp.PREC_FP32)) + 256,
+                           dtype=torch.uint8, device=dev)
+        rqlp.factor(A, a.k, a.p, a.q, Om, precision=rqlp.PREC_FP32, workspace=ws32, out=out32)
+        barrier()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        nf = 3
+        f0.record(st)
+        for _ in range(nf):
+            rqlp.factor(A, a.k, a.p, a.q, Om, precision=rqlp.PREC_FP32, workspace=ws32, out=out32)
+        f1.record(st)
+        barrier()
+        d32 = out32[4].cpu().tolist()
+        compare["fp32_ms_per_step"] = f0.elapsed_time(f1) / nf
+        compare["fp32_rel_residual"] = (max(d32[2], 0.0) / d32[0]) ** 0.5
+        compare["speedup_vs_fp32"] = compare["fp32_ms_per_step"] / ms_step
+        # ||L_split - L_fp32|| on the leading-k diagonal (both against the same A)
+        l16 = torch.diagonal(L)[: a.k].double()
+        l32 = torch.diagonal(out32[1])[: a.k].double()
+        compare["lead_k_Lii_rel_diff_vs_fp32"] = float(((l16 - l32).abs() / l32.abs()).max())
+        del ws32, out32
+        torch.cuda.empty_cache()
 
     # End to end through the host-buffer entry point (pinned buffers).
     e2e = None
@@ -295,7 +337,6 @@ def main():
                 torch.zeros(4, dtype=torch.float64))
         hws = torch.empty(rqlp.rqlp_host_workspace_bytes(a.m, a.n, a.k, a.p, a.q, opts) + 256,
                           dtype=torch.uint8, device=dev)
-        del A
         torch.cuda.empty_cache()
         for _ in range(max(1, a.warmup)):
             rqlp.factor_host(hA, a.k, a.p, a.q, hO, precision=prec, workspace=hws, out=hout)
@@ -314,10 +355,11 @@ def main():
         e2e = {"value": world * apass_bytes(a) / dt / 1e9, "unit": "GB/s", "ms_per_step": dt * 1e3,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
+    A_keep = A
     cpu = None
     if rank == 0 and not a.no_cpu_baseline:
         S = a.sample or 4000
-        gbs, dt, cores = oracle_sample(a, S)
+        gbs, dt, cores = oracle_time(a, *oracle_inputs(a, S, A_keep))
         cpu = {"value": gbs, "unit": "GB/s", "cores": cores, "kind": "oracle",
                "sample": f"FP64 oracle chain on the leading {S}x{S} block of the workload's A "
                          f"(q={a.q}, d={d}), {dt:.1f} s"}
@@ -334,6 +376,7 @@ def main():
                            "l2": "inputs larger than L2 (A is %.1f GB)" % (a.m * a.n * 4 / 1e9),
                            "parallelism": "replicas" if world > 1 else "single"},
                 "status": status, "clocks": ck, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "compare": compare,
                 "gpu_launches": launches, "kernel_sha": sha}
         print(json.dumps(line), flush=True)
     if world > 1:

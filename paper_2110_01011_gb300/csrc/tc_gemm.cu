@@ -738,7 +738,11 @@ cudaError_t TcEngine::pass(bool transA, const float* A, int64_t m, int64_t n, in
   a.idesc = tc::idesc_bf16(BM, npad_, transA, false);
   a.stage_bytes = stage_bytes_of(npad_);
   a.tmem_cols = tmem_cols_of(npad_);
-  return transA ? launch_pass<true>(ah, al, xh, xl, a, st) : launch_pass<false>(ah, al, xh, xl, a, st);
+  const bool prof = profiled_ && profiling_on();
+  if (prof) profile_mark_begin(st);
+  e = transA ? launch_pass<true>(ah, al, xh, xl, a, st) : launch_pass<false>(ah, al, xh, xl, a, st);
+  if (prof) profile_mark_end(st, transA ? 1 : 0);
+  return e;
 }
 
 cudaError_t TcEngine::gram(float* Gout, int64_t ldg, int* info, cudaStream_t st) {

@@ -20,6 +20,8 @@ class TcEngine {
   // largest K of a pass (rows of X); gram: reserve the Gram partial slots.
   void layout(Arena& ar, int64_t rows_cap, int64_t cols_cap, int d_cap, int64_t k_cap, bool gram);
   void reset() { split_of_ = nullptr; }
+  // Bracket this engine's MMA kernel with the library's profiling events.
+  void set_profiled(bool on) { profiled_ = on; }
   // A (rows x cols FP32) -> A_hi, A_lo; sumsq (optional) += ||A||_F^2.
   cudaError_t split(const float* A, int64_t rows, int64_t cols, int64_t lda, double* sumsq, cudaStream_t st);
   // transA: out (cols x d) = A^T X (X rows x d); else out (rows x d) = A X
@@ -39,6 +41,7 @@ class TcEngine {
   int* flag_ = nullptr;
   int* cnt_ = nullptr;
   const float* split_of_ = nullptr;
+  bool profiled_ = false;
 };
 
 }  // namespace rqlp
