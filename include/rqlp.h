@@ -178,6 +178,64 @@ rqlp_status rqlp_orth(float* X, int64_t rows, int d, int64_t ldx, float* R, int6
                       void* workspace, size_t ws_bytes, int* d_info, const rqlp_opts* opts,
                       void* stream);
 
+/* ---- Learned (q, p) (no counterpart in the paper, which fixes neither q nor
+ * p). A probe sketch Y_w = A^T Omega_w of width w = k + 20 (the widest sketch
+ * any p in {5, 10, 20} needs) has its R factor computed (FP32 Gram and
+ * Cholesky in both precisions); 12 statistics of its R-diagonal plus
+ * log10(target) (13 floats) feed a 3-layer MLP (13 -> 64 -> 64 -> 8, ReLU)
+ * whose two heads pick q in {0, 1, 2, 3, 4} and p in {5, 10, 20}: the pass
+ * count and oversampling expected to reach the requested excess rank-k error
+ *   target >= ||A - A P_k P_k^T||_F / (sum_{i>k} sigma_i^2)^(1/2) - 1
+ * at least cost (2q + 2)(k + p). The probe is the first sketch of the chain
+ * and its R factor the chain's first orthonormalisation, so prediction costs
+ * no extra pass over A. A failed probe (non-zero d_info status or non-finite
+ * logits) falls back to q = 2, p = 10.
+ *
+ * Parameters: RQLP_MLP_PARAMS floats, device, layout W1 (13 x 64 row-major),
+ * b1 (64), W2 (64 x 64), b2 (64), W3 (64 x 8), b3 (8); logits 0..4 = q head,
+ * 5..7 = p head. target: 0 < target < 1, else RQLP_ERR_ARG. */
+#define RQLP_MLP_FEATURES 13
+#define RQLP_MLP_HIDDEN 64
+#define RQLP_MLP_PARAMS 5576
+
+/* Forward pass: logits (batch x 8) of features X (batch x 13), device. */
+rqlp_status rqlp_mlp_forward(const float* params, const float* X, int batch, float* logits,
+                             void* stream);
+/* Mean cross-entropy of both heads and its gradient (RQLP_MLP_PARAMS floats)
+ * for labels yq in 0..4, yp in 0..2 (device int arrays). loss: 1 device float
+ * (may be NULL). workspace: rqlp_mlp_workspace_bytes(batch) bytes, device.
+ * Deterministic (fixed summation order). */
+size_t rqlp_mlp_workspace_bytes(int batch);
+rqlp_status rqlp_mlp_grad(const float* params, const float* X, const int* yq, const int* yp,
+                          int batch, float* grad, float* loss, void* workspace, size_t ws_bytes,
+                          void* stream);
+/* One Adam step (step is 1-based) on n parameters with moments m1, m2. */
+rqlp_status rqlp_mlp_adam(float* params, const float* grad, float* m1, float* m2, int n,
+                          float lr, float beta1, float beta2, float eps, int step, void* stream);
+
+/* Probe features (13 device floats, the last log10(target)) of A (m x n)
+ * with Omega (m x (k+20)). Workspace: rqlp_learned_workspace_bytes(...).
+ * d_info as for rqlp_factor. */
+size_t rqlp_learned_workspace_bytes(int64_t m, int64_t n, int k, const rqlp_opts* opts);
+rqlp_status rqlp_probe_features(const float* A, int64_t m, int64_t n, int64_t lda, int k,
+                                const float* Omega, int64_t ldo, double target, float* feat,
+                                void* workspace, size_t ws_bytes, int* d_info,
+                                const rqlp_opts* opts, void* stream);
+/* Probe + MLP + argmax: d_qp (2 device ints) receives (q, p). */
+rqlp_status rqlp_predict_qp(const float* A, int64_t m, int64_t n, int64_t lda, int k,
+                            const float* Omega, int64_t ldo, double target, const float* params,
+                            int* d_qp, void* workspace, size_t ws_bytes, int* d_info,
+                            const rqlp_opts* opts, void* stream);
+/* Rand-QLP with the predicted (q, p): the probe is the chain's first sketch
+ * (Omega's first k + p columns). Q (m x (k+p)), L, P (n x (k+p)) must have
+ * room for k + 20 columns. h_qp (2 host ints) receives the (q, p) used.
+ * Synchronises the stream once (to read (q, p)), so it cannot be captured. */
+rqlp_status rqlp_factor_learned(const float* A, int64_t m, int64_t n, int64_t lda, int k,
+                                const float* Omega, int64_t ldo, double target, const float* params,
+                                float* Q, int64_t ldq, float* L, int64_t ldl, float* P, int64_t ldp,
+                                void* workspace, size_t ws_bytes, int* d_info, double* d_diag,
+                                int* h_qp, const rqlp_opts* opts, void* stream);
+
 /* ---- Runtime services (host only; no device memory).
  *
  * rqlp_kernel_launches: cumulative number of CUDA kernels this library has

@@ -8,7 +8,9 @@ against.
 
 * ``probe_features``: features of the R-diagonal r_1..r_w of qf(A^T Omega_w),
   the probe sketch of width w = k + 20 (the widest sketch any p in {5, 10,
-  20} needs, so the probe is also the first sketch of the chain).
+  20} needs, so the probe is also the first sketch of the chain), and
+  log10 of the requested excess error (the network predicts the (q, p) that
+  reaches a requested error, so the request is one of its inputs).
 * ``forward`` / ``backward``: 3-layer MLP, F -> H -> H -> 8, ReLU, with two
   softmax heads (5 logits for q, 3 for p) and the mean cross-entropy of both.
 * ``adam``: one Adam step (Kingma & Ba 2015), bias-corrected.
@@ -24,7 +26,7 @@ __all__ = ["Q_CHOICES", "P_CHOICES", "N_FEATURES", "HIDDEN", "param_shapes", "n_
 
 Q_CHOICES = (0, 1, 2, 3, 4)
 P_CHOICES = (5, 10, 20)
-N_FEATURES = 12
+N_FEATURES = 13
 HIDDEN = 64
 N_OUT = len(Q_CHOICES) + len(P_CHOICES)
 
@@ -47,13 +49,15 @@ def unpack(theta, F=N_FEATURES, H=HIDDEN):
     return out
 
 
-def probe_features(r, k, m, n):
-    """Features of the probe R-diagonal r (length w >= k + 1, positive).
+def probe_features(r, k, m, n, target):
+    """Features of the probe R-diagonal r (length w >= k + 1, positive) and
+    of the requested excess error target (0 < target < 1).
 
     With l_i = log10(r_i / r_1) (1-based i, indices clamped to [1, w]):
     [l_k, l_ceil(k/2), l_k - l_ceil(k/2), l_{k+1} - l_k, l_{k+5} - l_k,
      l_{k+10} - l_k, l_{k+20} - l_k, l_{k+20} - l_{k+10}, std of the steps
-     l_{i+1} - l_i over i < w, log10 k, log10 min(m, n), k / min(m, n)].
+     l_{i+1} - l_i over i < w, log10 k, log10 min(m, n), k / min(m, n),
+     log10 target].
     """
     r = np.asarray(r, dtype=np.float64)
     w = r.shape[0]
@@ -68,7 +72,7 @@ def probe_features(r, k, m, n):
     return np.array([
         L(k), L(h), L(k) - L(h), L(k + 1) - L(k), L(k + 5) - L(k), L(k + 10) - L(k), L(k + 20) - L(k),
         L(k + 20) - L(k + 10), float(np.std(steps)) if steps.size else 0.0,
-        np.log10(k), np.log10(mn), k / mn,
+        np.log10(k), np.log10(mn), k / mn, np.log10(target),
     ])
 
 

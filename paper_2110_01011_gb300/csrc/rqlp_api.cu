@@ -33,11 +33,11 @@ constexpr int kScal = 4;    // [0] ||A||^2, [1] ||L||^2, [2] shifted Cholesky co
 // Building blocks of the chain for a fixed sketch width d, with their scratch.
 class Ops {
  public:
-  Ops(int d, const rqlp_opts& o) : d_(d), ld_(round_up(d, 4)), o_(o) {}
+  Ops(int d, const rqlp_opts& o) : d_(d), dcap_(d), ld_(round_up(d, 4)), o_(o) {}
 
   // part_floats: largest split-K partial buffer any product of the caller needs.
   void layout(Arena& ar, size_t part_floats, bool with_tc, int64_t m, int64_t n) {
-    const int64_t dd = (int64_t)d_ * ld_;
+    const int64_t dd = (int64_t)dcap_ * ld_;
     G_ = ar.take<float>(dd);
     for (int i = 0; i < 3; ++i) {
       R_[i] = ar.take<float>(dd);
@@ -47,17 +47,40 @@ class Ops {
     part_ = ar.take<float>(std::max<size_t>(part_floats, 1));
     scal = ar.take<double>(kScal);
     gates = ar.take<int>(kGates);
-    cstore_ = ar.take<char>(chol_global_bytes(d_, o_.small_fp64 != 0));
+    cstore_ = ar.take<char>(chol_global_bytes(dcap_, o_.small_fp64 != 0));
     if (with_tc) {
-      tc_.layout(ar, m, n, d_, std::max(m, n), false);
+      tc_.layout(ar, m, n, dcap_, std::max(m, n), false);
       tc_.set_profiled(true);
       // Tall d-column operands of CholeskyQR: Gram and X R^{-1} on the tensor cores.
-      tcs_.layout(ar, std::max(m, n), d_, d_, d_, true);
+      tcs_.layout(ar, std::max(m, n), dcap_, dcap_, dcap_, true);
     }
     tc_on_ = with_tc;
   }
   void bind(cudaStream_t st, int* info) { st_ = st; info_ = info; }
   int64_t ld() const { return ld_; }
+  // Current sketch width (<= the capacity the workspace was laid out for).
+  void set_d(int d) { d_ = d; }
+  int d() const { return d_; }
+  const float* R(int slot) const { return R_[slot]; }
+  // R factor of X (rows x d) in slot 0 without forming X R^{-1} (the probe).
+  // The Gram is FP32 in both precisions: the probe's small R-diagonal entries
+  // carry the Gram's error amplified by kappa(X)^2, and they are the features.
+  // gates[0] is raised if the Cholesky had to shift.
+  cudaError_t gram_chol(const float* X, int64_t ldx, int64_t rows) {
+    CK(gram(X, ldx, rows, nullptr));
+    return chol(0, &gates[0], nullptr);
+  }
+  // out = X R0^{-1} with the inverse already in slot 0. For a prefix of the
+  // columns the leading block of the triangular inverse is the inverse of the
+  // leading block, so a probe of a wider sketch serves every narrower width.
+  cudaError_t apply_r0(const float* X, int64_t ldx, int64_t rows, float* out, int64_t ldout) {
+    if (tc_on_ && rows > (int64_t)d_) {
+      tcs_.reset();
+      CK(tcs_.split(X, rows, d_, ldx, nullptr, st_));
+      return tcs_.pass(false, X, rows, d_, ldx, Ri_[0], ld_, d_, out, ldout, nullptr, info_, st_);
+    }
+    return trmm(X, ldx, rows, Ri_[0], out, ldout, nullptr);
+  }
 
   cudaError_t init() {
     tc_.reset();
@@ -108,8 +131,11 @@ class Ops {
     CK(chol(slot, gate_out, nullptr));
     return tcs_.pass(false, X, rows, d_, ldx, Ri_[slot], ld_, d_, out, ldout, nullptr, info_, st_);
   }
-  // One CholeskyQR pass (shifted on breakdown): out = X R^{-1}.
-  cudaError_t orth_inter(const float* X, int64_t ldx, int64_t rows, float* out, int64_t ldout) {
+  // One CholeskyQR pass (shifted on breakdown): out = X R^{-1}. have_r0: the
+  // R factor is already in slot 0 (the probe).
+  cudaError_t orth_inter(const float* X, int64_t ldx, int64_t rows, float* out, int64_t ldout,
+                         bool have_r0 = false) {
+    if (have_r0) return apply_r0(X, ldx, rows, out, ldout);
     if (tc_on_ && rows > (int64_t)d_) return tc_cqr(X, ldx, rows, out, ldout, 0, nullptr);
     CK(gram(X, ldx, rows, nullptr));
     CK(chol(0, nullptr, nullptr));
@@ -119,9 +145,11 @@ class Ops {
   // CholeskyQR3). X (rows x d) is overwritten; tmp holds rows x d (ld_);
   // Racc (optional, d x d, ld_) receives R = R3 R2 R1.
   cudaError_t orth_final(float* X, int64_t ldx, int64_t rows, float* out, int64_t ldout, float* tmp,
-                         float* Racc, int slot) {
+                         float* Racc, int slot, bool have_r0 = false) {
     int* g = &gates[slot];
-    if (tc_on_ && rows > (int64_t)d_) {
+    if (have_r0) {   // first pass from the probe's R (slot 0, gate in gates[0])
+      CK(apply_r0(X, ldx, rows, tmp, ld_));
+    } else if (tc_on_ && rows > (int64_t)d_) {
       // First pass on the tensor cores (it only has to leave X well conditioned);
       // the second pass, which sets the orthogonality, stays in FP32.
       CK(tc_cqr(X, ldx, rows, tmp, ld_, 0, g));
@@ -149,7 +177,7 @@ class Ops {
   int* gates = nullptr;
 
  private:
-  int d_;
+  int d_, dcap_;
   int64_t ld_;
   rqlp_opts o_;
   cudaStream_t st_ = nullptr;
@@ -163,6 +191,7 @@ class Ops {
 struct Dims {
   int64_t m, n, lda, ldo;
   int k, p, q, d;
+  bool learned = false;   // d = k + 20 is a capacity; the run picks p in {5, 10, 20}
 };
 
 struct Out {
@@ -171,7 +200,8 @@ struct Out {
   float* P; int64_t ldp;
 };
 
-// The whole chain for one matrix.
+// The whole chain for one matrix. Dims.d is the widest sketch the workspace
+// serves; the learned form runs the chain at a narrower width.
 class Plan {
  public:
   Plan(const Dims& dm, const rqlp_opts& o) : d_(dm), ops_(dm.d, o), o_(o) {}
@@ -187,26 +217,69 @@ class Plan {
     Ts_ = ar.take<float>(dd);
     Ts2_ = ar.take<float>(dd);
     Ph_ = ar.take<float>(dd);
-    size_t part = std::max({Ops::pass_part_floats(d_.m, d_.n, d_.d), Ops::orth_part_floats(d_.m, d_.d),
-                            Ops::orth_part_floats(d_.n, d_.d), Ops::orth_part_floats(d_.d, d_.d)});
+    feat_ = ar.take<float>(RQLP_MLP_FEATURES);
+    logits_ = ar.take<float>(8);
+    qp_ = ar.take<int>(2);
+    // Split-K partial buffers for every width this plan may run at.
+    size_t part = 0;
+    const int lo = d_.learned ? std::max(1, d_.d - 15) : d_.d;
+    for (int d = lo; d <= d_.d; ++d)
+      part = std::max({part, Ops::pass_part_floats(d_.m, d_.n, d), Ops::orth_part_floats(d_.m, d),
+                       Ops::orth_part_floats(d_.n, d), Ops::orth_part_floats(d, d)});
     ops_.layout(ar, part, o_.precision == RQLP_PREC_BF16X3, d_.m, d_.n);
     return ar.off;
   }
 
   cudaError_t run(const float* A, const float* Om, const Out& out, int* info, double* diag, cudaStream_t st) {
     ops_.bind(st, info);
-    const int64_t m = d_.m, n = d_.n, lda = d_.lda, ld = ops_.ld();
-    const int d = d_.d;
     CK(ops_.init());
     // Sketch Y = A^T Omega (Algorithm 1 step 3); ||A||_F^2 rides along.
-    CK(ops_.pass(true, A, m, n, lda, Om, d_.ldo, Y_, ld, &ops_.scal[0]));
-    if (d_.q == 0) CK(ops_.orth_final(Y_, ld, n, Pt_, ld, T1_, nullptr, 0));
-    else CK(ops_.orth_inter(Y_, ld, n, Pt_, ld));
-    for (int i = 1; i <= d_.q; ++i) {
+    CK(ops_.pass(true, A, d_.m, d_.n, d_.lda, Om, d_.ldo, Y_, ops_.ld(), &ops_.scal[0]));
+    return chain(A, d_.q, out, info, diag, st);
+  }
+
+  // Probe sketch of the full width, its R factor, features, MLP and (q, p),
+  // all on the device. params == nullptr stops after the features.
+  cudaError_t probe(const float* A, const float* Om, double target, const float* params, int* info,
+                    cudaStream_t st) {
+    ops_.bind(st, info);
+    CK(ops_.init());
+    ops_.set_d(d_.d);
+    CK(ops_.pass(true, A, d_.m, d_.n, d_.lda, Om, d_.ldo, Y_, ops_.ld(), &ops_.scal[0]));
+    CK(ops_.gram_chol(Y_, ops_.ld(), d_.n));
+    CK(probe_features(ops_.R(0), ops_.ld(), d_.d, d_.k, std::min(d_.m, d_.n), target, feat_, st));
+    if (params == nullptr) return cudaSuccess;
+    CK(mlp_forward(params, feat_, 1, logits_, st));
+    return predict_qp(logits_, info, qp_, st);
+  }
+  const float* features() const { return feat_; }
+  const int* qp() const { return qp_; }
+
+  // Continue from the probe with the predicted (q, p): the probe's first
+  // k + p columns are the sketch A^T Omega_{k+p}.
+  // Its R factor (slot 0) serves the chain's first orthonormalisation; the
+  // probe's shift gate only matters when that one is the final CholeskyQR2.
+  cudaError_t finish_learned(const float* A, int q, int p, const Out& out, int* info, double* diag,
+                             cudaStream_t st) {
+    ops_.set_d(d_.k + p);
+    if (q > 0) CK(cudaMemsetAsync(&ops_.gates[0], 0, sizeof(int), st));
+    return chain(A, q, out, info, diag, st, true);
+  }
+
+ private:
+  // From Y = A^T Omega (width ops_.d()) to Q, L, P.
+  // have_r0: the R factor of Y is already in slot 0.
+  cudaError_t chain(const float* A, int q, const Out& out, int* info, double* diag, cudaStream_t st,
+                    bool have_r0 = false) {
+    const int64_t m = d_.m, n = d_.n, lda = d_.lda, ld = ops_.ld();
+    const int d = ops_.d();
+    if (q == 0) CK(ops_.orth_final(Y_, ld, n, Pt_, ld, T1_, nullptr, 0, have_r0));
+    else CK(ops_.orth_inter(Y_, ld, n, Pt_, ld, have_r0));
+    for (int i = 1; i <= q; ++i) {
       CK(ops_.pass(false, A, m, n, lda, Pt_, ld, Z_, ld, nullptr));   // Z = A P~
       CK(ops_.orth_inter(Z_, ld, m, T1_, ld));                        // Z = qf(Z), one pass
       CK(ops_.pass(true, A, m, n, lda, T1_, ld, Y_, ld, nullptr));    // Y = A^T Z
-      if (i == d_.q) CK(ops_.orth_final(Y_, ld, n, Pt_, ld, T1_, nullptr, 0));
+      if (i == q) CK(ops_.orth_final(Y_, ld, n, Pt_, ld, T1_, nullptr, 0));
       else CK(ops_.orth_inter(Y_, ld, n, Pt_, ld));
     }
     // (Q, R) = qr(A P~)  (Algorithm 1 step 4)
@@ -222,12 +295,13 @@ class Plan {
     return finish_diag(ops_.scal, diag, info, st);
   }
 
- private:
   Dims d_;
   Ops ops_;
   rqlp_opts o_;
   float *Y_ = nullptr, *Z_ = nullptr, *Pt_ = nullptr, *T1_ = nullptr;
   float *Rb_ = nullptr, *Rh_ = nullptr, *Ts_ = nullptr, *Ts2_ = nullptr, *Ph_ = nullptr;
+  float *feat_ = nullptr, *logits_ = nullptr;
+  int* qp_ = nullptr;
 };
 
 rqlp_opts resolve(const rqlp_opts* o) {
@@ -444,6 +518,125 @@ rqlp_status rqlp_orth(float* X, int64_t rows, int d, int64_t ldx, float* R, int6
   if (e == cudaSuccess) e = copy_matrix(rows, d, tmp, ld, X, ldx, st);
   if (e == cudaSuccess && R != nullptr) e = copy_matrix(d, d, Racc, ld, R, ldr, st);
   return e == cudaSuccess ? RQLP_OK : RQLP_ERR_CUDA;
+}
+
+size_t rqlp_mlp_workspace_bytes(int batch) {
+  if (batch <= 0) return 0;
+  return mlp_workspace_floats(batch) * sizeof(float);
+}
+
+rqlp_status rqlp_mlp_forward(const float* params, const float* X, int batch, float* logits, void* stream) {
+  if (params == nullptr || X == nullptr || logits == nullptr || batch <= 0) return RQLP_ERR_ARG;
+  return mlp_forward(params, X, batch, logits, static_cast<cudaStream_t>(stream)) == cudaSuccess ? RQLP_OK
+                                                                                                 : RQLP_ERR_CUDA;
+}
+
+rqlp_status rqlp_mlp_grad(const float* params, const float* X, const int* yq, const int* yp, int batch,
+                          float* grad, float* loss, void* workspace, size_t ws_bytes, void* stream) {
+  if (params == nullptr || X == nullptr || yq == nullptr || yp == nullptr || grad == nullptr || batch <= 0)
+    return RQLP_ERR_ARG;
+  if (workspace == nullptr || ws_bytes < rqlp_mlp_workspace_bytes(batch) || !aligned(workspace, 16))
+    return RQLP_ERR_WORKSPACE;
+  return mlp_grad(params, X, yq, yp, batch, grad, loss, workspace, static_cast<cudaStream_t>(stream)) ==
+                 cudaSuccess
+             ? RQLP_OK
+             : RQLP_ERR_CUDA;
+}
+
+rqlp_status rqlp_mlp_adam(float* params, const float* grad, float* m1, float* m2, int n, float lr, float beta1,
+                          float beta2, float eps, int step, void* stream) {
+  if (params == nullptr || grad == nullptr || m1 == nullptr || m2 == nullptr || n <= 0 || step < 1)
+    return RQLP_ERR_ARG;
+  return mlp_adam(params, grad, m1, m2, n, lr, beta1, beta2, eps, step, static_cast<cudaStream_t>(stream)) ==
+                 cudaSuccess
+             ? RQLP_OK
+             : RQLP_ERR_CUDA;
+}
+
+namespace {
+bool valid_learned(int64_t m, int64_t n, int k) { return valid_sizes(m, n, k, 20, 0); }
+bool valid_target(double t) { return t > 0.0 && t < 1.0; }
+Dims learned_dims(int64_t m, int64_t n, int64_t lda, int k, int64_t ldo) {
+  Dims dm = make_dims(m, n, lda, k, 20, 4, ldo);
+  dm.learned = true;
+  return dm;
+}
+}  // namespace
+
+size_t rqlp_learned_workspace_bytes(int64_t m, int64_t n, int k, const rqlp_opts* opts) {
+  rqlp_opts o = resolve(opts);
+  if (!valid_opts(o) || !valid_learned(m, n, k)) return 0;
+  return plan_bytes(learned_dims(m, n, n, k, k + 20), o);
+}
+
+static rqlp_status probe_common(const float* A, int64_t m, int64_t n, int64_t lda, int k, const float* Omega,
+                                int64_t ldo, double target, const float* params, float* feat, int* d_qp,
+                                void* workspace, size_t ws_bytes, int* d_info, const rqlp_opts* opts,
+                                void* stream) {
+  rqlp_opts o = resolve(opts);
+  if (!valid_opts(o) || !valid_learned(m, n, k) || !valid_target(target) || A == nullptr || Omega == nullptr ||
+      d_info == nullptr)
+    return RQLP_ERR_ARG;
+  if (lda < n || ldo < k + 20) return RQLP_ERR_ARG;
+  if (o.precision == RQLP_PREC_BF16X3 && !tc_supported(A, lda, Omega, ldo)) return RQLP_ERR_UNSUPPORTED;
+  Dims dm = learned_dims(m, n, lda, k, ldo);
+  if (workspace == nullptr || ws_bytes < plan_bytes(dm, o) || !aligned(workspace, 256)) return RQLP_ERR_WORKSPACE;
+  Arena ar = arena_over(workspace, ws_bytes);
+  Plan pl(dm, o);
+  pl.layout(ar);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (pl.probe(A, Omega, target, params, d_info, st) != cudaSuccess) return RQLP_ERR_CUDA;
+  if (feat != nullptr &&
+      copy_matrix(1, RQLP_MLP_FEATURES, pl.features(), RQLP_MLP_FEATURES, feat, RQLP_MLP_FEATURES, st) != cudaSuccess)
+    return RQLP_ERR_CUDA;
+  if (d_qp != nullptr && cudaMemcpyAsync(d_qp, pl.qp(), 2 * sizeof(int), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    return RQLP_ERR_CUDA;
+  return RQLP_OK;
+}
+
+rqlp_status rqlp_probe_features(const float* A, int64_t m, int64_t n, int64_t lda, int k, const float* Omega,
+                                int64_t ldo, double target, float* feat, void* workspace, size_t ws_bytes,
+                                int* d_info, const rqlp_opts* opts, void* stream) {
+  if (feat == nullptr) return RQLP_ERR_ARG;
+  return probe_common(A, m, n, lda, k, Omega, ldo, target, nullptr, feat, nullptr, workspace, ws_bytes, d_info,
+                      opts, stream);
+}
+
+rqlp_status rqlp_predict_qp(const float* A, int64_t m, int64_t n, int64_t lda, int k, const float* Omega,
+                            int64_t ldo, double target, const float* params, int* d_qp, void* workspace,
+                            size_t ws_bytes, int* d_info, const rqlp_opts* opts, void* stream) {
+  if (params == nullptr || d_qp == nullptr) return RQLP_ERR_ARG;
+  return probe_common(A, m, n, lda, k, Omega, ldo, target, params, nullptr, d_qp, workspace, ws_bytes, d_info,
+                      opts, stream);
+}
+
+rqlp_status rqlp_factor_learned(const float* A, int64_t m, int64_t n, int64_t lda, int k, const float* Omega,
+                                int64_t ldo, double target, const float* params, float* Q, int64_t ldq, float* L,
+                                int64_t ldl, float* P, int64_t ldp, void* workspace, size_t ws_bytes, int* d_info,
+                                double* d_diag, int* h_qp, const rqlp_opts* opts, void* stream) {
+  rqlp_opts o = resolve(opts);
+  if (!valid_opts(o) || !valid_learned(m, n, k) || !valid_target(target) || A == nullptr || Omega == nullptr ||
+      params == nullptr || Q == nullptr || L == nullptr || P == nullptr || d_info == nullptr || h_qp == nullptr)
+    return RQLP_ERR_ARG;
+  const int dmax = k + 20;
+  if (lda < n || ldo < dmax || ldq < dmax || ldl < dmax || ldp < dmax) return RQLP_ERR_ARG;
+  if (o.precision == RQLP_PREC_BF16X3 && !tc_supported(A, lda, Omega, ldo)) return RQLP_ERR_UNSUPPORTED;
+  Dims dm = learned_dims(m, n, lda, k, ldo);
+  if (workspace == nullptr || ws_bytes < plan_bytes(dm, o) || !aligned(workspace, 256)) return RQLP_ERR_WORKSPACE;
+  Arena ar = arena_over(workspace, ws_bytes);
+  Plan pl(dm, o);
+  pl.layout(ar);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (pl.probe(A, Omega, target, params, d_info, st) != cudaSuccess) return RQLP_ERR_CUDA;
+  int qp[2] = {-1, -1};
+  if (cudaMemcpyAsync(qp, pl.qp(), sizeof(qp), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return RQLP_ERR_CUDA;
+  if (qp[0] < 0 || qp[0] > 4 || (qp[1] != 5 && qp[1] != 10 && qp[1] != 20)) return RQLP_ERR_CUDA;
+  h_qp[0] = qp[0];
+  h_qp[1] = qp[1];
+  Out out{Q, ldq, L, ldl, P, ldp};
+  return pl.finish_learned(A, qp[0], qp[1], out, d_info, d_diag, st) == cudaSuccess ? RQLP_OK : RQLP_ERR_CUDA;
 }
 
 const char* rqlp_status_string(int status) {

@@ -23,6 +23,11 @@ __all__ = ["load", "RqlpError", "rqlp_default_opts", "rqlp_workspace_bytes", "rq
 PREC_FP32 = 0
 PREC_BF16X3 = 1
 MAX_D = 256
+MLP_FEATURES = 13
+MLP_HIDDEN = 64
+MLP_PARAMS = 5576
+Q_CHOICES = (0, 1, 2, 3, 4)
+P_CHOICES = (5, 10, 20)
 STATUS = {0: "RQLP_OK", 1: "RQLP_ERR_ARG", 2: "RQLP_ERR_CUDA", 3: "RQLP_ERR_BREAKDOWN",
           4: "RQLP_ERR_NONFINITE", 5: "RQLP_ERR_TIMEOUT", 6: "RQLP_ERR_WORKSPACE",
           7: "RQLP_ERR_UNSUPPORTED"}
@@ -30,7 +35,9 @@ STATUS = {0: "RQLP_OK", 1: "RQLP_ERR_ARG", 2: "RQLP_ERR_CUDA", 3: "RQLP_ERR_BREA
 # Every symbol include/rqlp.h declares (checked by the ABI test).
 EXPORTED = ["rqlp_default_opts", "rqlp_workspace_bytes", "rqlp_factor", "rqlp_host_workspace_bytes",
             "rqlp_factor_host", "rqlp_factor_noalloc", "rqlp_sketch_workspace_bytes", "rqlp_sketch",
-            "rqlp_orth_workspace_bytes", "rqlp_orth", "rqlp_kernel_launches", "rqlp_profile_enable",
+            "rqlp_orth_workspace_bytes", "rqlp_orth", "rqlp_mlp_forward", "rqlp_mlp_workspace_bytes",
+            "rqlp_mlp_grad", "rqlp_mlp_adam", "rqlp_learned_workspace_bytes", "rqlp_probe_features",
+            "rqlp_predict_qp", "rqlp_factor_learned", "rqlp_kernel_launches", "rqlp_profile_enable",
             "rqlp_profile_read", "rqlp_status_string", "rqlp_version"]
 
 
@@ -74,6 +81,27 @@ def _declare(lib):
     lib.rqlp_orth_workspace_bytes.restype = _sz
     lib.rqlp_orth.argtypes = [_vp, _i64, _int, _i64, _vp, _i64, _vp, _sz, _vp, ctypes.POINTER(Opts), _vp]
     lib.rqlp_orth.restype = _int
+    _f = ctypes.c_float
+    lib.rqlp_mlp_forward.argtypes = [_vp, _vp, _int, _vp, _vp]
+    lib.rqlp_mlp_forward.restype = _int
+    lib.rqlp_mlp_workspace_bytes.argtypes = [_int]
+    lib.rqlp_mlp_workspace_bytes.restype = _sz
+    lib.rqlp_mlp_grad.argtypes = [_vp, _vp, _vp, _vp, _int, _vp, _vp, _vp, _sz, _vp]
+    lib.rqlp_mlp_grad.restype = _int
+    lib.rqlp_mlp_adam.argtypes = [_vp, _vp, _vp, _vp, _int, _f, _f, _f, _f, _int, _vp]
+    lib.rqlp_mlp_adam.restype = _int
+    lib.rqlp_learned_workspace_bytes.argtypes = [_i64, _i64, _int, ctypes.POINTER(Opts)]
+    lib.rqlp_learned_workspace_bytes.restype = _sz
+    _d = ctypes.c_double
+    lib.rqlp_probe_features.argtypes = [_vp, _i64, _i64, _i64, _int, _vp, _i64, _d, _vp, _vp, _sz, _vp,
+                                        ctypes.POINTER(Opts), _vp]
+    lib.rqlp_probe_features.restype = _int
+    lib.rqlp_predict_qp.argtypes = [_vp, _i64, _i64, _i64, _int, _vp, _i64, _d, _vp, _vp, _vp, _sz, _vp,
+                                    ctypes.POINTER(Opts), _vp]
+    lib.rqlp_predict_qp.restype = _int
+    lib.rqlp_factor_learned.argtypes = [_vp, _i64, _i64, _i64, _int, _vp, _i64, _d, _vp, _vp, _i64, _vp, _i64,
+                                        _vp, _i64, _vp, _sz, _vp, _vp, _vp, ctypes.POINTER(Opts), _vp]
+    lib.rqlp_factor_learned.restype = _int
     lib.rqlp_kernel_launches.argtypes = []
     lib.rqlp_kernel_launches.restype = ctypes.c_ulonglong
     lib.rqlp_profile_enable.argtypes = [_int]
@@ -167,6 +195,43 @@ def rqlp_orth_workspace_bytes(rows, d, opts=None):
 def rqlp_orth(X, rows, d, ldx, R, ldr, workspace, ws_bytes, d_info, opts, stream):
     return int(load().rqlp_orth(X, rows, d, ldx, R, ldr, workspace, ws_bytes, d_info,
                                 ctypes.byref(opts) if opts is not None else None, stream))
+
+
+def rqlp_mlp_forward(params, X, batch, logits, stream):
+    return int(load().rqlp_mlp_forward(params, X, batch, logits, stream))
+
+
+def rqlp_mlp_workspace_bytes(batch):
+    return int(load().rqlp_mlp_workspace_bytes(batch))
+
+
+def rqlp_mlp_grad(params, X, yq, yp, batch, grad, loss, workspace, ws_bytes, stream):
+    return int(load().rqlp_mlp_grad(params, X, yq, yp, batch, grad, loss, workspace, ws_bytes, stream))
+
+
+def rqlp_mlp_adam(params, grad, m1, m2, n, lr, beta1, beta2, eps, step, stream):
+    return int(load().rqlp_mlp_adam(params, grad, m1, m2, n, lr, beta1, beta2, eps, step, stream))
+
+
+def rqlp_learned_workspace_bytes(m, n, k, opts=None):
+    return int(load().rqlp_learned_workspace_bytes(m, n, k, ctypes.byref(opts or _opts())))
+
+
+def rqlp_probe_features(A, m, n, lda, k, Omega, ldo, target, feat, workspace, ws_bytes, d_info, opts, stream):
+    return int(load().rqlp_probe_features(A, m, n, lda, k, Omega, ldo, target, feat, workspace, ws_bytes, d_info,
+                                          ctypes.byref(opts) if opts is not None else None, stream))
+
+
+def rqlp_predict_qp(A, m, n, lda, k, Omega, ldo, target, params, d_qp, workspace, ws_bytes, d_info, opts, stream):
+    return int(load().rqlp_predict_qp(A, m, n, lda, k, Omega, ldo, target, params, d_qp, workspace, ws_bytes,
+                                      d_info, ctypes.byref(opts) if opts is not None else None, stream))
+
+
+def rqlp_factor_learned(A, m, n, lda, k, Omega, ldo, target, params, Q, ldq, L, ldl, P, ldp, workspace, ws_bytes,
+                        d_info, d_diag, h_qp, opts, stream):
+    return int(load().rqlp_factor_learned(A, m, n, lda, k, Omega, ldo, target, params, Q, ldq, L, ldl, P, ldp,
+                                          workspace, ws_bytes, d_info, d_diag, h_qp,
+                                          ctypes.byref(opts) if opts is not None else None, stream))
 
 
 def rqlp_kernel_launches():
@@ -282,6 +347,58 @@ def orth(X, small_fp64=False):
     if st != 0:
         raise RqlpError(st, "rqlp_orth")
     return X, R, info, buf
+
+
+def probe_features(A, k, Omega, target, precision=PREC_BF16X3, workspace=None):
+    """Probe features (13 floats, CUDA tensor; the last is log10(target)) of A
+    with Omega (m x (k+20))."""
+    import torch
+    m, n = A.shape
+    opts = _opts(precision)
+    nb = rqlp_learned_workspace_bytes(m, n, k, opts)
+    if nb == 0:
+        raise RqlpError(1, "rqlp_learned_workspace_bytes")
+    if workspace is None or workspace.numel() < nb + 256:
+        workspace = torch.empty(nb + 256, dtype=torch.uint8, device=A.device)
+    ws = (workspace.data_ptr() + 255) // 256 * 256
+    feat = torch.empty(MLP_FEATURES, dtype=torch.float32, device=A.device)
+    info = torch.empty(2, dtype=torch.int32, device=A.device)
+    st = rqlp_probe_features(A.data_ptr(), m, n, A.stride(0), k, Omega.data_ptr(), Omega.stride(0), float(target),
+                             feat.data_ptr(), ws, nb, info.data_ptr(), opts, _stream())
+    if st != 0:
+        raise RqlpError(st, "rqlp_probe_features")
+    return feat, info
+
+
+def factor_learned(A, k, Omega, params, target, precision=PREC_BF16X3, workspace=None, out=None):
+    """Rand-QLP with the (q, p) predicted for the requested excess rank-k
+    error ``target``. Returns (Q, L, P, info, diag, (q, p)); Q, L, P are views
+    of k + p columns of buffers sized for k + 20."""
+    import torch
+    m, n = A.shape
+    dmax = k + 20
+    opts = _opts(precision)
+    nb = rqlp_learned_workspace_bytes(m, n, k, opts)
+    if nb == 0:
+        raise RqlpError(1, "rqlp_learned_workspace_bytes")
+    dev = A.device
+    if workspace is None or workspace.numel() < nb + 256:
+        workspace = torch.empty(nb + 256, dtype=torch.uint8, device=dev)
+    ws = (workspace.data_ptr() + 255) // 256 * 256
+    if out is None:
+        out = (torch.empty(m, dmax, device=dev), torch.empty(dmax, dmax, device=dev),
+               torch.empty(n, dmax, device=dev), torch.empty(2, dtype=torch.int32, device=dev),
+               torch.empty(4, dtype=torch.float64, device=dev))
+    Q, L, P, info, diag = out
+    qp = (ctypes.c_int * 2)()
+    st = rqlp_factor_learned(A.data_ptr(), m, n, A.stride(0), k, Omega.data_ptr(), Omega.stride(0), float(target),
+                             params.data_ptr(), Q.data_ptr(), Q.stride(0), L.data_ptr(), L.stride(0),
+                             P.data_ptr(), P.stride(0), ws, nb, info.data_ptr(), diag.data_ptr(),
+                             ctypes.addressof(qp), opts, _stream())
+    if st != 0:
+        raise RqlpError(st, "rqlp_factor_learned")
+    d = k + qp[1]
+    return Q[:, :d], L[:d, :d], P[:, :d], info, diag, (qp[0], qp[1])
 
 
 def factor_host(A, k, p, q, Omega, precision=PREC_FP32, workspace=None, out=None):

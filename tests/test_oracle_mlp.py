@@ -13,7 +13,7 @@ def _theta(seed, scale=0.3):
 
 
 def test_param_count():
-    assert mo.n_params() == 12 * 64 + 64 + 64 * 64 + 64 + 64 * 8 + 8 == 5512
+    assert mo.n_params() == 13 * 64 + 64 + 64 * 64 + 64 + 64 * 8 + 8 == 5576
 
 
 def test_zero_network_loss_is_log5_plus_log3():
@@ -52,11 +52,11 @@ def test_first_adam_step_is_lr_times_sign():
 def test_features_of_geometric_diagonal():
     rho, k, w = 0.8, 30, 50
     r = rho ** np.arange(w)
-    f = mo.probe_features(r, k, 400, 300)
+    f = mo.probe_features(r, k, 400, 300, 2e-3)
     lg = np.log10(rho)
     h = (k + 1) // 2
     expect = [(k - 1) * lg, (h - 1) * lg, (k - h) * lg, lg, 5 * lg, 10 * lg, 20 * lg, 10 * lg, 0.0,
-              np.log10(k), np.log10(300), k / 300]
+              np.log10(k), np.log10(300), k / 300, np.log10(2e-3)]
     assert np.allclose(f, expect, atol=1e-12)
 
 
