@@ -236,6 +236,60 @@ rqlp_status rqlp_factor_learned(const float* A, int64_t m, int64_t n, int64_t ld
                                 void* workspace, size_t ws_bytes, int* d_info, double* d_diag,
                                 int* h_qp, const rqlp_opts* opts, void* stream);
 
+/* ---- Batched form: many independent problems, each with its own sizes,
+ * k, p and buffers (one q for the batch), factored by the chain of
+ * rqlp_factor in plain FP32 (RQLP_PREC_BF16X3 -> RQLP_ERR_UNSUPPORTED).
+ *
+ * A batch plan is built once on the host: it lays out the caller's
+ * workspace, writes the per-problem job tables into it (one synchronous
+ * copy on `stream` at creation) and fixes the launch sequence. Each step of
+ * the chain is one grouped launch over all problems; rqlp_batch_launch
+ * captures the sequence into a CUDA graph on first use and replays it as
+ * one launch (stream-ordered, no host synchronisation). The plan is bound to
+ * the buffers it was created with; the problems' matrices may change
+ * between launches, their addresses and sizes may not.
+ *
+ * Problems: A (m x n, lda >= n), Omega (m x (k+p), ldo >= k+p), outputs as
+ * in rqlp_factor; 1 <= k, p >= 0, d = k + p <= min(m, n) and
+ * d <= RQLP_BATCH_MAX_D, else RQLP_ERR_ARG. d_info: 2 device ints per
+ * problem (caller's order), d_diag: 4 device doubles per problem (optional),
+ * laid out as for rqlp_factor.
+ *
+ * rqlp_batch_autotune times every tile configuration of each grouped
+ * product shape (tall A^T X, tall A X, Gram, X R^{-1}, d x d) and width
+ * bucket (d <= 32, d > 32) on the plan's own problems, keeps the fastest and
+ * remembers the choice for later plans with the same size mix (process
+ * wide). It runs products out of order on the workspace: run it before the
+ * batch is launched, then launch. rqlp_batch_tuning writes the chosen
+ * configuration ids (shape-major, 2 buckets per shape) and returns their
+ * count. */
+#define RQLP_BATCH_MAX_D 128
+typedef struct {
+  const float* A; int64_t m, n, lda;
+  const float* Omega; int64_t ldo;
+  int k, p;
+  float* Q; int64_t ldq;
+  float* L; int64_t ldl;
+  float* P; int64_t ldp;
+} rqlp_problem;
+typedef struct rqlp_batch_s* rqlp_batch;
+
+size_t rqlp_batch_workspace_bytes(int count, const rqlp_problem* probs, int q, const rqlp_opts* opts);
+rqlp_status rqlp_batch_create(int count, const rqlp_problem* probs, int q, void* workspace,
+                              size_t ws_bytes, int* d_info, double* d_diag, const rqlp_opts* opts,
+                              void* stream, rqlp_batch* out);
+rqlp_status rqlp_batch_autotune(rqlp_batch batch, int reps, void* stream);
+int rqlp_batch_tuning(rqlp_batch batch, int* cfg, int cap);
+/* Plain launches of the whole sequence (no graph). */
+rqlp_status rqlp_batch_run(rqlp_batch batch, void* stream);
+/* The sequence as one graph launch (captured on first use). */
+rqlp_status rqlp_batch_launch(rqlp_batch batch, void* stream);
+rqlp_status rqlp_batch_destroy(rqlp_batch batch);
+/* create + launch + synchronise + destroy. */
+rqlp_status rqlp_factor_batched(int count, const rqlp_problem* probs, int q, void* workspace,
+                                size_t ws_bytes, int* d_info, double* d_diag, const rqlp_opts* opts,
+                                void* stream);
+
 /* ---- Runtime services (host only; no device memory).
  *
  * rqlp_kernel_launches: cumulative number of CUDA kernels this library has

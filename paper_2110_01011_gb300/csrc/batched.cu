@@ -1,0 +1,662 @@
+// Batched Rand-QLP: many independent problems, each with its own sizes,
+// k, p and buffers (one q for the batch), factored by the same chain as
+// rqlp_factor (Algorithm 1 steps 3-5 with q power passes, truncated to
+// d = k + p columns, CholeskyQR orthonormalisations) in plain FP32.
+//
+// Every step of the chain is one grouped launch over all problems: the
+// products are persistent grouped GEMMs over a flattened tile list, the
+// Choleskys one CTA per problem, the small steps one CTA per problem. Stage
+// boundaries are kernel boundaries, so no kernel waits on another. The
+// launch sequence is fixed at plan creation (gates are device flags), so it
+// is captured once into a CUDA graph and replayed as one launch.
+//
+// Problems are grouped into two width buckets (d <= 32, d > 32); each GEMM
+// stage runs one launch per non-empty bucket with the tile configuration
+// that the autotuner picked for its (product shape, bucket).
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+
+namespace rqlp {
+namespace {
+
+// Product shapes the tuner distinguishes.
+enum Shape { kTallT = 0, kTallN = 1, kGram = 2, kTrmm = 3, kSmall = 4, kShapes = 5 };
+constexpr int kBuckets = 2;
+constexpr int kGates = 4;
+
+int bucket_of(int d) { return d <= 32 ? 0 : 1; }
+
+int default_cfg(int shape, int bucket) {
+  switch (shape) {
+    case kTallT:
+    case kTallN:
+    case kTrmm: return bucket == 0 ? 2 : 0;
+    case kGram: return bucket == 0 ? 4 : 5;
+    default: return 4;
+  }
+}
+
+// Per-problem device buffers (in the workspace).
+struct Bufs {
+  float *Y, *Z, *Pt, *T1, *G, *R[3], *Ri[3], *Ra, *Rb, *Rh, *Ts, *Ts2, *Ph;
+  double* scal;
+  int* gates;
+  int64_t ld;
+};
+
+struct GemmStage {
+  bool transA;
+  int shape;
+  size_t jobs_off;                           // GroupGemm[count] (bucket order)
+  size_t tiles_off[kBuckets][kGroupCfgs];    // int[cnt_b + 1] per bucket and cfg
+  int total[kBuckets][kGroupCfgs];
+  bool gated;
+};
+
+struct Stage {
+  enum Kind { kInit, kGemm, kChol, kTranspose, kWriteL, kFinish } kind;
+  int gemm = -1;         // index into gemms
+  size_t jobs_off = 0;   // CholJob[] or SmallJob[]
+};
+
+}  // namespace
+}  // namespace rqlp
+
+struct rqlp_batch_s {
+  int count = 0, q = 0, dmax = 0;
+  long long sums[rqlp::kBuckets][3] = {};    // per bucket: sum of m, n, d (tuning key)
+  int cnt[rqlp::kBuckets] = {0, 0};          // problems per bucket (bucket 0 first)
+  rqlp_opts opts{};
+  char* dev = nullptr;                       // plan area in the workspace
+  std::vector<rqlp::Stage> stages;
+  std::vector<rqlp::GemmStage> gemms;
+  int cfg[rqlp::kShapes][rqlp::kBuckets];
+  cudaStream_t cap = nullptr;                // capture stream
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  long long graph_kernels = 0;
+};
+
+namespace rqlp {
+namespace {
+
+std::mutex g_tune_mu;
+std::map<std::vector<long long>, std::vector<int>> g_tuned;   // plan signature -> cfg table
+
+std::vector<long long> signature(const rqlp_batch_s* b) {
+  // Per bucket: count and the sums of m, n, d (the tuner's choice depends on
+  // the size mix, not on the exact problems).
+  std::vector<long long> s = {b->q, b->opts.small_fp64};
+  for (int bk = 0; bk < kBuckets; ++bk) {
+    s.push_back(b->cnt[bk]);
+    for (int t = 0; t < 3; ++t) s.push_back(b->sums[bk][t]);
+  }
+  return s;
+}
+
+// Host staging of the plan area; offsets are 256-byte aligned.
+struct Stager {
+  std::vector<char> h;
+  template <typename T>
+  size_t put(const T* p, size_t n) {
+    size_t off = (size_t)round_up((int64_t)h.size(), 256);
+    h.resize(off + n * sizeof(T));
+    if (n) std::memcpy(h.data() + off, p, n * sizeof(T));
+    return off;
+  }
+};
+
+struct Builder {
+  rqlp_batch_s* b;
+  const std::vector<rqlp_problem>& pr;   // bucket order
+  const std::vector<Bufs>& bf;
+  const std::vector<int>& orig;          // caller's index of each position
+  int* info;                             // caller order, 2 ints per problem
+  double* diag;                          // caller order, 4 doubles (optional)
+  Stager& sg;
+
+  int* info_of(int i) const { return info + 2 * (int64_t)orig[i]; }
+
+  int n() const { return (int)pr.size(); }
+  int d(int i) const { return pr[i].k + pr[i].p; }
+
+  void gemm(bool transA, int shape, const std::vector<GroupGemm>& jobs, bool gated) {
+    GemmStage g{};
+    g.transA = transA;
+    g.shape = shape;
+    g.gated = gated;
+    g.jobs_off = sg.put(jobs.data(), jobs.size());
+    int lo = 0;
+    for (int bk = 0; bk < kBuckets; ++bk) {
+      const int c = b->cnt[bk];
+      for (int cfg = 0; cfg < kGroupCfgs; ++cfg) {
+        int bm, bn;
+        grouped_tile(cfg, &bm, &bn);
+        std::vector<int> ts(c + 1, 0);
+        for (int i = 0; i < c; ++i) {
+          const GroupGemm& j = jobs[lo + i];
+          const int64_t t = (j.M > 0 && j.N > 0) ? cdiv(j.M, bm) * cdiv(j.N, bn) : 0;
+          ts[i + 1] = ts[i] + (int)t;
+        }
+        g.tiles_off[bk][cfg] = sg.put(ts.data(), ts.size());
+        g.total[bk][cfg] = ts[c];
+      }
+      lo += c;
+    }
+    Stage s;
+    s.kind = Stage::kGemm;
+    s.gemm = (int)b->gemms.size();
+    b->gemms.push_back(g);
+    b->stages.push_back(s);
+  }
+  void chol(const std::vector<CholJob>& jobs) {
+    Stage s;
+    s.kind = Stage::kChol;
+    s.jobs_off = sg.put(jobs.data(), jobs.size());
+    b->stages.push_back(s);
+  }
+  void small(Stage::Kind kind, const std::vector<SmallJob>& jobs) {
+    Stage s;
+    s.kind = kind;
+    s.jobs_off = sg.put(jobs.data(), jobs.size());
+    b->stages.push_back(s);
+  }
+
+  GroupGemm job(const float* A, int64_t lda, const float* B, int64_t ldb, float* C, int64_t ldc, int64_t M,
+                int64_t N, int64_t K) {
+    GroupGemm j{};
+    j.A = A; j.lda = lda; j.B = B; j.ldb = ldb; j.C = C; j.ldc = ldc;
+    j.M = M; j.N = N; j.K = K;
+    return j;
+  }
+
+  // G = X^T X over `rows(i)` rows.
+  template <typename XF, typename RF>
+  void gram(XF X, RF rows, int shape, int gate_slot) {
+    std::vector<GroupGemm> js;
+    for (int i = 0; i < n(); ++i) {
+      GroupGemm j = job(X(i), bf[i].ld, X(i), bf[i].ld, bf[i].G, bf[i].ld, d(i), d(i), rows(i));
+      if (gate_slot >= 0) {
+        j.gate = &bf[i].gates[gate_slot];
+        j.gate_mode = kGateSkip;
+      }
+      js.push_back(j);
+    }
+    gemm(true, shape, js, gate_slot >= 0);
+  }
+  void cholesky(int slot, int gate_out, int gate_in) {
+    std::vector<CholJob> js;
+    for (int i = 0; i < n(); ++i) {
+      CholJob j{};
+      j.d = d(i);
+      j.G = bf[i].G; j.ldg = bf[i].ld;
+      j.R = bf[i].R[slot]; j.Rinv = bf[i].Ri[slot]; j.ldr = bf[i].ld;
+      j.info = info_of(i);
+      j.shift_count = &bf[i].scal[2];
+      j.gate_out = gate_out >= 0 ? &bf[i].gates[gate_out] : nullptr;
+      j.gate_in = gate_in >= 0 ? &bf[i].gates[gate_in] : nullptr;
+      js.push_back(j);
+    }
+    chol(js);
+  }
+  // out = X R_slot^{-1}; gate_slot >= 0: out = X when that gate is 0.
+  template <typename XF, typename OF, typename LF, typename RF>
+  void trmm(XF X, OF out, LF ldout, RF rows, int slot, int shape, int gate_slot) {
+    std::vector<GroupGemm> js;
+    for (int i = 0; i < n(); ++i) {
+      GroupGemm j = job(X(i), bf[i].ld, bf[i].Ri[slot], bf[i].ld, out(i), ldout(i), rows(i), d(i), d(i));
+      j.b_upper = 1;
+      if (gate_slot >= 0) {
+        j.gate = &bf[i].gates[gate_slot];
+        j.gate_mode = kGateCopy;
+      }
+      js.push_back(j);
+    }
+    gemm(false, shape, js, gate_slot >= 0);
+  }
+  // One CholeskyQR pass: out = X R^{-1} (slot 0).
+  template <typename XF, typename OF, typename RF>
+  void orth_inter(XF X, OF out, RF rows, bool tall) {
+    gram(X, rows, tall ? kGram : kSmall, -1);
+    cholesky(0, -1, -1);
+    trmm(X, out, [&](int i) { return bf[i].ld; }, rows, 0, tall ? kTrmm : kSmall, -1);
+  }
+  // CholeskyQR2 plus a third pass gated on a shifted Cholesky; X is
+  // overwritten; Racc (optional) receives R3 R2 R1.
+  template <typename XF, typename OF, typename LF, typename TF, typename RF, typename AF>
+  void orth_final(XF X, OF out, LF ldout, TF tmp, RF rows, bool tall, int g, AF Racc, bool with_r) {
+    const int gs = tall ? kGram : kSmall, ts = tall ? kTrmm : kSmall;
+    auto ld = [&](int i) { return bf[i].ld; };
+    gram(X, rows, gs, -1);
+    cholesky(0, g, -1);
+    trmm(X, tmp, ld, rows, 0, ts, -1);
+    gram(tmp, rows, gs, -1);
+    cholesky(1, g, -1);
+    trmm(tmp, X, ld, rows, 1, ts, -1);
+    gram(X, rows, gs, g);
+    cholesky(2, -1, g);
+    trmm(X, out, ldout, rows, 2, ts, g);
+    if (with_r) {
+      std::vector<GroupGemm> a, c;
+      for (int i = 0; i < n(); ++i) {
+        GroupGemm j = job(bf[i].R[1], bf[i].ld, bf[i].R[0], bf[i].ld, bf[i].Ra, bf[i].ld, d(i), d(i), d(i));
+        j.b_upper = 1;
+        a.push_back(j);
+        GroupGemm k2 = job(bf[i].R[2], bf[i].ld, bf[i].Ra, bf[i].ld, Racc(i), bf[i].ld, d(i), d(i), d(i));
+        k2.b_upper = 1;
+        c.push_back(k2);
+      }
+      gemm(false, kSmall, a, false);
+      gemm(false, kSmall, c, false);
+    }
+  }
+
+  void build() {
+    const int q = b->q;
+    auto ld = [&](int i) { return bf[i].ld; };
+    auto rows_n = [&](int i) { return (int64_t)pr[i].n; };
+    auto rows_m = [&](int i) { return (int64_t)pr[i].m; };
+    auto rows_d = [&](int i) { return (int64_t)d(i); };
+    auto Y = [&](int i) { return bf[i].Y; };
+    auto Z = [&](int i) { return bf[i].Z; };
+    auto Pt = [&](int i) { return bf[i].Pt; };
+    auto T1 = [&](int i) { return bf[i].T1; };
+    auto none = [&](int) { return (float*)nullptr; };
+
+    std::vector<SmallJob> sj;
+    for (int i = 0; i < n(); ++i) {
+      SmallJob j{};
+      j.d = d(i);
+      j.scal = bf[i].scal;
+      j.info = info_of(i);
+      j.diag = diag != nullptr ? diag + 4 * (int64_t)orig[i] : nullptr;
+      j.gates = bf[i].gates;
+      j.ngates = kGates;
+      sj.push_back(j);
+    }
+    small(Stage::kInit, sj);
+
+    // Y = A^T Omega (Algorithm 1 step 3); ||A||_F^2 rides along.
+    {
+      std::vector<GroupGemm> js;
+      for (int i = 0; i < n(); ++i) {
+        GroupGemm j = job(pr[i].A, pr[i].lda, pr[i].Omega, pr[i].ldo, bf[i].Y, bf[i].ld, pr[i].n, d(i), pr[i].m);
+        j.sumsq = &bf[i].scal[0];
+        js.push_back(j);
+      }
+      gemm(true, kTallT, js, false);
+    }
+    auto passN = [&](auto X, auto out) {   // out (m x d) = A X
+      std::vector<GroupGemm> js;
+      for (int i = 0; i < n(); ++i)
+        js.push_back(job(pr[i].A, pr[i].lda, X(i), bf[i].ld, out(i), bf[i].ld, pr[i].m, d(i), pr[i].n));
+      gemm(false, kTallN, js, false);
+    };
+    auto passT = [&](auto X, auto out) {   // out (n x d) = A^T X
+      std::vector<GroupGemm> js;
+      for (int i = 0; i < n(); ++i)
+        js.push_back(job(pr[i].A, pr[i].lda, X(i), bf[i].ld, out(i), bf[i].ld, pr[i].n, d(i), pr[i].m));
+      gemm(true, kTallT, js, false);
+    };
+
+    if (q == 0) orth_final(Y, Pt, ld, T1, rows_n, true, 0, none, false);
+    else orth_inter(Y, Pt, rows_n, true);
+    for (int it = 1; it <= q; ++it) {
+      passN(Pt, Z);                          // Z = A P~
+      orth_inter(Z, T1, rows_m, true);       // Z = qf(Z), one pass
+      passT(T1, Y);                          // Y = A^T Z
+      if (it == q) orth_final(Y, Pt, ld, T1, rows_n, true, 0, none, false);
+      else orth_inter(Y, Pt, rows_n, true);
+    }
+    // (Q, R) = qr(A P~)  (Algorithm 1 step 4)
+    passN(Pt, Z);
+    orth_final(Z, [&](int i) { return pr[i].Q; }, [&](int i) { return pr[i].ldq; }, T1, rows_m, true, 1,
+               [&](int i) { return bf[i].Rb; }, true);
+    // (P^, R^) = qr(R^T), L = R^^T  (step 5 applied to the d x d factor)
+    std::vector<SmallJob> tj = sj;
+    for (int i = 0; i < n(); ++i) {
+      tj[i].X = bf[i].Rb; tj[i].ldx = bf[i].ld;
+      tj[i].Y = bf[i].Ts; tj[i].ldy = bf[i].ld;
+    }
+    small(Stage::kTranspose, tj);
+    orth_final([&](int i) { return bf[i].Ts; }, [&](int i) { return bf[i].Ph; }, ld,
+               [&](int i) { return bf[i].Ts2; }, rows_d, false, 2, [&](int i) { return bf[i].Rh; }, true);
+    std::vector<SmallJob> lj = sj;
+    for (int i = 0; i < n(); ++i) {
+      lj[i].X = bf[i].Rh; lj[i].ldx = bf[i].ld;
+      lj[i].Y = pr[i].L; lj[i].ldy = pr[i].ldl;
+    }
+    small(Stage::kWriteL, lj);
+    // P = P~ P^
+    {
+      std::vector<GroupGemm> js;
+      for (int i = 0; i < n(); ++i)
+        js.push_back(job(bf[i].Pt, bf[i].ld, bf[i].Ph, bf[i].ld, pr[i].P, pr[i].ldp, pr[i].n, d(i), d(i)));
+      gemm(false, kTrmm, js, false);
+    }
+    small(Stage::kFinish, sj);
+  }
+};
+
+Bufs take_bufs(Arena& ar, const rqlp_problem& p) {
+  Bufs f{};
+  const int d = p.k + p.p;
+  f.ld = round_up(d, 4);
+  const int64_t dd = (int64_t)d * f.ld, tall = std::max(p.m, p.n);
+  f.Y = ar.take<float>(p.n * f.ld);
+  f.Z = ar.take<float>(p.m * f.ld);
+  f.Pt = ar.take<float>(p.n * f.ld);
+  f.T1 = ar.take<float>(tall * f.ld);
+  f.G = ar.take<float>(dd);
+  for (int s = 0; s < 3; ++s) {
+    f.R[s] = ar.take<float>(dd);
+    f.Ri[s] = ar.take<float>(dd);
+  }
+  f.Ra = ar.take<float>(dd);
+  f.Rb = ar.take<float>(dd);
+  f.Rh = ar.take<float>(dd);
+  f.Ts = ar.take<float>(dd);
+  f.Ts2 = ar.take<float>(dd);
+  f.Ph = ar.take<float>(dd);
+  f.scal = ar.take<double>(4);
+  f.gates = ar.take<int>(kGates);
+  return f;
+}
+
+bool valid_problem(const rqlp_problem& p) {
+  if (p.A == nullptr || p.Omega == nullptr || p.Q == nullptr || p.L == nullptr || p.P == nullptr) return false;
+  if (p.m <= 0 || p.n <= 0 || p.k < 1 || p.p < 0) return false;
+  const int64_t d = (int64_t)p.k + p.p;
+  if (d > std::min(p.m, p.n) || d > RQLP_BATCH_MAX_D) return false;
+  return p.lda >= p.n && p.ldo >= d && p.ldq >= d && p.ldl >= d && p.ldp >= d;
+}
+
+// Bucket order: the permutation that puts the d <= 32 problems first.
+std::vector<int> bucket_order(int count, const rqlp_problem* probs, int* cnt) {
+  std::vector<int> ord;
+  cnt[0] = cnt[1] = 0;
+  for (int bk = 0; bk < kBuckets; ++bk)
+    for (int i = 0; i < count; ++i)
+      if (bucket_of(probs[i].k + probs[i].p) == bk) {
+        ord.push_back(i);
+        ++cnt[bk];
+      }
+  return ord;
+}
+
+// Lays out the workspace (per-problem buffers first, plan area last) and
+// builds the stage list into `sg`; a dry arena only measures.
+size_t layout(rqlp_batch_s* b, int count, const rqlp_problem* probs, Arena& ar, int* d_info, double* d_diag,
+              Stager& sg) {
+  std::vector<int> ord = bucket_order(count, probs, b->cnt);
+  std::vector<rqlp_problem> pr;
+  std::vector<Bufs> bf;
+  b->dmax = 0;
+  for (int bk = 0; bk < kBuckets; ++bk)
+    for (int t = 0; t < 3; ++t) b->sums[bk][t] = 0;
+  for (int i : ord) {
+    const int d = probs[i].k + probs[i].p, bk = bucket_of(d);
+    pr.push_back(probs[i]);
+    bf.push_back(take_bufs(ar, probs[i]));
+    b->dmax = std::max(b->dmax, d);
+    b->sums[bk][0] += probs[i].m;
+    b->sums[bk][1] += probs[i].n;
+    b->sums[bk][2] += d;
+  }
+  b->stages.clear();
+  b->gemms.clear();
+  Builder bd{b, pr, bf, ord, d_info, d_diag, sg};
+  bd.build();
+  char* plan = ar.take<char>(sg.h.size() + 256);
+  b->dev = ar.dry ? nullptr : plan;
+  return ar.off;
+}
+
+template <typename T>
+const T* at(const rqlp_batch_s* b, size_t off) {
+  return reinterpret_cast<const T*>(b->dev + off);
+}
+
+cudaError_t run_gemm(const rqlp_batch_s* b, const GemmStage& g, cudaStream_t st, int only_bucket = -1,
+                     int force_cfg = -1) {
+  const GroupGemm* jobs = at<GroupGemm>(b, g.jobs_off);
+  int lo = 0;
+  for (int bk = 0; bk < kBuckets; ++bk) {
+    const int c = b->cnt[bk];
+    if (c > 0 && (only_bucket < 0 || only_bucket == bk)) {
+      const int cfg = force_cfg >= 0 ? force_cfg : b->cfg[g.shape][bk];
+      CK(gemm_grouped(g.transA, cfg, jobs + lo, at<int>(b, g.tiles_off[bk][cfg]), c, g.total[bk][cfg], st));
+    }
+    lo += c;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t run_stages(const rqlp_batch_s* b, cudaStream_t st) {
+  const bool fp64 = b->opts.small_fp64 != 0;
+  for (const Stage& s : b->stages) {
+    switch (s.kind) {
+      case Stage::kInit: CK(init_batched(at<SmallJob>(b, s.jobs_off), b->count, st)); break;
+      case Stage::kGemm: CK(run_gemm(b, b->gemms[s.gemm], st)); break;
+      case Stage::kChol: CK(chol_inv_batched(at<CholJob>(b, s.jobs_off), b->count, b->dmax, fp64, st)); break;
+      case Stage::kTranspose: CK(transpose_batched(at<SmallJob>(b, s.jobs_off), b->count, st)); break;
+      case Stage::kWriteL: CK(write_L_batched(at<SmallJob>(b, s.jobs_off), b->count, st)); break;
+      case Stage::kFinish: CK(finish_diag_batched(at<SmallJob>(b, s.jobs_off), b->count, st)); break;
+    }
+  }
+  return cudaSuccess;
+}
+
+void drop_graph(rqlp_batch_s* b) {
+  if (b->exec != nullptr) cudaGraphExecDestroy(b->exec);
+  if (b->graph != nullptr) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+}
+
+rqlp_opts resolve_opts(const rqlp_opts* o) {
+  rqlp_opts r;
+  rqlp_default_opts(&r);
+  if (o != nullptr) r = *o;
+  return r;
+}
+
+bool valid_batch(int count, const rqlp_problem* probs, int q, const rqlp_opts& o) {
+  if (count <= 0 || probs == nullptr || q < 0 || q > 64) return false;
+  if (o.precision != RQLP_PREC_FP32 || (o.small_fp64 != 0 && o.small_fp64 != 1)) return false;
+  for (int i = 0; i < 6; ++i)
+    if (o.reserved[i] != 0) return false;
+  for (int i = 0; i < count; ++i)
+    if (!valid_problem(probs[i])) return false;
+  return true;
+}
+
+}  // namespace
+}  // namespace rqlp
+
+using namespace rqlp;
+
+extern "C" {
+
+size_t rqlp_batch_workspace_bytes(int count, const rqlp_problem* probs, int q, const rqlp_opts* opts) {
+  const rqlp_opts o = resolve_opts(opts);
+  if (!valid_batch(count, probs, q, o)) return 0;
+  rqlp_batch_s b;
+  b.count = count;
+  b.q = q;
+  b.opts = o;
+  Arena ar;
+  ar.dry = true;
+  Stager sg;
+  return layout(&b, count, probs, ar, nullptr, nullptr, sg);
+}
+
+rqlp_status rqlp_batch_create(int count, const rqlp_problem* probs, int q, void* workspace, size_t ws_bytes,
+                              int* d_info, double* d_diag, const rqlp_opts* opts, void* stream, rqlp_batch* out) {
+  if (out == nullptr) return RQLP_ERR_ARG;
+  *out = nullptr;
+  const rqlp_opts o = resolve_opts(opts);
+  if (o.precision != RQLP_PREC_FP32 && o.precision == RQLP_PREC_BF16X3) return RQLP_ERR_UNSUPPORTED;
+  if (!valid_batch(count, probs, q, o) || d_info == nullptr) return RQLP_ERR_ARG;
+  if (!chol_batched_fits(RQLP_BATCH_MAX_D, o.small_fp64 != 0)) return RQLP_ERR_UNSUPPORTED;
+  const size_t need = rqlp_batch_workspace_bytes(count, probs, q, &o);
+  if (workspace == nullptr || ws_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255) != 0)
+    return RQLP_ERR_WORKSPACE;
+  rqlp_batch_s* b = new (std::nothrow) rqlp_batch_s();
+  if (b == nullptr) return RQLP_ERR_CUDA;
+  b->count = count;
+  b->q = q;
+  b->opts = o;
+  Arena ar;
+  ar.base = static_cast<char*>(workspace);
+  ar.cap = ws_bytes;
+  Stager sg;
+  layout(b, count, probs, ar, d_info, d_diag, sg);
+  for (int s = 0; s < kShapes; ++s)
+    for (int bk = 0; bk < kBuckets; ++bk) b->cfg[s][bk] = default_cfg(s, bk);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find(signature(b));
+    if (it != g_tuned.end())
+      for (int s = 0; s < kShapes; ++s)
+        for (int bk = 0; bk < kBuckets; ++bk) b->cfg[s][bk] = it->second[s * kBuckets + bk];
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (gemm_grouped_prepare() != cudaSuccess ||
+      chol_inv_batched(nullptr, 0, 0, o.small_fp64 != 0, st) != cudaSuccess ||
+      cudaMemcpyAsync(b->dev, sg.h.data(), sg.h.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
+    delete b;
+    return RQLP_ERR_CUDA;
+  }
+  *out = b;
+  return RQLP_OK;
+}
+
+rqlp_status rqlp_batch_run(rqlp_batch b, void* stream) {
+  if (b == nullptr) return RQLP_ERR_ARG;
+  return run_stages(b, static_cast<cudaStream_t>(stream)) == cudaSuccess ? RQLP_OK : RQLP_ERR_CUDA;
+}
+
+rqlp_status rqlp_batch_launch(rqlp_batch b, void* stream) {
+  if (b == nullptr) return RQLP_ERR_ARG;
+  if (b->exec == nullptr) {
+    const unsigned long long before = rqlp_kernel_launches();
+    if (cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return RQLP_ERR_CUDA;
+    const cudaError_t e = run_stages(b, b->cap);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(b->cap, &g);
+    const long long captured = (long long)(rqlp_kernel_launches() - before);
+    note_launch((int)-captured);   // counted when the graph runs
+    if (e != cudaSuccess || e2 != cudaSuccess || g == nullptr) {
+      if (g != nullptr) cudaGraphDestroy(g);
+      return RQLP_ERR_CUDA;
+    }
+    if (cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) {
+      cudaGraphDestroy(g);
+      b->exec = nullptr;
+      return RQLP_ERR_CUDA;
+    }
+    b->graph = g;
+    b->graph_kernels = captured;
+  }
+  if (cudaGraphLaunch(b->exec, static_cast<cudaStream_t>(stream)) != cudaSuccess) return RQLP_ERR_CUDA;
+  note_launch((int)b->graph_kernels);
+  return RQLP_OK;
+}
+
+rqlp_status rqlp_batch_autotune(rqlp_batch b, int reps, void* stream) {
+  if (b == nullptr || reps < 1) return RQLP_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return RQLP_ERR_CUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return RQLP_ERR_CUDA;
+  }
+  rqlp_status rc = RQLP_OK;
+  // Representative stage per (shape, bucket): the first ungated one. Timing
+  // is data-independent for these FP32 products, so the workspace contents
+  // do not matter.
+  for (int shape = 0; shape < kShapes && rc == RQLP_OK; ++shape) {
+    const GemmStage* rep = nullptr;
+    for (const GemmStage& g : b->gemms)
+      if (g.shape == shape && !g.gated) {
+        rep = &g;
+        break;
+      }
+    if (rep == nullptr) continue;
+    for (int bk = 0; bk < kBuckets && rc == RQLP_OK; ++bk) {
+      if (b->cnt[bk] == 0) continue;
+      float best = 1e30f;
+      for (int cfg = 0; cfg < kGroupCfgs; ++cfg) {
+        float ms = 0.f;
+        if (run_gemm(b, *rep, st, bk, cfg) != cudaSuccess ||      // warm-up
+            cudaEventRecord(e0, st) != cudaSuccess) {
+          rc = RQLP_ERR_CUDA;
+          break;
+        }
+        for (int r = 0; r < reps; ++r)
+          if (run_gemm(b, *rep, st, bk, cfg) != cudaSuccess) rc = RQLP_ERR_CUDA;
+        if (rc != RQLP_OK || cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+          rc = RQLP_ERR_CUDA;
+          break;
+        }
+        if (ms < best) {
+          best = ms;
+          b->cfg[shape][bk] = cfg;
+        }
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != RQLP_OK) return rc;
+  drop_graph(b);   // recaptured with the new tiles on the next launch
+  std::vector<int> t(kShapes * kBuckets);
+  for (int s = 0; s < kShapes; ++s)
+    for (int bk = 0; bk < kBuckets; ++bk) t[s * kBuckets + bk] = b->cfg[s][bk];
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tuned[signature(b)] = t;
+  return RQLP_OK;
+}
+
+int rqlp_batch_tuning(rqlp_batch b, int* cfg, int cap) {
+  if (b == nullptr) return 0;
+  int n = 0;
+  for (int s = 0; s < kShapes; ++s)
+    for (int bk = 0; bk < kBuckets; ++bk) {
+      if (cfg != nullptr && n < cap) cfg[n] = b->cfg[s][bk];
+      ++n;
+    }
+  return n;
+}
+
+rqlp_status rqlp_batch_destroy(rqlp_batch b) {
+  if (b == nullptr) return RQLP_OK;
+  drop_graph(b);
+  if (b->cap != nullptr) cudaStreamDestroy(b->cap);
+  delete b;
+  return RQLP_OK;
+}
+
+rqlp_status rqlp_factor_batched(int count, const rqlp_problem* probs, int q, void* workspace, size_t ws_bytes,
+                                int* d_info, double* d_diag, const rqlp_opts* opts, void* stream) {
+  rqlp_batch b = nullptr;
+  rqlp_status s = rqlp_batch_create(count, probs, q, workspace, ws_bytes, d_info, d_diag, opts, stream, &b);
+  if (s != RQLP_OK) return s;
+  s = rqlp_batch_launch(b, stream);
+  if (s == RQLP_OK && cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) s = RQLP_ERR_CUDA;
+  rqlp_batch_destroy(b);
+  return s;
+}
+
+}  // extern "C"

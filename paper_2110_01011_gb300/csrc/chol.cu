@@ -29,6 +29,7 @@ namespace {
 constexpr int NB = 16;
 constexpr int kMaxD = RQLP_MAX_D;
 constexpr int kThreads = 512;
+constexpr int kBatchThreads = 128;
 
 template <typename T> struct Vec4;
 template <> struct Vec4<float> { using type = float4; };
@@ -68,10 +69,13 @@ __device__ void write_identity(int d, float* R, float* Rinv, int64_t ldr) {
   }
 }
 
+// The factorisation of one problem by the whole CTA (any multiple of 32
+// threads up to kThreads). gS: the square buffer in global memory, or nullptr
+// for shared memory.
 template <typename T>
-__global__ void __launch_bounds__(kThreads)
-chol_blocked_kernel(int d, const float* __restrict__ G, int64_t ldg, float* __restrict__ R, float* __restrict__ Rinv,
-                    int64_t ldr, int* info, double* shift_count, int* gate_out, const int* gate_in, T* gS) {
+__device__ __forceinline__ void chol_body(int d, const float* __restrict__ G, int64_t ldg, float* __restrict__ R,
+                                          float* __restrict__ Rinv, int64_t ldr, int* info, double* shift_count,
+                                          int* gate_out, const int* gate_in, T* gS) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int LDS = lds_of(d), PTLD = ptld_of(d);
   T* dyn = reinterpret_cast<T*>(smem_raw);
@@ -300,6 +304,23 @@ chol_blocked_kernel(int d, const float* __restrict__ G, int64_t ldg, float* __re
   }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+chol_blocked_kernel(int d, const float* __restrict__ G, int64_t ldg, float* __restrict__ R, float* __restrict__ Rinv,
+                    int64_t ldr, int* info, double* shift_count, int* gate_out, const int* gate_in, T* gS) {
+  chol_body<T>(d, G, ldg, R, Rinv, ldr, info, shift_count, gate_out, gate_in, gS);
+}
+
+// One CTA per problem of a batch; every square buffer in shared memory.
+template <typename T>
+__global__ void __launch_bounds__(kBatchThreads, 3)
+chol_batched_kernel(const CholJob* __restrict__ jobs, int count) {
+  const int b = blockIdx.x;
+  if (b >= count) return;
+  const CholJob j = jobs[b];
+  chol_body<T>(j.d, j.G, j.ldg, j.R, j.Rinv, j.ldr, j.info, j.shift_count, j.gate_out, j.gate_in, nullptr);
+}
+
 size_t smem_optin_chol() {
   static size_t v = 0;
   if (v == 0) {
@@ -343,7 +364,32 @@ cudaError_t launch(int d, const float* G, int64_t ldg, float* R, float* Rinv, in
   return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_batched(const CholJob* jobs, int count, int dmax, cudaStream_t st) {
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(chol_batched_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(smem_optin_chol() - static_bytes<T>()));
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  if (count <= 0) return cudaSuccess;   // configuration only
+  if (!square_in_smem<T>(dmax)) return cudaErrorInvalidValue;
+  const size_t dyn = panel_bytes<T>(dmax) + square_bytes<T>(dmax);
+  chol_batched_kernel<T><<<count, kBatchThreads, dyn, st>>>(jobs, count);
+  note_launch();
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+bool chol_batched_fits(int dmax, bool fp64) {
+  return fp64 ? square_in_smem<double>(dmax) : square_in_smem<float>(dmax);
+}
+
+cudaError_t chol_inv_batched(const CholJob* jobs, int count, int dmax, bool fp64, cudaStream_t st) {
+  return fp64 ? launch_batched<double>(jobs, count, dmax, st) : launch_batched<float>(jobs, count, dmax, st);
+}
 
 size_t chol_global_bytes(int d, bool fp64) {
   if (fp64) return square_in_smem<double>(d) ? 0 : square_bytes<double>(d);

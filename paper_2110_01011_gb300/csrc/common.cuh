@@ -7,6 +7,13 @@
 
 #include "../../include/rqlp.h"
 
+// Return the CUDA error of x from the enclosing function.
+#define CK(x)                         \
+  do {                                \
+    cudaError_t e_ = (x);             \
+    if (e_ != cudaSuccess) return e_; \
+  } while (0)
+
 namespace rqlp {
 
 // Round x up to a multiple of a (a > 0); ceil(x / a).
@@ -55,6 +62,26 @@ cudaError_t gemm_f32_ex(bool transA, int64_t M, int64_t N, int64_t K, const floa
 int gemm_f32_splits(int64_t M, int64_t N, int64_t K);
 size_t gemm_f32_part_floats(int64_t M, int64_t N, int64_t K);
 
+// Grouped form for batches: one launch covers job b = 0..count-1, C_b =
+// op(A_b) B_b, each with its own sizes, gate and options (no split-K).
+// tile_start (device, count + 1 ints): exclusive prefix sum of the per-job
+// tile counts cdiv(M, BM) * cdiv(N, BN) for the configuration's tile.
+struct GroupGemm {
+  const float* A; const float* B; float* C;
+  int64_t lda, ldb, ldc;
+  int64_t M, N, K;
+  double* sumsq;
+  const int* gate;
+  int gate_mode;
+  int b_upper;
+};
+constexpr int kGroupCfgs = 6;
+void grouped_tile(int cfg, int* bm, int* bn);
+cudaError_t gemm_grouped(bool transA, int cfg, const GroupGemm* jobs, const int* tile_start, int count,
+                         int total_tiles, cudaStream_t st);
+// Runs every one-time query of the grouped kernels (call before capturing).
+cudaError_t gemm_grouped_prepare();
+
 // ---------------------------------------------------------------- d x d kernels
 // R^T R = G (+ s I on breakdown; raises *gate_out), Rinv = R^{-1}; gate_in == 0
 // -> R = Rinv = I. gstore: global scratch when the factor does not fit in
@@ -63,6 +90,30 @@ cudaError_t chol_inv(int d, const float* G, int64_t ldg, float* R, float* Rinv, 
                      double* shift_count, int* gate_out, const int* gate_in, void* gstore, bool fp64,
                      cudaStream_t st);
 size_t chol_global_bytes(int d, bool fp64);
+// One CTA per job; every factor in shared memory (chol_batched_fits(dmax)).
+struct CholJob {
+  int d;
+  const float* G; int64_t ldg;
+  float* R; float* Rinv; int64_t ldr;
+  int* info; double* shift_count; int* gate_out; const int* gate_in;
+};
+bool chol_batched_fits(int dmax, bool fp64);
+cudaError_t chol_inv_batched(const CholJob* jobs, int count, int dmax, bool fp64, cudaStream_t st);
+// count == 0 only configures the kernel (call before capturing).
+// Batched small steps, one CTA per job.
+struct SmallJob {
+  int d;
+  const float* X; int64_t ldx;   // transpose: source; write_L: Rhat
+  float* Y; int64_t ldy;         // transpose: destination; write_L: L
+  double* scal;                  // the job's scalars [||A||^2, ||L||^2, shifts, -]
+  int* info;
+  double* diag;                  // optional output (4 doubles)
+  int* gates; int ngates;
+};
+cudaError_t init_batched(const SmallJob* jobs, int count, cudaStream_t st);
+cudaError_t transpose_batched(const SmallJob* jobs, int count, cudaStream_t st);
+cudaError_t write_L_batched(const SmallJob* jobs, int count, cudaStream_t st);
+cudaError_t finish_diag_batched(const SmallJob* jobs, int count, cudaStream_t st);
 cudaError_t transpose_small(int d, const float* X, int64_t ldx, float* Y, int64_t ldy, cudaStream_t st);
 cudaError_t write_L(int d, const float* Rh, int64_t ldrh, float* L, int64_t ldl, double* l2_accum,
                     cudaStream_t st);

@@ -27,9 +27,10 @@ struct GemmArgs {
   int b_upper;                              // B upper triangular: skip k >= n-tile end
 };
 
+// One BM x BN tile of C (rows m0.., columns n0..) over K-slice `slice`, by the
+// whole CTA.
 template <int BM, int BN, int BK, int TM, int TN, bool TRANS_A>
-__global__ void __launch_bounds__((BM / TM) * (BN / TN))
-gemm_f32_kernel(GemmArgs g) {
+__device__ __forceinline__ void gemm_tile(const GemmArgs& g, int64_t m0, int64_t n0, int slice) {
   constexpr int NT = (BM / TM) * (BN / TN);
   constexpr int TX = BN / TN;
   constexpr int AL = BM * BK / NT;
@@ -40,8 +41,7 @@ gemm_f32_kernel(GemmArgs g) {
 
   const int tid = threadIdx.x;
   const int tx = tid % TX, ty = tid / TX;
-  const int64_t m0 = (int64_t)blockIdx.y * BM, n0 = (int64_t)blockIdx.x * BN;
-  float* C = g.C + (int64_t)blockIdx.z * g.c_slice;
+  float* C = g.C + (int64_t)slice * g.c_slice;
 
   if (g.gate != nullptr && *g.gate == 0) {
     if (g.gate_mode == kGateSkip) return;
@@ -53,14 +53,14 @@ gemm_f32_kernel(GemmArgs g) {
     return;
   }
 
-  const int64_t kbeg = (int64_t)blockIdx.z * g.kchunk;
+  const int64_t kbeg = (int64_t)slice * g.kchunk;
   int64_t kend = kbeg + g.kchunk < g.K ? kbeg + g.kchunk : g.K;
   if (g.b_upper && kend > n0 + BN) kend = n0 + BN;
   const int64_t ntiles = kend > kbeg ? cdiv(kend - kbeg, BK) : 0;
 
   float ra[AL], rb[BL];
   float sq = 0.f, sq_c = 0.f;   // Kahan sum of squares of the A tiles read
-  const bool want_sq = g.sumsq != nullptr && blockIdx.x == 0;
+  const bool want_sq = g.sumsq != nullptr && n0 == 0;   // each element of A once
 
   auto load = [&](int64_t k0) {
 #pragma unroll
@@ -166,6 +166,44 @@ gemm_f32_kernel(GemmArgs g) {
   }
 }
 
+template <int BM, int BN, int BK, int TM, int TN, bool TRANS_A>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+gemm_f32_kernel(GemmArgs g) {
+  gemm_tile<BM, BN, BK, TM, TN, TRANS_A>(g, (int64_t)blockIdx.y * BM, (int64_t)blockIdx.x * BN, blockIdx.z);
+}
+
+// Grouped form: the tiles of every problem's C in one list (tile_start is the
+// exclusive prefix sum of the per-problem tile counts); persistent CTAs walk
+// the list. Problem b's tiles run over its M x N output in row-major order.
+template <int BM, int BN, int BK, int TM, int TN, bool TRANS_A>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN), 512 / ((BM / TM) * (BN / TN)))
+gemm_grouped_kernel(const GroupGemm* __restrict__ jobs, const int* __restrict__ tile_start, int count) {
+  const int total = tile_start[count];
+  for (int t = blockIdx.x; t < total; t += gridDim.x) {
+    int lo = 0, hi = count - 1;   // last b with tile_start[b] <= t
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (tile_start[mid] <= t) lo = mid;
+      else hi = mid - 1;
+    }
+    const GroupGemm& j = jobs[lo];
+    const int local = t - tile_start[lo];
+    const int tn = (int)cdiv(j.N, BN);
+    GemmArgs g;
+    g.M = j.M; g.N = j.N; g.K = j.K;
+    g.A = j.A; g.lda = j.lda;
+    g.B = j.B; g.ldb = j.ldb;
+    g.C = j.C; g.ldc = j.ldc; g.c_slice = 0;
+    g.kchunk = round_up(j.K > 0 ? j.K : 1, BK);
+    g.sumsq = j.sumsq;
+    g.gate = j.gate;
+    g.gate_mode = j.gate_mode;
+    g.b_upper = j.b_upper;
+    __syncthreads();   // the previous tile's shared-memory reads are done
+    gemm_tile<BM, BN, BK, TM, TN, TRANS_A>(g, (int64_t)(local / tn) * BM, (int64_t)(local % tn) * BN, 0);
+  }
+}
+
 // C[m, n] = sum_z part[z][m][n] (fixed order, Kahan-compensated FP32).
 __global__ void splitk_reduce_kernel(int64_t M, int64_t N, int splits, const float* __restrict__ part,
                                      float* __restrict__ C, int64_t ldc) {
@@ -259,6 +297,63 @@ cudaError_t gemm_f32_ex(bool transA, int64_t M, int64_t N, int64_t K, const floa
   splitk_reduce_kernel<<<blocks, 256, 0, st>>>(M, N, used, part, C, ldc);
   note_launch();
   return cudaGetLastError();
+}
+
+// Grouped configurations (BM, BN, BK, TM, TN; threads = (BM/TM) (BN/TN)).
+namespace {
+// Resident CTAs per SM of one configuration (queried once; a launch with
+// total <= 0 only primes the query, so that no query runs under capture).
+template <int BM, int BN, int TM, int TN>
+cudaError_t launch_grouped_cfg(bool transA, const GroupGemm* jobs, const int* tile_start, int count, int total,
+                               cudaStream_t st) {
+  constexpr int NT = (BM / TM) * (BN / TN);
+  static int per_sm[2] = {0, 0};
+  int& occ = per_sm[transA ? 1 : 0];
+  if (occ == 0) {
+    cudaError_t e = transA ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                 &occ, gemm_grouped_kernel<BM, BN, 16, TM, TN, true>, NT, 0)
+                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                 &occ, gemm_grouped_kernel<BM, BN, 16, TM, TN, false>, NT, 0);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) occ = 1;
+  }
+  if (total <= 0 || count <= 0) return cudaSuccess;
+  const int grid = std::max(1, std::min(total, sm_count() * occ));
+  if (transA) gemm_grouped_kernel<BM, BN, 16, TM, TN, true><<<grid, NT, 0, st>>>(jobs, tile_start, count);
+  else        gemm_grouped_kernel<BM, BN, 16, TM, TN, false><<<grid, NT, 0, st>>>(jobs, tile_start, count);
+  note_launch();
+  return cudaGetLastError();
+}
+}  // namespace
+
+void grouped_tile(int cfg, int* bm, int* bn) {
+  static const int kBM[kGroupCfgs] = {128, 64, 128, 64, 32, 32};
+  static const int kBN[kGroupCfgs] = {64, 64, 32, 32, 32, 64};
+  *bm = kBM[cfg];
+  *bn = kBN[cfg];
+}
+
+cudaError_t gemm_grouped_prepare() {
+  sm_count();
+  for (int cfg = 0; cfg < kGroupCfgs; ++cfg)
+    for (int t = 0; t < 2; ++t) {
+      cudaError_t e = gemm_grouped(t == 1, cfg, nullptr, nullptr, 0, 0, nullptr);
+      if (e != cudaSuccess) return e;
+    }
+  return cudaSuccess;
+}
+
+cudaError_t gemm_grouped(bool transA, int cfg, const GroupGemm* jobs, const int* tile_start, int count,
+                         int total_tiles, cudaStream_t st) {
+  switch (cfg) {
+    case 0: return launch_grouped_cfg<128, 64, 8, 4>(transA, jobs, tile_start, count, total_tiles, st);
+    case 1: return launch_grouped_cfg<64, 64, 4, 4>(transA, jobs, tile_start, count, total_tiles, st);
+    case 2: return launch_grouped_cfg<128, 32, 8, 4>(transA, jobs, tile_start, count, total_tiles, st);
+    case 3: return launch_grouped_cfg<64, 32, 4, 4>(transA, jobs, tile_start, count, total_tiles, st);
+    case 4: return launch_grouped_cfg<32, 32, 4, 4>(transA, jobs, tile_start, count, total_tiles, st);
+    case 5: return launch_grouped_cfg<32, 64, 4, 4>(transA, jobs, tile_start, count, total_tiles, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace rqlp

@@ -18,12 +18,6 @@
 #include "common.cuh"
 #include "tc_gemm.cuh"
 
-#define CK(x)                             \
-  do {                                    \
-    cudaError_t e_ = (x);                 \
-    if (e_ != cudaSuccess) return e_;     \
-  } while (0)
-
 namespace rqlp {
 namespace {
 

@@ -23,9 +23,9 @@ __global__ void transpose_kernel(int d, const float* __restrict__ X, int64_t ldx
 }
 
 // L = Rhat^T written as a full d x d block (strict upper part zero) and
-// ||L||_F^2 accumulated into diag[1] (double, one atomic per CTA).
+// ||L||_F^2 accumulated into *l2 (double, one atomic per CTA).
 __global__ void write_L_kernel(int d, const float* __restrict__ Rh, int64_t ldrh, float* __restrict__ L,
-                               int64_t ldl, double* diag) {
+                               int64_t ldl, double* l2) {
   __shared__ double red[32];
   double acc = 0.0;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < d * d; e += gridDim.x * blockDim.x) {
@@ -37,10 +37,10 @@ __global__ void write_L_kernel(int d, const float* __restrict__ Rh, int64_t ldrh
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
   __syncthreads();
-  if (threadIdx.x == 0 && diag != nullptr) {
+  if (threadIdx.x == 0 && l2 != nullptr) {
     double s = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-    atomicAdd(&diag[1], s);
+    atomicAdd(l2, s);
   }
 }
 
@@ -75,7 +75,92 @@ __global__ void copy_kernel(int64_t rows, int64_t cols, const float* __restrict_
   }
 }
 
+// ---- batched forms: blockIdx.x = job
+__global__ void init_batched_kernel(const SmallJob* __restrict__ jobs, int count) {
+  const int b = blockIdx.x;
+  if (b >= count) return;
+  const SmallJob& j = jobs[b];
+  const int t = threadIdx.x;
+  if (t < 2) j.info[t] = 0;
+  if (t < j.ngates) j.gates[t] = 0;
+  if (t < 4) j.scal[t] = 0.0;
+}
+
+__global__ void transpose_batched_kernel(const SmallJob* __restrict__ jobs, int count) {
+  const int b = blockIdx.x;
+  if (b >= count) return;
+  const SmallJob& j = jobs[b];
+  for (int e = threadIdx.x; e < j.d * j.d; e += blockDim.x) {
+    const int i = e / j.d, l = e % j.d;
+    j.Y[(int64_t)l * j.ldy + i] = j.X[(int64_t)i * j.ldx + l];
+  }
+}
+
+__global__ void write_L_batched_kernel(const SmallJob* __restrict__ jobs, int count) {
+  const int b = blockIdx.x;
+  if (b >= count) return;
+  const SmallJob& j = jobs[b];
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (int e = threadIdx.x; e < j.d * j.d; e += blockDim.x) {
+    const int i = e / j.d, c = e % j.d;
+    const float v = c <= i ? j.X[(int64_t)c * j.ldx + i] : 0.f;
+    j.Y[(int64_t)i * j.ldy + c] = v;
+    acc += (double)v * (double)v;
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    j.scal[1] = s;
+  }
+}
+
+__global__ void finish_diag_batched_kernel(const SmallJob* __restrict__ jobs, int count) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= count) return;
+  const SmallJob& j = jobs[b];
+  const double a2 = j.scal[0], l2 = j.scal[1];
+  if (!isfinite(a2)) post_error(j.info, RQLP_ERR_NONFINITE, 0);
+  if (j.diag != nullptr) {
+    j.diag[0] = a2;
+    j.diag[1] = l2;
+    j.diag[2] = a2 - l2;
+    j.diag[3] = j.scal[2];
+  }
+}
+
 }  // namespace
+
+cudaError_t init_batched(const SmallJob* jobs, int count, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  init_batched_kernel<<<count, 32, 0, st>>>(jobs, count);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t transpose_batched(const SmallJob* jobs, int count, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  transpose_batched_kernel<<<count, 256, 0, st>>>(jobs, count);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t write_L_batched(const SmallJob* jobs, int count, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  write_L_batched_kernel<<<count, 256, 0, st>>>(jobs, count);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t finish_diag_batched(const SmallJob* jobs, int count, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  finish_diag_batched_kernel<<<(count + 127) / 128, 128, 0, st>>>(jobs, count);
+  note_launch();
+  return cudaGetLastError();
+}
 
 cudaError_t transpose_small(int d, const float* X, int64_t ldx, float* Y, int64_t ldy, cudaStream_t st) {
   int blocks = std::max(1, std::min(64, (d * d + 255) / 256));

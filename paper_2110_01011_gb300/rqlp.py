@@ -37,13 +37,23 @@ EXPORTED = ["rqlp_default_opts", "rqlp_workspace_bytes", "rqlp_factor", "rqlp_ho
             "rqlp_factor_host", "rqlp_factor_noalloc", "rqlp_sketch_workspace_bytes", "rqlp_sketch",
             "rqlp_orth_workspace_bytes", "rqlp_orth", "rqlp_mlp_forward", "rqlp_mlp_workspace_bytes",
             "rqlp_mlp_grad", "rqlp_mlp_adam", "rqlp_learned_workspace_bytes", "rqlp_probe_features",
-            "rqlp_predict_qp", "rqlp_factor_learned", "rqlp_kernel_launches", "rqlp_profile_enable",
+            "rqlp_predict_qp", "rqlp_factor_learned", "rqlp_batch_workspace_bytes", "rqlp_batch_create",
+            "rqlp_batch_autotune", "rqlp_batch_tuning", "rqlp_batch_run", "rqlp_batch_launch",
+            "rqlp_batch_destroy", "rqlp_factor_batched", "rqlp_kernel_launches", "rqlp_profile_enable",
             "rqlp_profile_read", "rqlp_status_string", "rqlp_version"]
 
 
 class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("small_fp64", ctypes.c_int),
                 ("reserved", ctypes.c_int * 6)]
+
+
+class Problem(ctypes.Structure):
+    """rqlp_problem: one problem of a batch (device pointers, row-major)."""
+    _fields_ = [("A", ctypes.c_void_p), ("m", ctypes.c_int64), ("n", ctypes.c_int64), ("lda", ctypes.c_int64),
+                ("Omega", ctypes.c_void_p), ("ldo", ctypes.c_int64), ("k", ctypes.c_int), ("p", ctypes.c_int),
+                ("Q", ctypes.c_void_p), ("ldq", ctypes.c_int64), ("L", ctypes.c_void_p), ("ldl", ctypes.c_int64),
+                ("P", ctypes.c_void_p), ("ldp", ctypes.c_int64)]
 
 
 class RqlpError(RuntimeError):
@@ -102,6 +112,24 @@ def _declare(lib):
     lib.rqlp_factor_learned.argtypes = [_vp, _i64, _i64, _i64, _int, _vp, _i64, _d, _vp, _vp, _i64, _vp, _i64,
                                         _vp, _i64, _vp, _sz, _vp, _vp, _vp, ctypes.POINTER(Opts), _vp]
     lib.rqlp_factor_learned.restype = _int
+    _pp = ctypes.POINTER(Problem)
+    lib.rqlp_batch_workspace_bytes.argtypes = [_int, _pp, _int, ctypes.POINTER(Opts)]
+    lib.rqlp_batch_workspace_bytes.restype = _sz
+    lib.rqlp_batch_create.argtypes = [_int, _pp, _int, _vp, _sz, _vp, _vp, ctypes.POINTER(Opts), _vp,
+                                      ctypes.POINTER(_vp)]
+    lib.rqlp_batch_create.restype = _int
+    lib.rqlp_batch_autotune.argtypes = [_vp, _int, _vp]
+    lib.rqlp_batch_autotune.restype = _int
+    lib.rqlp_batch_tuning.argtypes = [_vp, ctypes.POINTER(_int), _int]
+    lib.rqlp_batch_tuning.restype = _int
+    lib.rqlp_batch_run.argtypes = [_vp, _vp]
+    lib.rqlp_batch_run.restype = _int
+    lib.rqlp_batch_launch.argtypes = [_vp, _vp]
+    lib.rqlp_batch_launch.restype = _int
+    lib.rqlp_batch_destroy.argtypes = [_vp]
+    lib.rqlp_batch_destroy.restype = _int
+    lib.rqlp_factor_batched.argtypes = [_int, _pp, _int, _vp, _sz, _vp, _vp, ctypes.POINTER(Opts), _vp]
+    lib.rqlp_factor_batched.restype = _int
     lib.rqlp_kernel_launches.argtypes = []
     lib.rqlp_kernel_launches.restype = ctypes.c_ulonglong
     lib.rqlp_profile_enable.argtypes = [_int]
@@ -231,6 +259,46 @@ def rqlp_factor_learned(A, m, n, lda, k, Omega, ldo, target, params, Q, ldq, L, 
                         d_info, d_diag, h_qp, opts, stream):
     return int(load().rqlp_factor_learned(A, m, n, lda, k, Omega, ldo, target, params, Q, ldq, L, ldl, P, ldp,
                                           workspace, ws_bytes, d_info, d_diag, h_qp,
+                                          ctypes.byref(opts) if opts is not None else None, stream))
+
+
+def rqlp_batch_workspace_bytes(count, probs, q, opts=None):
+    return int(load().rqlp_batch_workspace_bytes(count, probs, q, ctypes.byref(opts or _opts())))
+
+
+def rqlp_batch_create(count, probs, q, workspace, ws_bytes, d_info, d_diag, opts, stream):
+    """Returns (status, handle)."""
+    h = ctypes.c_void_p()
+    st = int(load().rqlp_batch_create(count, probs, q, workspace, ws_bytes, d_info, d_diag,
+                                      ctypes.byref(opts) if opts is not None else None, stream, ctypes.byref(h)))
+    return st, h
+
+
+def rqlp_batch_autotune(batch, reps, stream):
+    return int(load().rqlp_batch_autotune(batch, reps, stream))
+
+
+def rqlp_batch_tuning(batch):
+    n = int(load().rqlp_batch_tuning(batch, None, 0))
+    buf = (_int * max(n, 1))()
+    load().rqlp_batch_tuning(batch, buf, n)
+    return [int(buf[i]) for i in range(n)]
+
+
+def rqlp_batch_run(batch, stream):
+    return int(load().rqlp_batch_run(batch, stream))
+
+
+def rqlp_batch_launch(batch, stream):
+    return int(load().rqlp_batch_launch(batch, stream))
+
+
+def rqlp_batch_destroy(batch):
+    return int(load().rqlp_batch_destroy(batch))
+
+
+def rqlp_factor_batched(count, probs, q, workspace, ws_bytes, d_info, d_diag, opts, stream):
+    return int(load().rqlp_factor_batched(count, probs, q, workspace, ws_bytes, d_info, d_diag,
                                           ctypes.byref(opts) if opts is not None else None, stream))
 
 
@@ -432,3 +500,70 @@ def factor_host(A, k, p, q, Omega, precision=PREC_FP32, workspace=None, out=None
     if st != 0:
         raise RqlpError(st, "rqlp_factor_host")
     return Q, L, P, info, diag
+
+
+class Batch:
+    """A batch plan over CUDA FP32 row-major matrices: As[i] (m_i x n_i),
+    Omegas[i] (m_i x (k_i + p_i)), one q. Allocates the outputs, the
+    per-problem info/diag rows and the workspace with torch; ``launch()``
+    replays the captured graph, ``run()`` launches the kernels one by one."""
+
+    def __init__(self, As, Omegas, ks, ps, q, small_fp64=False):
+        import torch
+        self.count = len(As)
+        dev = As[0].device
+        self.As, self.Omegas = list(As), list(Omegas)
+        self.Q, self.L, self.P = [], [], []
+        arr = (Problem * self.count)()
+        for i, (A, O, k, p) in enumerate(zip(As, Omegas, ks, ps)):
+            m, n = A.shape
+            d = k + p
+            Q = torch.empty(m, d, device=dev)
+            L = torch.empty(d, d, device=dev)
+            P = torch.empty(n, d, device=dev)
+            self.Q.append(Q)
+            self.L.append(L)
+            self.P.append(P)
+            arr[i] = Problem(A.data_ptr(), m, n, A.stride(0), O.data_ptr(), O.stride(0), k, p, Q.data_ptr(),
+                             Q.stride(0), L.data_ptr(), L.stride(0), P.data_ptr(), P.stride(0))
+        self.probs = arr
+        self.opts = _opts(PREC_FP32, small_fp64)
+        nb = rqlp_batch_workspace_bytes(self.count, arr, q, self.opts)
+        if nb == 0:
+            raise RqlpError(1, "rqlp_batch_workspace_bytes")
+        self.ws_bytes = nb
+        self.ws_buf, self.ws = _workspace(nb, dev)
+        self.info = torch.empty(self.count, 2, dtype=torch.int32, device=dev)
+        self.diag = torch.empty(self.count, 4, dtype=torch.float64, device=dev)
+        st, h = rqlp_batch_create(self.count, arr, q, self.ws, nb, self.info.data_ptr(), self.diag.data_ptr(),
+                                  self.opts, _stream())
+        if st != 0:
+            raise RqlpError(st, "rqlp_batch_create")
+        self.handle = h
+
+    def autotune(self, reps=3):
+        st = rqlp_batch_autotune(self.handle, reps, _stream())
+        if st != 0:
+            raise RqlpError(st, "rqlp_batch_autotune")
+        return rqlp_batch_tuning(self.handle)
+
+    def run(self):
+        st = rqlp_batch_run(self.handle, _stream())
+        if st != 0:
+            raise RqlpError(st, "rqlp_batch_run")
+
+    def launch(self):
+        st = rqlp_batch_launch(self.handle, _stream())
+        if st != 0:
+            raise RqlpError(st, "rqlp_batch_launch")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            rqlp_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -57,7 +57,11 @@ def compare(A, Om, k, p, q, gpu, elem_atol=2e-4, precision=0):
     err["L_lead"] = np.max(np.abs(Lg[:k, :k] - ref.L[:k, :k])) / np.abs(ref.L).max()
     err["L_upper_zero"] = float(np.abs(np.triu(Lg, 1)).max()) if d > 1 else 0.0
     nA2 = np.linalg.norm(A64) ** 2
+    nL2 = float((Lg * Lg).sum())
     err["diag_A2_rel"] = abs(diag[0] - nA2) / nA2
+    # d_diag = [||A||^2, ||L||^2, ||A||^2 - ||L||^2, shifted Choleskys]
+    err["diag_L2_rel"] = abs(diag[1] - nL2) / nL2
+    err["diag_res2"] = abs(diag[2] - (diag[0] - diag[1])) / nA2
     assert err["L_upper_zero"] == 0.0
     assert (np.diag(Lg) > 0).all()
     assert err["orthQ"] <= TOL_ORTH, err
@@ -67,4 +71,6 @@ def compare(A, Om, k, p, q, gpu, elem_atol=2e-4, precision=0):
     assert err["Q_lead"] <= elem_atol and err["P_lead"] <= elem_atol, err
     assert err["L_lead"] <= elem_atol, err
     assert err["diag_A2_rel"] <= 1e-6, err
+    assert err["diag_L2_rel"] <= 1e-6 and err["diag_res2"] <= 1e-12, err
+    assert diag[3] == np.round(diag[3]) and diag[3] >= 0, err
     return err

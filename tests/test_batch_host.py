@@ -1,0 +1,44 @@
+"""Host-side rules of the batch plan (no GPU): workspace sizing and argument
+validation run on the host only."""
+import pytest
+
+from paper_2110_01011_gb300 import rqlp
+
+
+def _prob(m, n, k, p, ld_extra=0):
+    fake = 1 << 20   # never dereferenced by the sizing call
+    d = k + p
+    return rqlp.Problem(fake, m, n, n + ld_extra, fake, d, k, p, fake, d, fake, d, fake, d)
+
+
+def _arr(ps):
+    a = (rqlp.Problem * len(ps))()
+    for i, p in enumerate(ps):
+        a[i] = p
+    return a
+
+
+def test_sizing_grows_with_problems():
+    one = rqlp.rqlp_batch_workspace_bytes(1, _arr([_prob(300, 200, 20, 5)]), 1)
+    two = rqlp.rqlp_batch_workspace_bytes(2, _arr([_prob(300, 200, 20, 5), _prob(500, 100, 50, 5)]), 1)
+    assert 0 < one < two
+    # per-problem buffers: Y, Pt (n x ld), Z (m x ld), T1 (max x ld) at least
+    assert one >= 4 * (200 + 300 + 200 + 300) * 28
+
+
+@pytest.mark.parametrize("bad", [
+    _prob(30, 20, 18, 5),          # d > min(m, n)
+    _prob(300, 300, 125, 5),       # d > RQLP_BATCH_MAX_D
+    _prob(300, 200, 0, 5),         # k < 1
+    _prob(300, 200, 10, -1),       # p < 0
+    _prob(300, 200, 10, 5, -1),    # lda < n
+])
+def test_invalid_problem_sizes_to_zero(bad):
+    assert rqlp.rqlp_batch_workspace_bytes(2, _arr([_prob(300, 200, 20, 5), bad]), 1) == 0
+
+
+def test_invalid_batch_arguments():
+    a = _arr([_prob(300, 200, 20, 5)])
+    assert rqlp.rqlp_batch_workspace_bytes(0, a, 1) == 0
+    assert rqlp.rqlp_batch_workspace_bytes(1, a, -1) == 0
+    assert rqlp.rqlp_batch_workspace_bytes(1, a, 1, rqlp._opts(rqlp.PREC_BF16X3)) == 0
