@@ -2,13 +2,23 @@
 """Benchmark: Rand-QLP time-to-factor and A-pass GB/s on one GB300.
 
 Workload: A = U_r diag(exp(-i/50)) V_r^T + 1e-6 G / sqrt(n), 20000 x 20000
-FP32 (Haar U_r, V_r, r = 1000), k = 200, p = 10, q = 2, Gaussian Omega
-20000 x 210. One step = one full factorisation A -> (Q, L, P) through the
-C ABI with A resident in HBM. value = GB/s of A streamed by the 2q + 2
-passes over A (aggregate over ranks), ms_per_step = time to factor.
+FP32 (Haar U_r, V_r, r = 1000), k = 200, Gaussian Omega 20000 x 220 (its
+first k + p columns are the sketch's test matrix).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|bf16x3|auto]
-  (auto = the BF16-split tensor-core form; the plain FP32 form is timed beside it)
+Headline (``--form learned``, the default): the BF16-split tensor-core form
+with (q, p) predicted by the trained network for the excess rank-k error that
+the plain FP32 form reaches with the fixed q = 2, p = 10 on the same matrix
+(equal accuracy). One step = one rqlp_factor_learned call (probe, prediction,
+chain) with A resident in HBM. value = GB/s of A streamed by the 2q + 2 passes
+over A (aggregate over ranks), ms_per_step = time to factor. The plain FP32
+form and the split form with the fixed (2, 10) are timed beside it.
+``--form fixed`` times rqlp_factor with --precision and --q/--p instead.
+
+A ``batched`` object times the batched form on 512 uneven problems (m in
+[256, 4096], n in [256, 2048], k in [8, 64], p = 5, q = 1; half exponential,
+half polynomial spectra) as one graph launch after autotuning.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--form learned|fixed]
   python bench.py --impl reference      # the FP64 CPU oracle on a bounded sample
 
 For N > 1 (torchrun) every rank factors its own replica (the path does not
@@ -42,7 +52,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "bf16x3"])
+    ap.add_argument("--form", default="learned", choices=["learned", "fixed"])
+    ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "bf16x3"],
+                    help="--form fixed: the form timed (auto = bf16x3)")
     ap.add_argument("--m", type=int, default=20000)
     ap.add_argument("--n", type=int, default=20000)
     ap.add_argument("--k", type=int, default=200)
@@ -51,6 +63,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip timing the plain FP32 form")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched form")
+    ap.add_argument("--batch", type=int, default=512)
     ap.add_argument("--sample", type=int, default=0,
                     help="rows/cols of the oracle's sample block (0 = default for the workload)")
     return ap.parse_args()
@@ -66,12 +80,48 @@ def apass_bytes(a):
 
 # ------------------------------------------------------------------ inputs
 
-def make_inputs(a, device):
+SPECTRUM_RANK = 1000
+
+
+def spectrum():
     from paper_2110_01011_gb300 import inputs
-    sig = inputs.exp_spectrum(1000, 50.0)
-    A = inputs.low_rank_matrix_torch(a.m, a.n, sig, 1e-6, seed=1002, rank=1000, device=device)
-    Om = inputs.omega_torch(a.m, a.k + a.p, seed=2002, device=device)
+    return inputs.exp_spectrum(SPECTRUM_RANK, 50.0)
+
+
+def make_inputs(a, device):
+    """A and an Omega wide enough for the probe (k + 20 columns)."""
+    from paper_2110_01011_gb300 import inputs
+    A = inputs.low_rank_matrix_torch(a.m, a.n, spectrum(), 1e-6, seed=1002, rank=SPECTRUM_RANK, device=device)
+    Om = inputs.omega_torch(a.m, a.k + 20, seed=2002, device=device)
     return A, Om
+
+
+def tail2(a):
+    """sum_{i > k} sigma_i^2 of the workload (the noise floor adds ~1e-12 m)."""
+    sig = spectrum()
+    return float((sig[a.k:] ** 2).sum()) + 1e-12 * a.m
+
+
+class Judge:
+    """Accuracy of a factorisation from its P, evaluated directly in FP64:
+    ||A - A P_j P_j^T||_F for the leading j = k columns (the excess rank-k
+    error eps = that / (sum_{i>k} sigma_i^2)^(1/2) - 1) and for all d columns
+    (relative to ||A||_F). The identity ||A||^2 - ||L||^2 is not used here:
+    at a 3e-4 relative tail the rounding of L itself would dominate it."""
+
+    def __init__(self, a, A):
+        self.a = a
+        self.A64 = A.double()
+        self.nA = float(self.A64.norm())
+
+    def resid(self, P, j):
+        Pj = P[:, :j].double()
+        return float((self.A64 - (self.A64 @ Pj) @ Pj.T).norm())
+
+    def __call__(self, P):
+        r_k = self.resid(P, self.a.k)
+        return {"excess_error": r_k / tail2(self.a) ** 0.5 - 1.0,
+                "rel_residual": self.resid(P, P.shape[1]) / self.nA}
 
 
 # ------------------------------------------------------------------ clocks
@@ -131,11 +181,10 @@ def oracle_inputs(a, S, A=None):
 
     from paper_2110_01011_gb300 import inputs
     if A is None:
-        sig = inputs.exp_spectrum(1000, 50.0)
         dev = "cuda" if torch.cuda.is_available() else "cpu"
-        A = inputs.low_rank_matrix_torch(a.m, a.n, sig, 1e-6, seed=1002, rank=1000, device=dev)
+        A = inputs.low_rank_matrix_torch(a.m, a.n, spectrum(), 1e-6, seed=1002, rank=SPECTRUM_RANK, device=dev)
     As = A[:S, :S].double().cpu().numpy()
-    Om = inputs.omega(a.m, a.k + a.p, seed=2002)[:S].astype(np.float64)
+    Om = inputs.omega(a.m, a.k + 20, seed=2002)[:S, :a.k + a.p].astype(np.float64)
     return As, Om
 
 
@@ -197,6 +246,212 @@ def traffic_for(kernel, sha):
     return None
 
 
+class Ctx:
+    def __init__(self, world, rank, dev):
+        self.world, self.rank, self.dev = world, rank, dev
+
+    def barrier(self):
+        import torch
+        import torch.distributed as dist
+        if self.world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(self, x):
+        import torch
+        import torch.distributed as dist
+        if self.world == 1:
+            return x
+        t = torch.tensor([x], device=self.dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+
+def time_steps(ctx, fn, steps):
+    """ms per step of fn over `steps` calls (CUDA events on the current stream)."""
+    import torch
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ctx.barrier()
+    e0.record(st)
+    for _ in range(steps):
+        fn()
+    e1.record(st)
+    ctx.barrier()
+    return ctx.max_over_ranks(e0.elapsed_time(e1) / steps)
+
+
+def fixed_runner(a, A, Om, q, p, prec, dev):
+    import torch
+
+    from paper_2110_01011_gb300 import rqlp
+    d = a.k + p
+    opts = rqlp._opts(prec)
+    ws = torch.empty(rqlp.rqlp_workspace_bytes(a.m, a.n, a.k, p, q, opts) + 256, dtype=torch.uint8, device=dev)
+    out = (torch.empty(a.m, d, device=dev), torch.empty(d, d, device=dev), torch.empty(a.n, d, device=dev),
+           torch.empty(2, dtype=torch.int32, device=dev), torch.empty(4, dtype=torch.float64, device=dev))
+    Omp = Om[:, :d]
+
+    def step():
+        rqlp.factor(A, a.k, p, q, Omp, precision=prec, workspace=ws, out=out)
+    return step, out
+
+
+def learned_runner(a, A, Om, params, target, prec, dev):
+    import torch
+
+    from paper_2110_01011_gb300 import rqlp
+    w = a.k + 20
+    nb = rqlp.rqlp_learned_workspace_bytes(a.m, a.n, a.k, rqlp._opts(prec))
+    ws = torch.empty(nb + 256, dtype=torch.uint8, device=dev)
+    out = (torch.empty(a.m, w, device=dev), torch.empty(w, w, device=dev), torch.empty(a.n, w, device=dev),
+           torch.empty(2, dtype=torch.int32, device=dev), torch.empty(4, dtype=torch.float64, device=dev))
+    res = {}
+
+    def step():
+        Q, L, P, info, diag, qp = rqlp.factor_learned(A, a.k, Om, params, target, precision=prec, workspace=ws,
+                                                      out=out)
+        res["out"] = (Q, L, P, info, diag)
+        res["qp"] = qp
+    return step, res
+
+
+def roofline(a, recs, d, prec, peaks, dev):
+    import torch
+
+    from paper_2110_01011_gb300 import rqlp
+    by_tag = {0: [r[0] for r in recs if r[1] == 0], 1: [r[0] for r in recs if r[1] == 1]}
+    dom = max(by_tag, key=lambda t: sum(by_tag[t]))
+    pass_ms = statistics.mean(by_tag[dom]) if by_tag[dom] else float("nan")
+    flops = 2.0 * a.m * a.n * d
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    kname = {0: "pass_AX", 1: "pass_AtX"}[dom]
+    sha = kernel_sha()
+    if prec == rqlp.PREC_FP32:
+        peak = nsm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": flops / (pass_ms * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                "peak_source": f"derived: {nsm} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz",
+                "flops_per_launch": flops}
+    else:
+        # Three BF16 products per pass (A_hi X_hi + A_hi X_lo + A_lo X_hi).
+        peak = peaks.get("bf16_tflops_sustained", 1683.0)
+        roof = {"bound": "tensor", "achieved": 3 * flops / (pass_ms * 1e-3) / 1e12, "peak": peak,
+                "unit": "TFLOP/s", "flops_per_launch": 3 * flops,
+                "peak_source": "MEASURED_PEAKS bf16_tflops_sustained (of measured)"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = traffic_for(f"{kname}_{'fp32' if prec == 0 else 'bf16x3'}", sha)
+    roof["kernel"] = kname
+    roof["launch_ms"] = pass_ms
+    roof["launches_timed"] = len(by_tag[dom])
+    roof["hbm_gbs"] = a.m * a.n * 4 / (pass_ms * 1e-3) / 1e9
+    roof["hbm_frac_of_measured"] = roof["hbm_gbs"] / peaks.get("hbm_gbs", 6761.6)
+    return roof, sha
+
+
+def batched_leg(a, ctx):
+    """512 uneven problems (m in [256, 4096], n in [256, 2048], k in [8, 64],
+    p = 5, q = 1) as one graph launch after autotuning."""
+    import torch
+
+    from paper_2110_01011_gb300 import inputs, rqlp
+    probs = inputs.random_batch(a.batch, seed=4004)
+    t0 = time.perf_counter()
+    As = [inputs.low_rank_matrix_reflect(pr.m, pr.n, pr.sigma(), pr.seed, ctx.dev) for pr in probs]
+    Os = [inputs.omega_torch(pr.m, pr.d, pr.seed + 1, ctx.dev) for pr in probs]
+    gen_s = time.perf_counter() - t0
+    b = rqlp.Batch(As, Os, [pr.k for pr in probs], [pr.p for pr in probs], probs[0].q)
+    tune = b.autotune(reps=2)
+    for _ in range(max(1, a.warmup)):
+        b.launch()
+    ctx.barrier()
+    l0 = rqlp.rqlp_kernel_launches()
+    reps = max(3, a.steps)
+    ms = time_steps(ctx, b.launch, reps)
+    launches = (rqlp.rqlp_kernel_launches() - l0) // reps
+    bad = int((b.info[:, 0] != 0).sum().item())
+    q = probs[0].q
+    abytes = sum((2 * q + 2) * pr.m * pr.n * 4 for pr in probs)
+    out = {"problems": len(probs), "ms_per_batch": ms, "value": ctx.world * abytes / (ms * 1e-3) / 1e9,
+           "unit": "GB/s", "problems_per_s": ctx.world * len(probs) / (ms * 1e-3), "A_bytes_per_batch": abytes,
+           "graph_kernels": launches, "tuning": tune, "nonzero_status": bad, "generate_s": gen_s,
+           "workload": f"{len(probs)} problems, m in [256,4096], n in [256,2048], k in [8,64], p=5, q={q}, "
+                       "half exp / half poly spectra, FP32"}
+    b.close()
+    del As, Os
+    torch.cuda.empty_cache()
+    return out
+
+
+def e2e_learned(a, ctx, A, Om, params, target, prec, steps, warmup):
+    """End to end through the public API: pinned host A and Omega copied in,
+    rqlp_factor_learned, Q, L, P copied back, every step."""
+    import torch
+
+    from paper_2110_01011_gb300 import rqlp
+    dev = ctx.dev
+    w = a.k + 20
+    hA, hO = A.cpu().pin_memory(), Om.cpu().pin_memory()
+    dA, dO = torch.empty_like(A), torch.empty_like(Om)
+    hQ, hL, hP = (torch.empty(a.m, w).pin_memory(), torch.empty(w, w).pin_memory(), torch.empty(a.n, w).pin_memory())
+    nb = rqlp.rqlp_learned_workspace_bytes(a.m, a.n, a.k, rqlp._opts(prec))
+    ws = torch.empty(nb + 256, dtype=torch.uint8, device=dev)
+    out = (torch.empty(a.m, w, device=dev), torch.empty(w, w, device=dev), torch.empty(a.n, w, device=dev),
+           torch.empty(2, dtype=torch.int32, device=dev), torch.empty(4, dtype=torch.float64, device=dev))
+    d_used = [w]
+
+    def step():
+        dA.copy_(hA, non_blocking=True)
+        dO.copy_(hO, non_blocking=True)
+        Q, L, P, info, diag, qp = rqlp.factor_learned(dA, a.k, dO, params, target, precision=prec, workspace=ws,
+                                                      out=out)
+        d = a.k + qp[1]
+        d_used[0] = d
+        hQ[:, :d].copy_(Q, non_blocking=True)
+        hL[:d, :d].copy_(L, non_blocking=True)
+        hP[:, :d].copy_(P, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        return qp
+
+    for _ in range(max(1, warmup)):
+        qp = step()
+    ctx.barrier()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        qp = step()
+    ctx.barrier()
+    dt = ctx.max_over_ranks((time.perf_counter() - t0) / steps)
+    d = d_used[0]
+    h2d = 4 * (a.m * a.n + a.m * w)
+    d2h = 4 * (a.m * d + d * d + a.n * d)
+    return {"value": ctx.world * (2 * qp[0] + 2) * a.m * a.n * 4 / dt / 1e9, "unit": "GB/s", "ms_per_step": dt * 1e3,
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "api": "rqlp_factor_learned + pinned copies"}
+
+
+def e2e_fixed(a, ctx, A, Om, q, p, prec, steps, warmup):
+    import torch
+
+    from paper_2110_01011_gb300 import rqlp
+    d = a.k + p
+    hA = A.cpu().pin_memory()
+    hO = Om[:, :d].contiguous().cpu().pin_memory()
+    hout = (torch.empty(a.m, d).pin_memory(), torch.empty(d, d).pin_memory(), torch.empty(a.n, d).pin_memory(),
+            torch.zeros(2, dtype=torch.int32), torch.zeros(4, dtype=torch.float64))
+    hws = torch.empty(rqlp.rqlp_host_workspace_bytes(a.m, a.n, a.k, p, q, rqlp._opts(prec)) + 256,
+                      dtype=torch.uint8, device=ctx.dev)
+    for _ in range(max(1, warmup)):
+        rqlp.factor_host(hA, a.k, p, q, hO, precision=prec, workspace=hws, out=hout)
+    ctx.barrier()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        rqlp.factor_host(hA, a.k, p, q, hO, precision=prec, workspace=hws, out=hout)
+    ctx.barrier()
+    dt = ctx.max_over_ranks((time.perf_counter() - t0) / steps)
+    return {"value": ctx.world * (2 * q + 2) * a.m * a.n * 4 / dt / 1e9, "unit": "GB/s", "ms_per_step": dt * 1e3,
+            "h2d_bytes_per_step": 4 * (a.m * a.n + a.m * d),
+            "d2h_bytes_per_step": 4 * (a.m * d + d * d + a.n * d) + 8 + 32, "api": "rqlp_factor_host"}
+
+
 def main():
     a = parse()
     if a.impl == "reference":
@@ -205,7 +460,7 @@ def main():
     import torch
     import torch.distributed as dist
 
-    from paper_2110_01011_gb300 import rqlp
+    from paper_2110_01011_gb300 import learn, rqlp
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -213,170 +468,128 @@ def main():
     if world > 1:
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
-    lib = rqlp.load()
-    del lib
-    # The headline form is the BF16-split tensor-core path; FP32 is timed beside it.
-    prec = {"fp32": rqlp.PREC_FP32, "bf16x3": rqlp.PREC_BF16X3}.get(a.precision, rqlp.PREC_BF16X3)
-    d = a.k + a.p
-
-    def barrier():
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
-
+    ctx = Ctx(world, rank, dev)
+    rqlp.load()
+    peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
     A, Om = make_inputs(a, dev)
-    opts = rqlp._opts(prec)
-    wsb = rqlp.rqlp_workspace_bytes(a.m, a.n, a.k, a.p, a.q, opts)
-    ws = torch.empty(wsb + 256, dtype=torch.uint8, device=dev)
-    Q = torch.empty(a.m, d, device=dev)
-    L = torch.empty(d, d, device=dev)
-    P = torch.empty(a.n, d, device=dev)
-    info = torch.empty(2, dtype=torch.int32, device=dev)
-    diag = torch.empty(4, dtype=torch.float64, device=dev)
-    out = (Q, L, P, info, diag)
 
-    def step():
-        rqlp.factor(A, a.k, a.p, a.q, Om, precision=prec, workspace=ws, out=out)
+    params = None
+    learned_note = None
+    if a.form == "learned":
+        if os.path.exists(learn.WEIGHTS):
+            params = torch.from_numpy(learn.load_weights()).to(dev)
+        else:
+            learned_note = "no trained weights in the package: fixed (q, p) timed instead"
+    form = "learned" if params is not None else "fixed"
+
+    compare = {}
+    judge = Judge(a, A)
+    # The plain FP32 form with the fixed (2, 10): its time and the accuracy the
+    # learned form is asked to match.
+    target = None
+    if form == "learned" or (not a.no_compare and a.precision != "fp32"):
+        step32, out32 = fixed_runner(a, A, Om, 2 if form == "learned" else a.q, 10 if form == "learned" else a.p,
+                                     rqlp.PREC_FP32, dev)
+        step32()
+        ctx.barrier()
+        ms32 = time_steps(ctx, step32, 3)
+        acc32 = judge(out32[2])
+        compare.update({"fp32_fixed_qp": [2, 10] if form == "learned" else [a.q, a.p], "fp32_ms_per_step": ms32,
+                        "fp32_rel_residual": acc32["rel_residual"], "fp32_excess_error": acc32["excess_error"]})
+        target = min(max(acc32["excess_error"], 1e-3), 0.5)
+        del out32, step32
+        torch.cuda.empty_cache()
+
+    prec = rqlp.PREC_BF16X3
+    if form == "fixed":
+        prec = {"fp32": rqlp.PREC_FP32, "bf16x3": rqlp.PREC_BF16X3}.get(a.precision, rqlp.PREC_BF16X3)
+        step, out = fixed_runner(a, A, Om, a.q, a.p, prec, dev)
+        res = None
+        q_used, p_used = a.q, a.p
+    else:
+        step, res = learned_runner(a, A, Om, params, target, prec, dev)
 
     for _ in range(a.warmup):
         step()
-    barrier()
-    status = int(info[0].item())
+    ctx.barrier()
+    if res is not None:
+        q_used, p_used = res["qp"]
+        out = res["out"]
+    status = int(out[3][0].item())
     rqlp.rqlp_profile_read()          # drop records from the warm-up
     rqlp.rqlp_profile_enable(True)
     clocks = ClockSampler(local)
     l0 = rqlp.rqlp_kernel_launches()
-    st = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    barrier()
-    e0.record(st)
-    for _ in range(a.steps):
-        step()
-    e1.record(st)
-    barrier()
+    ms_step = time_steps(ctx, step, a.steps)
     launches = rqlp.rqlp_kernel_launches() - l0
     rqlp.rqlp_profile_enable(False)
     ck = clocks.stop()
-    ms_total = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms_total], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
     recs = rqlp.rqlp_profile_read()
-    ms_step = ms_total / a.steps
-    value = world * apass_bytes(a) / (ms_step * 1e-3) / 1e9
+    if res is not None:
+        q_used, p_used = res["qp"]
+        out = res["out"]
+    d = a.k + p_used
+    abytes = (2 * q_used + 2) * a.m * a.n * 4
+    value = world * abytes / (ms_step * 1e-3) / 1e9
+    roof, sha = roofline(a, recs, d, prec, peaks, dev)
 
-    # Dominant kernel: the pass over A (A^T X / A X products), timed per launch.
-    peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
-    by_tag = {0: [r[0] for r in recs if r[1] == 0], 1: [r[0] for r in recs if r[1] == 1]}
-    dom = max(by_tag, key=lambda t: sum(by_tag[t]))
-    pass_ms = statistics.mean(by_tag[dom]) if by_tag[dom] else float("nan")
-    flops = 2.0 * a.m * a.n * d
-    sm_max = peaks.get("sm_max_mhz", 2070.0)
-    props = torch.cuda.get_device_properties(dev)
-    nsm = props.multi_processor_count
-    kname = {0: "pass_AX", 1: "pass_AtX"}[dom]
-    sha = kernel_sha()
-    if prec == rqlp.PREC_FP32:
-        peak = nsm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-        roof = {"bound": "alu", "achieved": flops / (pass_ms * 1e-3) / 1e12, "peak": peak,
-                "unit": "TFLOP/s", "peak_source": f"derived: {nsm} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz"}
-    else:
-        # The split form's algorithm is three BF16 products per pass (A_hi X_hi +
-        # A_hi X_lo + A_lo X_hi); the pass timed is a power-pass / projection one.
-        peak = peaks.get("bf16_tflops_sustained", 1683.0)
-        mma_flops = 3 * flops
-        roof = {"bound": "tensor", "achieved": mma_flops / (pass_ms * 1e-3) / 1e12, "peak": peak,
-                "unit": "TFLOP/s", "flops_per_launch": mma_flops,
-                "peak_source": "MEASURED_PEAKS bf16_tflops_sustained (of measured)"}
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    roof.setdefault("flops_per_launch", flops)
-    roof["traffic"] = traffic_for(f"{kname}_{'fp32' if prec == 0 else 'bf16x3'}", sha)
-    roof["kernel"] = kname
-    roof["launch_ms"] = pass_ms
-    roof["hbm_gbs"] = a.m * a.n * 4 / (pass_ms * 1e-3) / 1e9
-    roof["hbm_frac_of_measured"] = roof["hbm_gbs"] / peaks.get("hbm_gbs", 6761.6)
-
-    # Accuracy of the timed form (Q L P^T = A P~ P~^T, so the residual follows from
-    # ||A||_F^2 - ||L||_F^2) and the plain-FP32 form timed on the same inputs.
-    dg = diag.cpu().tolist()
-    relres = (max(dg[2], 0.0) / dg[0]) ** 0.5 if dg[0] > 0 else float("nan")
-    compare = {"form": "fp32" if prec == rqlp.PREC_FP32 else "bf16x3", "rel_residual": relres}
-    if prec != rqlp.PREC_FP32 and not a.no_compare:
-        out32 = (torch.empty_like(Q), torch.empty_like(L), torch.empty_like(P), torch.empty_like(info),
-                 torch.empty_like(diag))
-        ws32 = torch.empty(rqlp.rqlp_workspace_bytes(a.m, a.n, a.k, a.p, a.q, rqlp._opts(rqlp.PREC_FP32)) + 256,
-                           dtype=torch.uint8, device=dev)
-        rqlp.factor(A, a.k, a.p, a.q, Om, precision=rqlp.PREC_FP32, workspace=ws32, out=out32)
-        barrier()
-        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        nf = 3
-        f0.record(st)
-        for _ in range(nf):
-            rqlp.factor(A, a.k, a.p, a.q, Om, precision=rqlp.PREC_FP32, workspace=ws32, out=out32)
-        f1.record(st)
-        barrier()
-        d32 = out32[4].cpu().tolist()
-        compare["fp32_ms_per_step"] = f0.elapsed_time(f1) / nf
-        compare["fp32_rel_residual"] = (max(d32[2], 0.0) / d32[0]) ** 0.5
+    compare.update({"form": ("learned_" if form == "learned" else "fixed_") + ("fp32" if prec == 0 else "bf16x3"),
+                    "qp": [q_used, p_used], **judge(out[2])})
+    if target is not None:
+        compare["requested_excess_error"] = target
+    if "fp32_ms_per_step" in compare:
         compare["speedup_vs_fp32"] = compare["fp32_ms_per_step"] / ms_step
-        # ||L_split - L_fp32|| on the leading-k diagonal (both against the same A)
-        l16 = torch.diagonal(L)[: a.k].double()
-        l32 = torch.diagonal(out32[1])[: a.k].double()
-        compare["lead_k_Lii_rel_diff_vs_fp32"] = float(((l16 - l32).abs() / l32.abs()).max())
-        del ws32, out32
+    if form == "learned" and not a.no_compare:
+        # the split form with the fixed (2, 10): what the prediction changed
+        s16, o16 = fixed_runner(a, A, Om, 2, 10, rqlp.PREC_BF16X3, dev)
+        s16()
+        ctx.barrier()
+        compare["bf16x3_fixed_ms_per_step"] = time_steps(ctx, s16, 3)
+        acc16 = judge(o16[2])
+        compare["bf16x3_fixed_excess_error"] = acc16["excess_error"]
+        compare["bf16x3_fixed_rel_residual"] = acc16["rel_residual"]
+        del s16, o16
         torch.cuda.empty_cache()
+    if learned_note:
+        compare["learned"] = learned_note
 
-    # End to end through the host-buffer entry point (pinned buffers).
     e2e = None
     if not a.no_e2e:
-        hA = A.cpu().pin_memory()
-        hO = Om.cpu().pin_memory()
-        hout = (torch.empty(a.m, d).pin_memory(), torch.empty(d, d).pin_memory(),
-                torch.empty(a.n, d).pin_memory(), torch.zeros(2, dtype=torch.int32),
-                torch.zeros(4, dtype=torch.float64))
-        hws = torch.empty(rqlp.rqlp_host_workspace_bytes(a.m, a.n, a.k, a.p, a.q, opts) + 256,
-                          dtype=torch.uint8, device=dev)
         torch.cuda.empty_cache()
-        for _ in range(max(1, a.warmup)):
-            rqlp.factor_host(hA, a.k, a.p, a.q, hO, precision=prec, workspace=hws, out=hout)
-        barrier()
-        t0 = time.perf_counter()
-        for _ in range(a.steps):
-            rqlp.factor_host(hA, a.k, a.p, a.q, hO, precision=prec, workspace=hws, out=hout)
-        barrier()
-        dt = (time.perf_counter() - t0) / a.steps
-        if world > 1:
-            t = torch.tensor([dt], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
-        h2d = 4 * (a.m * a.n + a.m * d)
-        d2h = 4 * (a.m * d + d * d + a.n * d) + 8 + 32
-        e2e = {"value": world * apass_bytes(a) / dt / 1e9, "unit": "GB/s", "ms_per_step": dt * 1e3,
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+        if form == "learned":
+            e2e = e2e_learned(a, ctx, A, Om, params, target, prec, a.steps, a.warmup)
+        else:
+            e2e = e2e_fixed(a, ctx, A, Om, a.q, a.p, prec, a.steps, a.warmup)
 
-    A_keep = A
     cpu = None
     if rank == 0 and not a.no_cpu_baseline:
         S = a.sample or 4000
-        gbs, dt, cores = oracle_time(a, *oracle_inputs(a, S, A_keep))
+        import argparse as _ap
+        ao = _ap.Namespace(**vars(a))
+        ao.q, ao.p = q_used, p_used
+        gbs, dt, cores = oracle_time(ao, *oracle_inputs(ao, S, A))
         cpu = {"value": gbs, "unit": "GB/s", "cores": cores, "kind": "oracle",
                "sample": f"FP64 oracle chain on the leading {S}x{S} block of the workload's A "
-                         f"(q={a.q}, d={d}), {dt:.1f} s"}
+                         f"(q={q_used}, d={d}), {dt:.1f} s"}
+
+    del A, Om, judge
+    torch.cuda.empty_cache()
+    batched = None if a.no_batched else batched_leg(a, ctx)
 
     if rank == 0:
+        ao = argparse.Namespace(**vars(a))
+        ao.q, ao.p = q_used, p_used
         line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": a.steps,
                 "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32" if prec == rqlp.PREC_FP32 else "bf16x3",
                 "data": "synthetic",
-                "config": {"workload": workload_name(a), "m": a.m, "n": a.n, "k": a.k, "p": a.p,
-                           "q": a.q, "precision": "fp32" if prec == 0 else "bf16x3",
-                           "A_bytes_per_step": apass_bytes(a),
+                "config": {"workload": workload_name(ao), "m": a.m, "n": a.n, "k": a.k, "p": p_used, "q": q_used,
+                           "form": compare["form"], "A_bytes_per_step": abytes,
                            "l2": "inputs larger than L2 (A is %.1f GB)" % (a.m * a.n * 4 / 1e9),
                            "parallelism": "replicas" if world > 1 else "single"},
                 "status": status, "clocks": ck, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-                "compare": compare,
+                "compare": compare, "batched": batched,
                 "gpu_launches": launches, "kernel_sha": sha}
         print(json.dumps(line), flush=True)
     if world > 1:

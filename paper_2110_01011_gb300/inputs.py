@@ -169,6 +169,36 @@ def low_rank_matrix_torch(m: int, n: int, sigma: np.ndarray, noise: float, seed:
         torch.backends.cuda.matmul.allow_tf32 = prev
 
 
+def low_rank_matrix_reflect(m: int, n: int, sigma: np.ndarray, seed: int, device="cuda", reflectors: int = 4):
+    """A = U diag(sigma) V^T (FP32, on ``device``) with U, V the first
+    r = min(m, n) columns of products of ``reflectors`` random Householder
+    reflectors: exactly orthonormal, dense, and built from elementwise ops and
+    one matmul only (no device QR). A Gaussian Omega is rotation invariant,
+    so the sketch's error law depends on sigma alone; these matrices stand in
+    for Haar ones where many large matrices are needed quickly."""
+    import torch
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed))
+    r = min(m, n)
+
+    def basis(rows):
+        X = torch.zeros(rows, r, device=device, dtype=torch.float32)
+        X.diagonal().fill_(1.0)
+        for _ in range(reflectors):
+            v = torch.randn(rows, generator=gen, device=device, dtype=torch.float32)
+            v /= torch.sqrt((v * v).sum())
+            X -= 2.0 * torch.outer(v, v @ X)
+        return X
+
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        U = basis(m) * torch.as_tensor(np.asarray(sigma[:r], dtype=np.float32), device=device)
+        return (U @ basis(n).T).contiguous()
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+
+
 def omega_torch(m: int, d: int, seed: int, device="cuda", bf16_exact: bool = False):
     """Gaussian Omega drawn on the host (``omega``) and copied to ``device``."""
     import torch

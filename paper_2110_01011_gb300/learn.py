@@ -18,7 +18,10 @@ matrix A and Gaussian Omega of width w = k + 20:
   exact to ~1e-11 of the tail for tails >= 0.3 % of ||A||_F);
 * rows: several requested errors per matrix, log-uniform in [1e-3, 1e-1];
   label = the cheapest pair, by cost (2q + 2)(k + p) (ties: smaller q, then
-  smaller p), whose eps is at most the request; (4, 20) when none is.
+  smaller p), whose eps is at most the request / LABEL_MARGIN; (4, 20) when
+  none is. The margin keeps the prediction on the safe side of a boundary
+  that the features only approximate: without it about a third of the
+  predictions for 1-3 % requests missed the request.
 
 The MLP is trained with the library's kernels (``rqlp_mlp_grad``,
 ``rqlp_mlp_adam``). Trained weights (standardisation folded into the first
@@ -40,6 +43,7 @@ import numpy as np
 from . import inputs, rqlp
 
 TARGET = 1e-3                    # the headline request
+LABEL_MARGIN = 2.0               # labels aim at request / LABEL_MARGIN
 TARGET_RANGE = (1e-3, 1e-1)      # requests seen in training
 EVAL_TARGETS = (1e-3, 3e-3, 1e-2, 3e-2, 1e-1)
 Q_CHOICES = rqlp.Q_CHOICES
@@ -144,7 +148,7 @@ def eps_table(A, Om, k, tail2):
     return tab
 
 
-def build_dataset(count, seed, device, log_every=500):
+def build_dataset(count, seed, device, log_every=500, n_range=(384, 2048)):
     """Probe features (12 statistics; the 13th input is added per request),
     error tables, k and sizes for ``count`` generated matrices."""
     import torch
@@ -152,7 +156,7 @@ def build_dataset(count, seed, device, log_every=500):
     feats, ks, tabs, meta = [], [], [], []
     t0 = time.time()
     for i in range(count):
-        m, n, k, sig, kind = draw_problem(g)
+        m, n, k, sig, kind = draw_problem(g, n_range=n_range)
         A = make_matrix(m, n, sig, seed * 1000003 + i, device)
         Om = torch.from_numpy(inputs.omega(m, k + 20, seed=seed * 7919 + i)).to(device)
         tail2 = float((sig[k:] ** 2).sum())
@@ -166,13 +170,14 @@ def build_dataset(count, seed, device, log_every=500):
     return np.array(feats), np.array(ks), np.array(tabs), np.array(meta, dtype=object)
 
 
-def rows(feats, ks, tabs, targets):
-    """Training rows: for matrix i and request t, features + log10 t and the label."""
+def rows(feats, ks, tabs, targets, margin=LABEL_MARGIN):
+    """Training rows: for matrix i and request t, features + log10 t and the
+    label for t / margin."""
     X, yq, yp, idx, ts = [], [], [], [], []
     for i in range(len(ks)):
         for t in targets[i]:
             X.append(np.concatenate([feats[i], [math.log10(t)]]))
-            a, b = label_from_table(tabs[i], ks[i], t)
+            a, b = label_from_table(tabs[i], ks[i], t / margin)
             yq.append(a)
             yp.append(b)
             idx.append(i)
@@ -339,6 +344,8 @@ def main():
     ap.add_argument("--lr", type=float, default=3e-3)
     ap.add_argument("--out", default="learn_out")
     ap.add_argument("--data", default=None, help="reuse a qp_dataset.npz instead of generating one")
+    ap.add_argument("--large", type=int, default=0,
+                    help="add this many training matrices with n in [2048, 8192] (and a fifth as many to test)")
     ap.add_argument("--save", action="store_true", help="write data/qp_mlp.f32")
     a = ap.parse_args()
     import torch
@@ -350,6 +357,14 @@ def main():
     else:
         ftr, ktr, tabtr, _ = build_dataset(a.train, seed=501, device="cuda")
         fte, kte, tabte, _ = build_dataset(a.test, seed=909, device="cuda")
+    if a.large > 0:
+        big = (2048, 8192)
+        f2, k2, t2, _ = build_dataset(a.large, seed=601, device="cuda", log_every=50, n_range=big)
+        f3, k3, t3, _ = build_dataset(max(1, a.large // 5), seed=919, device="cuda", log_every=50, n_range=big)
+        # interleave so that the validation slice (the first tenth) holds both sizes
+        order = np.random.default_rng(5).permutation(len(ktr) + len(k2))
+        ftr, ktr, tabtr = (np.concatenate([x, y])[order] for x, y in ((ftr, f2), (ktr, k2), (tabtr, t2)))
+        fte, kte, tabte = (np.concatenate([x, y]) for x, y in ((fte, f3), (kte, k3), (tabte, t3)))
     t_data = time.time() - t0
     # 10 % of the training matrices (all their requests) validate the early stop
     nv = max(1, len(ktr) // 10)
@@ -366,12 +381,13 @@ def main():
     params = fold_standardisation(params, mu, sd)
     ev = evaluate(params, fte, tabte, kte)
     report = {"train_matrices": int(len(ktr)), "train_rows": int(len(yqtr)), "val_rows": int(len(yqva)),
+              "label_margin": LABEL_MARGIN,
               "test_matrices": int(len(kte)), "steps": a.steps, "lr": a.lr, "target_range": TARGET_RANGE,
               "seconds_data": t_data, "seconds_train": t_train, "curve": curve,
               "label_hist_q": np.bincount(yqtr, minlength=5).tolist(),
               "label_hist_p": np.bincount(yptr, minlength=3).tolist(), "test": ev}
     os.makedirs(a.out, exist_ok=True)
-    if not a.data:
+    if not a.data or a.large > 0:
         np.savez(os.path.join(a.out, "qp_dataset.npz"), ftr=ftr, ktr=ktr, tabtr=tabtr, fte=fte, kte=kte,
                  tabte=tabte)
     with open(os.path.join(a.out, "qp_report.json"), "w") as f:

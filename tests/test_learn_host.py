@@ -54,7 +54,7 @@ def test_rows_and_labels():
     tab[3, 0] = 5e-3        # feasible for requests >= 5e-3
     tab[4, 2] = 5e-4        # feasible for requests >= 5e-4
     tabs = np.array([tab, tab])
-    X, yq, yp, idx, ts = learn.rows(feats, np.array([20, 40]), tabs, [[1e-2, 1e-3], [1e-4]])
+    X, yq, yp, idx, ts = learn.rows(feats, np.array([20, 40]), tabs, [[1e-2, 1e-3], [1e-4]], margin=1.0)
     assert X.shape == (3, 13) and list(idx) == [0, 0, 1]
     np.testing.assert_allclose(X[:, 12], np.log10([1e-2, 1e-3, 1e-4]))
     assert (yq[0], yp[0]) == (3, 0) and (yq[1], yp[1]) == (4, 2) and (yq[2], yp[2]) == (4, 2)
@@ -73,3 +73,15 @@ def test_evaluate_at_counts():
     assert r["default_success"] == 0.5 and r["matched_fixed"] is None
     r = learn.evaluate_at(np.array([0, 0]), np.array([0, 0]), tabs, ks, 1e-2)
     assert r["learned_success"] == 0.5 and r["matched_fixed"] == [0, 5]
+
+
+def test_rows_margin_tightens_labels():
+    feats = np.zeros((1, 12))
+    tab = np.full((5, 3), np.inf)
+    tab[1, 0] = 8e-3        # reaches 1e-2, not 1e-2 / 2
+    tab[3, 0] = 4e-3        # reaches both
+    tabs = np.array([tab])
+    _, yq, yp, _, _ = learn.rows(feats, np.array([20]), tabs, [[1e-2]], margin=1.0)
+    assert (yq[0], yp[0]) == (1, 0)
+    _, yq, yp, _, _ = learn.rows(feats, np.array([20]), tabs, [[1e-2]], margin=2.0)
+    assert (yq[0], yp[0]) == (3, 0)
