@@ -52,7 +52,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--form", default="learned", choices=["learned", "fixed"])
+    ap.add_argument("--form", default="learned", choices=["learned", "fixed", "batched"],
+                    help="batched: only the batched leg, printed as its own line")
+    ap.add_argument("--target", type=float, default=None,
+                    help="learned form: this request instead of the excess error FP32 (2, 10) reaches")
     ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "bf16x3"],
                     help="--form fixed: the form timed (auto = bf16x3)")
     ap.add_argument("--m", type=int, default=20000)
@@ -65,6 +68,7 @@ def parse():
     ap.add_argument("--no-compare", action="store_true", help="skip timing the plain FP32 form")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched form")
     ap.add_argument("--batch", type=int, default=512)
+    ap.add_argument("--no-autotune", action="store_true", help="batched leg: default tile shapes")
     ap.add_argument("--sample", type=int, default=0,
                     help="rows/cols of the oracle's sample block (0 = default for the workload)")
     return ap.parse_args()
@@ -361,7 +365,7 @@ def batched_leg(a, ctx):
     Os = [inputs.omega_torch(pr.m, pr.d, pr.seed + 1, ctx.dev) for pr in probs]
     gen_s = time.perf_counter() - t0
     b = rqlp.Batch(As, Os, [pr.k for pr in probs], [pr.p for pr in probs], probs[0].q)
-    tune = b.autotune(reps=2)
+    tune = None if a.no_autotune else b.autotune(reps=2)
     for _ in range(max(1, a.warmup)):
         b.launch()
     ctx.barrier()
@@ -471,6 +475,20 @@ def main():
     ctx = Ctx(world, rank, dev)
     rqlp.load()
     peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
+    if a.form == "batched":
+        ck = ClockSampler(local)
+        bt = batched_leg(a, ctx)
+        clocks = ck.stop()
+        if rank == 0:
+            line = {"metric": "batched Rand-QLP A-pass GB/s", "value": bt["value"], "unit": "GB/s", "n_gpus": world,
+                    "steps": max(3, a.steps), "warmup": max(1, a.warmup), "ms_per_step": bt["ms_per_batch"],
+                    "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                    "data": "synthetic", "config": {"workload": bt["workload"], "l2": "inputs larger than L2"},
+                    "clocks": clocks, "batched": bt}
+            print(json.dumps(line), flush=True)
+        if world > 1:
+            dist.destroy_process_group()
+        return
     A, Om = make_inputs(a, dev)
 
     params = None
@@ -487,7 +505,7 @@ def main():
     # The plain FP32 form with the fixed (2, 10): its time and the accuracy the
     # learned form is asked to match.
     target = None
-    if form == "learned" or (not a.no_compare and a.precision != "fp32"):
+    if (form == "learned" and a.target is None) or (form == "fixed" and not a.no_compare and a.precision != "fp32"):
         step32, out32 = fixed_runner(a, A, Om, 2 if form == "learned" else a.q, 10 if form == "learned" else a.p,
                                      rqlp.PREC_FP32, dev)
         step32()
@@ -499,6 +517,8 @@ def main():
         target = min(max(acc32["excess_error"], 1e-3), 0.5)
         del out32, step32
         torch.cuda.empty_cache()
+    if form == "learned" and a.target is not None:
+        target = a.target
 
     prec = rqlp.PREC_BF16X3
     if form == "fixed":

@@ -4,8 +4,9 @@
 //
 // Blocked right-looking elimination on the augmented matrix [G | I] with
 // 16-column panels:
-//   (1) one warp factors the 16 x 16 diagonal block (row per lane, shuffles)
-//       and inverts it (column per lane): L_JJ, D = L_JJ^{-1};
+//   (1) one warp factors the 16 x 16 diagonal block (left-looking, row per
+//       lane, rows of L_JJ broadcast by shuffles) and inverts it (column per
+//       lane, same broadcasts): L_JJ, D = L_JJ^{-1};
 //   (2) panel L_IJ = G_IJ D^T for the rows below, and the block row of W:
 //       W_J,: = D X_J,: (X = the eliminated identity, W_JJ = D);
 //   (3) trailing updates G_II -= L_IJ L_IJ^T (lower part) and
@@ -83,7 +84,7 @@ __device__ __forceinline__ void chol_body(int d, const float* __restrict__ G, in
   T* PT = gS != nullptr ? dyn : dyn + (size_t)d * LDS;
   T* WT = PT + NB * PTLD;
   __shared__ T gdiag[kMaxD], wdiag[kMaxD];
-  __shared__ T Lb[NB][NB + 1], Dinv[NB][NB + 1], rdiag[NB];
+  __shared__ T Dinv[NB][NB + 1], rdiag[NB];
   __shared__ T s_red[32];
   __shared__ int s_fail;
 
@@ -123,59 +124,45 @@ __device__ __forceinline__ void chol_body(int d, const float* __restrict__ G, in
     fail = -1;
     for (int j0 = 0; j0 < d; j0 += NB) {
       const int jb = min(NB, d - j0);
-      // (1) diagonal block: Cholesky (lane = row) and inverse (lane = column).
+      // (1) diagonal block, warp 0 (lane = row): left-looking Cholesky, row j
+      // of L_JJ broadcast by shuffles, one reciprocal square root per column;
+      // then D = L_JJ^{-1} with lane = column, rows of L_JJ broadcast the same
+      // way. Everything stays in registers until the results are stored.
       if (warp == 0) {
-        T a[NB];
+        T l[NB];
 #pragma unroll
-        for (int k = 0; k < NB; ++k) a[k] = (lane < jb && k <= lane) ? S[(size_t)(j0 + lane) * LDS + j0 + k] : (T)0;
+        for (int k = 0; k < NB; ++k) l[k] = (lane < jb && k <= lane) ? S[(size_t)(j0 + lane) * LDS + j0 + k] : (T)0;
         int f = -1;
 #pragma unroll
-        for (int k = 0; k < NB; ++k) {
-          if (k < jb && f < 0) {
-            const T piv = __shfl_sync(0xffffffffu, a[k], k);
-            if (!(piv > rel_tol * gdiag[j0 + k]) || !isfinite(piv)) {
-              f = j0 + k;
-            } else {
-              // One reciprocal square root gives both 1/L_kk and L_kk = piv / sqrt(piv).
-              const T rl = rsqrt(piv), lkk = piv * rl;
-              if (lane == k) a[k] = lkk;
-              else if (lane > k) a[k] *= rl;
-              if (lane == 0) rdiag[k] = rl;
-              const T lik = a[k];
+        for (int j = 0; j < NB; ++j) {
+          if (j < jb && f < 0) {
+            T s = l[j];                       // a_ij - sum_{t<j} l_it l_jt
 #pragma unroll
-              for (int j = k + 1; j < NB; ++j) {
-                const T ljk = __shfl_sync(0xffffffffu, lik, j);
-                if (j < jb && lane >= j) a[j] -= lik * ljk;
-              }
+            for (int t = 0; t < j; ++t) s -= l[t] * __shfl_sync(0xffffffffu, l[t], j);
+            const T piv = __shfl_sync(0xffffffffu, s, j);
+            if (!(piv > rel_tol * gdiag[j0 + j]) || !isfinite(piv)) {
+              f = j0 + j;
+            } else {
+              const T rl = rsqrt(piv);
+              if (lane == 0) rdiag[j] = rl;
+              l[j] = lane == j ? piv * rl : (lane > j ? s * rl : (T)0);
             }
           }
         }
         if (f < 0) {
 #pragma unroll
-          for (int k = 0; k < NB; ++k) {
-            if (lane < jb && k <= lane) {
-              Lb[lane][k] = a[k];
-              S[(size_t)(j0 + lane) * LDS + j0 + k] = a[k];
-            }
-          }
+          for (int k = 0; k < NB; ++k)
+            if (lane < jb && k <= lane) S[(size_t)(j0 + lane) * LDS + j0 + k] = l[k];
           __syncwarp();
-          const int c = lane;
+          const int c = lane;   // column of D: x[i] = D_ic
           T x[NB];
 #pragma unroll
           for (int i = 0; i < NB; ++i) {
-            T v = 0;
-            if (c < jb && i < jb) {
-              if (i == c) {
-                v = rdiag[c];
-              } else if (i > c) {
-                T s2 = 0;
+            T s = 0;
 #pragma unroll
-                for (int t = 0; t < NB; ++t)
-                  if (t >= c && t < i) s2 += Lb[i][t] * x[t];
-                v = -s2 * rdiag[i];
-              }
-            }
-            x[i] = v;
+            for (int t = 0; t < i; ++t) s += __shfl_sync(0xffffffffu, l[t], i) * x[t];
+            const T ri = rdiag[i];
+            x[i] = (i < c || i >= jb) ? (T)0 : (i == c ? ri : -s * ri);
           }
 #pragma unroll
           for (int i = 0; i < NB; ++i)
@@ -189,7 +176,8 @@ __device__ __forceinline__ void chol_body(int d, const float* __restrict__ G, in
         break;
       }
       const int jn = j0 + jb, Nt = d - jn;
-      // (2) panel rows below the block, block row of W, and W's diagonal block.
+      // (2) panel rows below the block, block row of W, and W's diagonal
+      // block. Results are computed in registers and stored afterwards.
       for (int idx = tid; idx < Nt + jn; idx += blockDim.x) {
         if (idx < Nt) {
           const int i = jn + idx;
@@ -202,14 +190,15 @@ __device__ __forceinline__ void chol_body(int d, const float* __restrict__ G, in
 #pragma unroll
             for (int k = 0; k <= c; ++k) s2 += v[k] * Dinv[c][k];
             o[c] = s2;
-            PT[c * PTLD + i] = s2;
           }
+#pragma unroll
+          for (int c = 0; c < NB; ++c) PT[c * PTLD + i] = o[c];
 #pragma unroll
           for (int k = 0; k < NB; k += 4) st4(&S[(size_t)i * LDS + j0 + k], &o[k]);
         } else {
           const int c = idx - Nt;
           if (c < j0) {
-            T w[NB];
+            T w[NB], o[NB];
             if (jb == NB) {
 #pragma unroll
               for (int k = 0; k < NB; k += 4) ld4(&S[(size_t)c * LDS + j0 + k], &w[k]);
@@ -218,24 +207,28 @@ __device__ __forceinline__ void chol_body(int d, const float* __restrict__ G, in
               for (int k = 0; k < NB; ++k) w[k] = k < jb ? S[(size_t)c * LDS + j0 + k] : (T)0;
             }
 #pragma unroll
-            for (int r = 0; r < NB; ++r) {
-              if (r < jb) {
-                T s2 = 0;
+            for (int rr = 0; rr < NB; ++rr) {
+              T s2 = 0;
 #pragma unroll
-                for (int k = 0; k <= r; ++k) s2 += Dinv[r][k] * w[k];
-                S[(size_t)c * LDS + j0 + r] = s2;
-                WT[r * PTLD + c] = s2;
+              for (int k = 0; k <= rr; ++k) s2 += Dinv[rr][k] * w[k];
+              o[rr] = s2;
+            }
+#pragma unroll
+            for (int rr = 0; rr < NB; ++rr) {
+              if (rr < jb) {
+                S[(size_t)c * LDS + j0 + rr] = o[rr];
+                WT[rr * PTLD + c] = o[rr];
               }
             }
           } else {
             const int cc = c - j0;
             wdiag[c] = Dinv[cc][cc];
 #pragma unroll
-            for (int r = 0; r < NB; ++r) {
-              if (r < jb) {
-                const T wv = r >= cc ? Dinv[r][cc] : (T)0;
-                if (r > cc) S[(size_t)c * LDS + j0 + r] = wv;
-                WT[r * PTLD + c] = wv;
+            for (int rr = 0; rr < NB; ++rr) {
+              if (rr < jb) {
+                const T wv = rr >= cc ? Dinv[rr][cc] : (T)0;
+                if (rr > cc) S[(size_t)c * LDS + j0 + rr] = wv;
+                WT[rr * PTLD + c] = wv;
               }
             }
           }
@@ -339,7 +332,7 @@ size_t square_bytes(int d) { return (size_t)d * lds_of(d) * sizeof(T); }
 template <typename T>
 size_t panel_bytes(int d) { return (size_t)2 * NB * ptld_of(d) * sizeof(T); }
 template <typename T>
-size_t static_bytes() { return (2 * kMaxD + 2 * NB * (NB + 1) + NB + 32) * sizeof(T) + 64; }
+size_t static_bytes() { return (2 * kMaxD + NB * (NB + 1) + NB + 32) * sizeof(T) + 64; }
 template <typename T>
 bool square_in_smem(int d) {
   return square_bytes<T>(d) + panel_bytes<T>(d) + static_bytes<T>() <= smem_optin_chol();
