@@ -2,8 +2,9 @@
 """Benchmark: Rand-QLP time-to-factor and A-pass GB/s on one GB300.
 
 Workload: A = U_r diag(exp(-i/50)) V_r^T + 1e-6 G / sqrt(n), 20000 x 20000
-FP32 (Haar U_r, V_r, r = 1000), k = 200, Gaussian Omega 20000 x 220 (its
-first k + p columns are the sketch's test matrix).
+FP32 (Haar U_r, V_r, r = 1000), k = 200, Gaussian Omega 20000 x 220 rounded
+to BF16-representable values (its first k + p columns are the sketch's test
+matrix; every form then sketches with the same one).
 
 Headline (``--form learned``, the default): the BF16-split tensor-core form
 with (q, p) predicted by the trained network for the excess rank-k error that
@@ -96,7 +97,8 @@ def make_inputs(a, device):
     """A and an Omega wide enough for the probe (k + 20 columns)."""
     from paper_2110_01011_gb300 import inputs
     A = inputs.low_rank_matrix_torch(a.m, a.n, spectrum(), 1e-6, seed=1002, rank=SPECTRUM_RANK, device=device)
-    Om = inputs.omega_torch(a.m, a.k + 20, seed=2002, device=device)
+    # BF16-representable, so that every form sketches with the same test matrix
+    Om = inputs.omega_torch(a.m, a.k + 20, seed=2002, device=device, bf16_exact=True)
     return A, Om
 
 
@@ -188,7 +190,7 @@ def oracle_inputs(a, S, A=None):
         dev = "cuda" if torch.cuda.is_available() else "cpu"
         A = inputs.low_rank_matrix_torch(a.m, a.n, spectrum(), 1e-6, seed=1002, rank=SPECTRUM_RANK, device=dev)
     As = A[:S, :S].double().cpu().numpy()
-    Om = inputs.omega(a.m, a.k + 20, seed=2002)[:S, :a.k + a.p].astype(np.float64)
+    Om = inputs.omega(a.m, a.k + 20, seed=2002, bf16_exact=True)[:S, :a.k + a.p].astype(np.float64)
     return As, Om
 
 

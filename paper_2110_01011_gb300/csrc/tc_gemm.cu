@@ -45,6 +45,13 @@ constexpr int kMaxStages = 8;
 constexpr long long kWaitLimit = 4000000000LL;   // cycles (~2 s) before a wait gives up
 constexpr uint32_t kABytes = BM * BK * 2;        // one BF16 A tile (8 KB)
 constexpr int kMaxSlots = 16;                    // partial tiles summed from a cached slot list
+// The FP32 accumulation of tcgen05.mma in TMEM loses a little of every add in
+// the same direction: over K = 20000 a pass shrinks by ~1.5e-6 relative to
+// its partial sums, which the cancelling small-singular-value columns of
+// A P~ turn into ~1e-4 of their own size (and into the leading diagonal of
+// L). Accumulation chains in TMEM are therefore cut every kChunk k-blocks
+// (K = 2048); the epilogue adds the chunks in FP32 with round-to-nearest.
+constexpr int kChunk = 64;
 
 struct TcArgs {
   int M, K, d, npad, kblocks, tiles, G, stages;
@@ -73,6 +80,12 @@ __device__ inline long long cta_begin(const int c, const long long units, const 
 // The CTA whose unit range holds unit u (empty ranges never match).
 __host__ __device__ inline int unit_owner(long long u, long long units, int G) {
   return (int)(((u + 1) * G + units - 1) / units) - 1;
+}
+
+// End of the accumulation chunk that starts at unit u (a CTA's range [.., u1)).
+__device__ inline long long chunk_end(long long u, long long u1, int KB) {
+  const long long t_end = (u / KB + 1) * (long long)KB;
+  return min(min(u1, t_end), u + kChunk);
 }
 
 __device__ void post_timeout(int* info) {
@@ -168,8 +181,7 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant_
     bool ok = true;
     long long u = u0;
     while (u < u1 && ok) {
-      const int t = (int)(u / KB);
-      const long long seg_begin = u, seg_end = std::min(u1, (long long)(t + 1) * KB);
+      const long long seg_begin = u, seg_end = chunk_end(u, u1, KB);
       const int ab = seg & 1;
       if (!tc::mbar_wait(&acce[ab], (uint32_t)(((seg >> 1) & 1) ^ 1), kWaitLimit)) { ok = false; break; }
       tc::tc_fence_after();
@@ -213,8 +225,11 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant_
     long long u = u0;
     while (u < u1) {
       const int t = (int)(u / KB);
-      const long long seg_begin = u, seg_end = std::min(u1, (long long)(t + 1) * KB);
-      const bool whole = seg_begin == (long long)t * KB && seg_end == (long long)(t + 1) * KB;
+      const long long seg_begin = u, seg_end = chunk_end(u, u1, KB);
+      // This CTA's part of tile t, and where the chunk sits in it.
+      const long long tb = std::max(u0, (long long)t * KB), te = std::min(u1, (long long)(t + 1) * KB);
+      const bool whole = tb == (long long)t * KB && te == (long long)(t + 1) * KB;
+      const bool first_chunk = seg_begin == tb, last_chunk = seg_end == te;
       const int ab = seg & 1;
       // One thread waits; the verdict is shared so the four warps stay in step.
       if (threadIdx.x == 0) *epi_ok = tc::mbar_wait(&accf[ab], (uint32_t)((seg >> 1) & 1), kWaitLimit) ? 1 : 0;
@@ -232,7 +247,7 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant_
         dst = a.out + gm * a.ldo;
         ncols = gm < a.M ? a.d : 0;
       } else {
-        const int slot = seg == 0 ? 2 * cta : 2 * cta + 1;
+        const int slot = (tb == u0) ? 2 * cta : 2 * cta + 1;   // first or last tile of the range
         dst = a.part + ((long long)slot * BM + row) * a.npad;
         ncols = a.npad;
       }
@@ -242,17 +257,24 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant_
         tc::tmem_ld16(taddr + (uint32_t)c0, v);
         if (vec && c0 + 16 <= ncols) {
           float4* d4 = reinterpret_cast<float4*>(dst + c0);
+          if (!first_chunk) {   // this thread wrote the row's earlier chunks
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const float4 o = d4[q];
+              v[4 * q] += o.x; v[4 * q + 1] += o.y; v[4 * q + 2] += o.z; v[4 * q + 3] += o.w;
+            }
+          }
 #pragma unroll
           for (int q = 0; q < 4; ++q) d4[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
         } else {
 #pragma unroll
           for (int i = 0; i < 16; ++i)
-            if (c0 + i < ncols) dst[c0 + i] = v[i];
+            if (c0 + i < ncols) dst[c0 + i] = first_chunk ? v[i] : dst[c0 + i] + v[i];
         }
       }
       tc::tc_fence_before();
       tc::mbar_arrive(&acce[ab]);
-      if (!whole) {
+      if (!whole && last_chunk) {
         // Publish the partial tile; the last CTA to arrive on the tile sums them.
         __threadfence();
         asm volatile("bar.sync 1, 128;" ::: "memory");
