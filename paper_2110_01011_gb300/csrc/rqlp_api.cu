@@ -45,8 +45,9 @@ class Ops {
     if (with_tc) {
       tc_.layout(ar, m, n, dcap_, std::max(m, n), false);
       tc_.set_profiled(true);
-      // Tall d-column operands of CholeskyQR: the Gram on the tensor cores.
-      tcs_.layout(ar, std::max(m, n), dcap_, dcap_, dcap_, true);
+      // Tall d-column operands of CholeskyQR: the Gram (BF16x3) and the
+      // products X R^{-1} (exact mode, six products) on the tensor cores.
+      tcs_.layout(ar, std::max(m, n), dcap_, dcap_, dcap_, true, /*three_part=*/true);
     }
     tc_on_ = with_tc;
   }
@@ -68,6 +69,11 @@ class Ops {
   // columns the leading block of the triangular inverse is the inverse of the
   // leading block, so a probe of a wider sketch serves every narrower width.
   cudaError_t apply_r0(const float* X, int64_t ldx, int64_t rows, float* out, int64_t ldout) {
+    if (tc_on_ && rows > (int64_t)d_) {
+      tcs_.reset();
+      CK(tcs_.split(X, rows, d_, ldx, nullptr, st_));
+      return tcs_.pass(false, X, rows, d_, ldx, Ri_[0], ld_, d_, out, ldout, nullptr, info_, st_, true);
+    }
     return trmm(X, ldx, rows, Ri_[0], out, ldout, nullptr);
   }
 
@@ -110,19 +116,20 @@ class Ops {
     return chol_inv(d_, G_, ld_, R_[slot], Ri_[slot], ld_, info_, &scal[2], gate_out, gate_in, cstore_,
                     o_.small_fp64 != 0, st_);
   }
-  // One CholeskyQR pass (shifted on breakdown) with the Gram on the tensor
-  // cores (BF16x3): out = X R^{-1}; gate_out raised if the Cholesky shifted.
-  // R only has to precondition, so the Gram's rounding leaves the span of the
-  // result untouched; X R^{-1} itself stays in FP32, because its BF16x3 form
-  // errs by 2^-18 of |X| |R^{-1}|, about kappa(X) times the result (measured:
-  // 1.6x the leading-diagonal error of L on the 20000^2 class).
+  // One CholeskyQR pass (shifted on breakdown) on the tensor cores: out =
+  // X R^{-1}; gate_out raised if the Cholesky shifted. R only has to
+  // precondition, so the BF16x3 Gram's rounding leaves the span of the result
+  // untouched. X R^{-1} takes the exact mode: in BF16x3 its error, relative to
+  // |X| |R^{-1}|, would be about kappa(X) times the result (measured: 1.6x the
+  // leading-diagonal error of L on the 20000^2 class); six products bring it
+  // to the FP32 product's level.
   cudaError_t tc_cqr(const float* X, int64_t ldx, int64_t rows, float* out, int64_t ldout, int slot,
                      int* gate_out) {
     tcs_.reset();
     CK(tcs_.split(X, rows, d_, ldx, nullptr, st_));
     CK(tcs_.gram(G_, ld_, info_, st_));
     CK(chol(slot, gate_out, nullptr));
-    return trmm(X, ldx, rows, Ri_[slot], out, ldout, nullptr);
+    return tcs_.pass(false, X, rows, d_, ldx, Ri_[slot], ld_, d_, out, ldout, nullptr, info_, st_, true);
   }
   // One CholeskyQR pass (shifted on breakdown): out = X R^{-1}. have_r0: the
   // R factor is already in slot 0 (the probe).
@@ -143,8 +150,8 @@ class Ops {
     if (have_r0) {   // first pass from the probe's R (slot 0, gate in gates[0])
       CK(apply_r0(X, ldx, rows, tmp, ld_));
     } else if (tc_on_ && rows > (int64_t)d_) {
-      // First pass with the Gram on the tensor cores (its R only preconditions);
-      // the products X R^{-1} and the second pass stay in FP32.
+      // First pass on the tensor cores (BF16x3 Gram, exact-mode X R^{-1});
+      // the second pass, which sets the orthogonality, stays in FP32.
       CK(tc_cqr(X, ldx, rows, tmp, ld_, 0, g));
     } else {
       CK(gram(X, ldx, rows, nullptr));

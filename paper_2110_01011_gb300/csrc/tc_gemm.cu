@@ -8,6 +8,13 @@
 // (the dropped A_lo X_lo term is below 2^-16 relative). When X has no low
 // part (a BF16-exact Omega) the middle product is skipped.
 //
+// Exact mode (the products X R^{-1} of CholeskyQR, K = d): A and X in three
+// parts each, A = A_hi + A_lo + A_lo2 (error 2^-27), and every product above
+// 2^-27, A_hi X_hi + A_hi X_lo + A_lo X_hi + A_lo2 X_hi + A_hi X_lo2 +
+// A_lo X_lo (six). R^{-1} spreads its entries over orders of magnitude, so
+// the two-part form's error, relative to |X| |R^{-1}|, would be kappa(X)
+// times larger relative to the result.
+//
 // Data flow per factorisation: split_a_kernel writes A_hi, A_lo once (and
 // ||A||_F^2); prep_x_kernel writes X_hi^T, X_lo^T (d x K, K-major) before
 // every pass; tc_pass_kernel streams A tiles through shared memory with TMA
@@ -63,6 +70,7 @@ struct TcArgs {
   float* part;               // 2 * G slots of BM x npad floats
   int* tile_cnt;             // per-tile arrival counters (zero between passes)
   const int* xlo_nonzero;    // 1 when X has a nonzero low part
+  int exact;                 // 1: A and X in three parts, six products
   int* info;                 // status word (may be null)
   uint32_t idesc, stage_bytes, tmem_cols;
 };
@@ -96,6 +104,7 @@ template <bool MN_A>
 __global__ void __launch_bounds__(kThreads, 1)
 tc_pass_kernel(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUtensorMap tmAlo,
                const __grid_constant__ CUtensorMap tmXhi, const __grid_constant__ CUtensorMap tmXlo,
+               const __grid_constant__ CUtensorMap tmAlo2, const __grid_constant__ CUtensorMap tmXlo2,
                const TcArgs a) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem =
@@ -140,8 +149,11 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant_
   __syncthreads();
   tc::tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
-  const int products = (*a.xlo_nonzero) ? 3 : 2;
+  // Stage layout: A_hi, A_lo[, A_lo2], X_hi[, X_lo[, X_lo2]].
+  const bool ex = a.exact != 0;
+  const int nx = ex ? 3 : ((*a.xlo_nonzero) ? 2 : 1);
   const uint32_t xbytes = (uint32_t)a.npad * BK * 2;
+  const uint32_t xoff = (ex ? 3u : 2u) * kABytes;
 
   if (warp == 4 && lane == 0) {
     // ------------------------------------------------ TMA producer
@@ -149,6 +161,10 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant_
     tc::prefetch_tmap(&tmAlo);
     tc::prefetch_tmap(&tmXhi);
     tc::prefetch_tmap(&tmXlo);
+    if (ex) {
+      tc::prefetch_tmap(&tmAlo2);
+      tc::prefetch_tmap(&tmXlo2);
+    }
     long long issued = 0;
     bool ok = true;
     for (long long u = u0; u < u1; ++u, ++issued) {
@@ -157,18 +173,24 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant_
       if (!tc::mbar_wait(&empty[stage], par ^ 1u, kWaitLimit)) { ok = false; break; }
       const int t = (int)(u / KB), kb = (int)(u % KB);
       unsigned char* base = smem + (size_t)stage * a.stage_bytes;
-      tc::mbar_expect_tx(&full[stage], 2 * kABytes + (products == 3 ? 2u : 1u) * xbytes);
+      tc::mbar_expect_tx(&full[stage], xoff + (uint32_t)nx * xbytes);
       if (MN_A) {
         tc::tma_load_2d(base, &tmAhi, &full[stage], t * BM, kb * BK);
         tc::tma_load_2d(base + kABytes / 2, &tmAhi, &full[stage], t * BM + 64, kb * BK);
         tc::tma_load_2d(base + kABytes, &tmAlo, &full[stage], t * BM, kb * BK);
         tc::tma_load_2d(base + kABytes + kABytes / 2, &tmAlo, &full[stage], t * BM + 64, kb * BK);
+        if (ex) {
+          tc::tma_load_2d(base + 2 * kABytes, &tmAlo2, &full[stage], t * BM, kb * BK);
+          tc::tma_load_2d(base + 2 * kABytes + kABytes / 2, &tmAlo2, &full[stage], t * BM + 64, kb * BK);
+        }
       } else {
         tc::tma_load_2d(base, &tmAhi, &full[stage], kb * BK, t * BM);
         tc::tma_load_2d(base + kABytes, &tmAlo, &full[stage], kb * BK, t * BM);
+        if (ex) tc::tma_load_2d(base + 2 * kABytes, &tmAlo2, &full[stage], kb * BK, t * BM);
       }
-      tc::tma_load_2d(base + 2 * kABytes, &tmXhi, &full[stage], kb * BK, 0);
-      if (products == 3) tc::tma_load_2d(base + 2 * kABytes + xbytes, &tmXlo, &full[stage], kb * BK, 0);
+      tc::tma_load_2d(base + xoff, &tmXhi, &full[stage], kb * BK, 0);
+      if (nx >= 2) tc::tma_load_2d(base + xoff + xbytes, &tmXlo, &full[stage], kb * BK, 0);
+      if (nx == 3) tc::tma_load_2d(base + xoff + 2 * xbytes, &tmXlo2, &full[stage], kb * BK, 0);
     }
     if (!ok) post_timeout(a.info);
     // Drain: every load this thread started has landed before the CTA exits.
@@ -191,23 +213,32 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant_
         if (!tc::mbar_wait(&full[stage], (uint32_t)((consumed / S) & 1), kWaitLimit)) { ok = false; break; }
         tc::tc_fence_after();
         const uint32_t base = tc::smem_u32(smem + (size_t)stage * a.stage_bytes);
-        const uint32_t ahi = base, alo = base + kABytes, xhi = base + 2 * kABytes, xlo = xhi + xbytes;
+        const uint32_t ahi = base, alo = base + kABytes, alo2 = base + 2 * kABytes, xhi = base + xoff,
+                       xlo = xhi + xbytes, xlo2 = xlo + xbytes;
 #pragma unroll
         for (int ks = 0; ks < BK / 16; ++ks) {
-          uint64_t dah, dal;
+          uint64_t dah, dal, dal2;
           if (MN_A) {   // MN-major, 128B swizzle: 16 k-rows = two 1024-byte atoms
             dah = tc::smem_desc(ahi + ks * 2048, kABytes / 2, 1024, tc::kSwizzle128);
             dal = tc::smem_desc(alo + ks * 2048, kABytes / 2, 1024, tc::kSwizzle128);
+            dal2 = tc::smem_desc(alo2 + ks * 2048, kABytes / 2, 1024, tc::kSwizzle128);
           } else {      // K-major, 64B swizzle: 16 k-columns = 32 bytes into the row
             dah = tc::smem_desc(ahi + ks * 32, 16, 512, tc::kSwizzle64);
             dal = tc::smem_desc(alo + ks * 32, 16, 512, tc::kSwizzle64);
+            dal2 = tc::smem_desc(alo2 + ks * 32, 16, 512, tc::kSwizzle64);
           }
           const uint64_t dxh = tc::smem_desc(xhi + ks * 32, 16, 512, tc::kSwizzle64);
           const uint64_t dxl = tc::smem_desc(xlo + ks * 32, 16, 512, tc::kSwizzle64);
+          const uint64_t dxl2 = tc::smem_desc(xlo2 + ks * 32, 16, 512, tc::kSwizzle64);
           const uint32_t acc = (u > seg_begin || ks > 0) ? 1u : 0u;
           tc::mma_bf16(d_tmem, dah, dxh, a.idesc, acc);
-          if (products == 3) tc::mma_bf16(d_tmem, dah, dxl, a.idesc, 1u);
+          if (nx >= 2) tc::mma_bf16(d_tmem, dah, dxl, a.idesc, 1u);
           tc::mma_bf16(d_tmem, dal, dxh, a.idesc, 1u);
+          if (ex) {
+            tc::mma_bf16(d_tmem, dal2, dxh, a.idesc, 1u);
+            tc::mma_bf16(d_tmem, dah, dxl2, a.idesc, 1u);
+            tc::mma_bf16(d_tmem, dal, dxl, a.idesc, 1u);
+          }
         }
         tc::mma_commit(&empty[stage]);
       }
@@ -494,8 +525,10 @@ __global__ void tc_gram_reduce_kernel(const float* __restrict__ part, int G, int
 }
 
 // A (m x n FP32) -> A_hi, A_lo (BF16, ld ldb, padding columns zero) and ||A||_F^2.
+// lo2 (optional) receives bf16(A - A_hi - A_lo); both differences are exact in FP32.
 __global__ void split_a_kernel(const float* __restrict__ A, long long m, long long n, long long lda, bool vec,
-                               bf16* __restrict__ hi, bf16* __restrict__ lo, long long ldb, double* sumsq) {
+                               bf16* __restrict__ hi, bf16* __restrict__ lo, bf16* __restrict__ lo2, long long ldb,
+                               double* sumsq) {
   const long long cpr = ldb / 8, total = m * cpr;
   float s = 0.f, comp = 0.f;
   for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
@@ -513,15 +546,19 @@ __global__ void split_a_kernel(const float* __restrict__ A, long long m, long lo
     }
     __align__(16) bf16 h[8];
     __align__(16) bf16 l[8];
+    __align__(16) bf16 l2[8];
     float ss = 0.f;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       h[i] = __float2bfloat16_rn(x[i]);
-      l[i] = __float2bfloat16_rn(x[i] - __bfloat162float(h[i]));
+      const float r1 = x[i] - __bfloat162float(h[i]);
+      l[i] = __float2bfloat16_rn(r1);
+      l2[i] = __float2bfloat16_rn(r1 - __bfloat162float(l[i]));
       ss = fmaf(x[i], x[i], ss);
     }
     *reinterpret_cast<uint4*>(hi + r * ldb + c0) = *reinterpret_cast<const uint4*>(h);
     *reinterpret_cast<uint4*>(lo + r * ldb + c0) = *reinterpret_cast<const uint4*>(l);
+    if (lo2 != nullptr) *reinterpret_cast<uint4*>(lo2 + r * ldb + c0) = *reinterpret_cast<const uint4*>(l2);
     const float y = ss - comp, tt = s + y;
     comp = (tt - s) - y;
     s = tt;
@@ -540,8 +577,10 @@ __global__ void split_a_kernel(const float* __restrict__ A, long long m, long lo
 }
 
 // X (rows x d FP32) -> X_hi^T, X_lo^T (d x ldk BF16, K-major); flags a nonzero low part.
+// tl2 (optional) receives bf16(X - X_hi - X_lo).
 __global__ void prep_x_kernel(const float* __restrict__ X, long long rows, int d, long long ldx,
-                              bf16* __restrict__ th, bf16* __restrict__ tl, long long ldk, int* nonzero_lo) {
+                              bf16* __restrict__ th, bf16* __restrict__ tl, bf16* __restrict__ tl2, long long ldk,
+                              int* nonzero_lo) {
   __shared__ float tile[32][33];
   const long long r0 = (long long)blockIdx.x * 32;
   const int c0 = blockIdx.y * 32;
@@ -558,9 +597,11 @@ __global__ void prep_x_kernel(const float* __restrict__ X, long long rows, int d
     if (c < d && r < ldk) {
       const float x = tile[threadIdx.x][i];
       const bf16 h = __float2bfloat16_rn(x);
-      const bf16 l = __float2bfloat16_rn(x - __bfloat162float(h));
+      const float r1 = x - __bfloat162float(h);
+      const bf16 l = __float2bfloat16_rn(r1);
       th[(long long)c * ldk + r] = h;
       tl[(long long)c * ldk + r] = l;
+      if (tl2 != nullptr) tl2[(long long)c * ldk + r] = __float2bfloat16_rn(r1 - __bfloat162float(l));
       any |= __bfloat162float(l) != 0.f;
     }
   }
@@ -608,7 +649,9 @@ uint32_t tmem_cols_of(int npad) {
   while (c < need) c <<= 1;
   return c;
 }
-uint32_t stage_bytes_of(int npad) { return 2 * kABytes + 2u * (uint32_t)npad * BK * 2; }
+uint32_t stage_bytes_of(int npad, bool exact = false) {
+  return (exact ? 3u : 2u) * kABytes + (exact ? 3u : 2u) * (uint32_t)npad * BK * 2;
+}
 
 size_t smem_optin_tc() {
   static size_t v = 0;
@@ -623,15 +666,16 @@ size_t smem_optin_tc() {
   return v;
 }
 
-int stages_of(int npad) {
+int stages_of(int npad, bool exact = false) {
   const size_t avail = smem_optin_tc() - 1024 - 512;
-  int s = (int)(avail / stage_bytes_of(npad));
+  int s = (int)(avail / stage_bytes_of(npad, exact));
   return std::max(2, std::min(kMaxStages, s));
 }
 
 template <bool MN_A>
 cudaError_t launch_pass(const CUtensorMap& ah, const CUtensorMap& al, const CUtensorMap& xh,
-                        const CUtensorMap& xl, const TcArgs& a, cudaStream_t st) {
+                        const CUtensorMap& xl, const CUtensorMap& al2, const CUtensorMap& xl2, const TcArgs& a,
+                        cudaStream_t st) {
   const size_t smem = (size_t)a.stages * a.stage_bytes + 1024 + 512;
   static bool configured = false;
   if (!configured) {
@@ -640,7 +684,7 @@ cudaError_t launch_pass(const CUtensorMap& ah, const CUtensorMap& al, const CUte
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  tc_pass_kernel<MN_A><<<a.G, kThreads, smem, st>>>(ah, al, xh, xl, a);
+  tc_pass_kernel<MN_A><<<a.G, kThreads, smem, st>>>(ah, al, xh, xl, al2, xl2, a);
   note_launch();
   return cudaGetLastError();
 }
@@ -659,7 +703,8 @@ bool tc_supported(const float* A, int64_t lda, const float* Omega, int64_t ldo) 
 
 constexpr int kGramMaxCtas = 64;
 
-void TcEngine::layout(Arena& ar, int64_t rows_cap, int64_t cols_cap, int d_cap, int64_t k_cap, bool gram) {
+void TcEngine::layout(Arena& ar, int64_t rows_cap, int64_t cols_cap, int d_cap, int64_t k_cap, bool gram,
+                      bool three_part) {
   rows_cap_ = rows_cap;
   cols_cap_ = cols_cap;
   d_cap_ = d_cap;
@@ -669,8 +714,10 @@ void TcEngine::layout(Arena& ar, int64_t rows_cap, int64_t cols_cap, int d_cap, 
   const int npad = npad_of(d_cap);
   Ahi_ = ar.take<uint16_t>((size_t)(rows_cap * ldb_));
   Alo_ = ar.take<uint16_t>((size_t)(rows_cap * ldb_));
+  Alo2_ = three_part ? ar.take<uint16_t>((size_t)(rows_cap * ldb_)) : nullptr;
   Xhi_ = ar.take<uint16_t>((size_t)d_cap * round_up(k_cap, 8));
   Xlo_ = ar.take<uint16_t>((size_t)d_cap * round_up(k_cap, 8));
+  Xlo2_ = three_part ? ar.take<uint16_t>((size_t)d_cap * round_up(k_cap, 8)) : nullptr;
   part_ = ar.take<float>((size_t)2 * G_ * BM * npad);
   flag_ = ar.take<int>(4);
   cnt_ = ar.take<int>((size_t)cdiv(std::max(rows_cap, cols_cap), BM));
@@ -687,7 +734,8 @@ cudaError_t TcEngine::split(const float* A, int64_t rows, int64_t cols, int64_t 
   const long long total = rows * (ldb_ / 8);
   const int blocks = (int)std::min<long long>(cdiv(total, 256), (long long)G_ * 8);
   split_a_kernel<<<blocks, 256, 0, st>>>(A, rows, cols, lda, vec, reinterpret_cast<bf16*>(Ahi_),
-                                         reinterpret_cast<bf16*>(Alo_), ldb_, sumsq);
+                                         reinterpret_cast<bf16*>(Alo_), reinterpret_cast<bf16*>(Alo2_), ldb_,
+                                         sumsq);
   note_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -700,8 +748,9 @@ cudaError_t TcEngine::split(const float* A, int64_t rows, int64_t cols, int64_t 
 
 cudaError_t TcEngine::pass(bool transA, const float* A, int64_t m, int64_t n, int64_t lda, const float* X,
                            int64_t ldx, int d, float* out, int64_t ldout, double* sumsq, int* info,
-                           cudaStream_t st) {
+                           cudaStream_t st, bool exact) {
   if (d > d_cap_) return cudaErrorInvalidValue;
+  if (exact && (Alo2_ == nullptr || Xlo2_ == nullptr)) return cudaErrorInvalidValue;
   cudaError_t e;
   if (split_of_ != A || m != m_ || n != n_) {
     if ((e = split(A, m, n, lda, sumsq, st)) != cudaSuccess) return e;
@@ -715,22 +764,31 @@ cudaError_t TcEngine::pass(bool transA, const float* A, int64_t m, int64_t n, in
   {
     dim3 grid((unsigned)cdiv(round_up(K, 8), 32), (unsigned)cdiv(d, 32));
     prep_x_kernel<<<grid, dim3(32, 8), 0, st>>>(X, K, d, ldx, reinterpret_cast<bf16*>(Xhi_),
-                                                 reinterpret_cast<bf16*>(Xlo_), round_up(K, 8), flag_);
+                                                 reinterpret_cast<bf16*>(Xlo_),
+                                                 exact ? reinterpret_cast<bf16*>(Xlo2_) : nullptr, round_up(K, 8),
+                                                 flag_);
     note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  CUtensorMap ah, al, xh, xl;
+  CUtensorMap ah, al, xh, xl, al2, xl2;
   const long long ldk = round_up(K, 8);
   bool ok;
+  // The third parts are read in exact mode only; otherwise their maps repeat
+  // the low parts'.
+  const uint16_t* A3 = exact ? Alo2_ : Alo_;
+  const uint16_t* X3 = exact ? Xlo2_ : Xlo_;
   if (transA) {   // op(A) = A^T: MN-major tiles, box 64 (j) x 32 (i), 128B swizzle
     ok = make_map(&ah, Ahi_, n, m, ldb_, 64, BK, CU_TENSOR_MAP_SWIZZLE_128B) &&
-         make_map(&al, Alo_, n, m, ldb_, 64, BK, CU_TENSOR_MAP_SWIZZLE_128B);
+         make_map(&al, Alo_, n, m, ldb_, 64, BK, CU_TENSOR_MAP_SWIZZLE_128B) &&
+         make_map(&al2, A3, n, m, ldb_, 64, BK, CU_TENSOR_MAP_SWIZZLE_128B);
   } else {        // op(A) = A: K-major tiles, box 32 (j) x 128 (i), 64B swizzle
     ok = make_map(&ah, Ahi_, n, m, ldb_, BK, BM, CU_TENSOR_MAP_SWIZZLE_64B) &&
-         make_map(&al, Alo_, n, m, ldb_, BK, BM, CU_TENSOR_MAP_SWIZZLE_64B);
+         make_map(&al, Alo_, n, m, ldb_, BK, BM, CU_TENSOR_MAP_SWIZZLE_64B) &&
+         make_map(&al2, A3, n, m, ldb_, BK, BM, CU_TENSOR_MAP_SWIZZLE_64B);
   }
   ok = ok && make_map(&xh, Xhi_, K, d, ldk, BK, npad_, CU_TENSOR_MAP_SWIZZLE_64B) &&
-       make_map(&xl, Xlo_, K, d, ldk, BK, npad_, CU_TENSOR_MAP_SWIZZLE_64B);
+       make_map(&xl, Xlo_, K, d, ldk, BK, npad_, CU_TENSOR_MAP_SWIZZLE_64B) &&
+       make_map(&xl2, X3, K, d, ldk, BK, npad_, CU_TENSOR_MAP_SWIZZLE_64B);
   if (!ok) return cudaErrorInvalidValue;
 
   TcArgs a;
@@ -750,7 +808,8 @@ cudaError_t TcEngine::pass(bool transA, const float* A, int64_t m, int64_t n, in
     a.G = (int)cdiv(a.tiles, a.tpc);
   }
   a.vec_out = ((reinterpret_cast<uintptr_t>(out) % 16) == 0 && ldout % 4 == 0) ? 1 : 0;
-  a.stages = stages_of(npad_);
+  a.exact = exact ? 1 : 0;
+  a.stages = stages_of(npad_, exact);
   a.out = out;
   a.ldo = ldout;
   a.part = part_;
@@ -758,11 +817,12 @@ cudaError_t TcEngine::pass(bool transA, const float* A, int64_t m, int64_t n, in
   a.xlo_nonzero = flag_;
   a.info = info;
   a.idesc = tc::idesc_bf16(BM, npad_, transA, false);
-  a.stage_bytes = stage_bytes_of(npad_);
+  a.stage_bytes = stage_bytes_of(npad_, exact);
   a.tmem_cols = tmem_cols_of(npad_);
   const bool prof = profiled_ && profiling_on();
   if (prof) profile_mark_begin(st);
-  e = transA ? launch_pass<true>(ah, al, xh, xl, a, st) : launch_pass<false>(ah, al, xh, xl, a, st);
+  e = transA ? launch_pass<true>(ah, al, xh, xl, al2, xl2, a, st)
+             : launch_pass<false>(ah, al, xh, xl, al2, xl2, a, st);
   if (prof) profile_mark_end(st, transA ? 1 : 0);
   return e;
 }
