@@ -11,9 +11,9 @@
 //       W_J,: = D X_J,: (X = the eliminated identity, W_JJ = D);
 //   (3) trailing updates G_II -= L_IJ L_IJ^T (lower part) and
 //       X_I,: -= L_IJ W_J,: for the rows below.
-// Step (3) runs as warp tasks of 16 x 64 outputs with the panel operands in
-// transposed shared-memory buffers (row values broadcast, two column values
-// per lane). L lives in the lower triangle of one square buffer and
+// Step (3) gives each thread 4 x 4 blocks of outputs, with the panel operands
+// in transposed shared-memory buffers (one 128-bit load of row values and one
+// of column values per 16 FMAs). L lives in the lower triangle of one square buffer and
 // W^T in its strict upper triangle (W's diagonal in a side array).
 //
 // A pivot that is not clearly positive restarts the elimination on G + s I
@@ -235,42 +235,59 @@ __device__ __forceinline__ void chol_body(int d, const float* __restrict__ G, in
         }
       }
       __syncthreads();
-      // (3) trailing updates as 16 x 64 warp tasks: each lane owns two columns
-      // (one PT value each), 16 row values are broadcast from PT / WT.
+      // (3) trailing updates G_II -= L_IJ L_IJ^T (lower part) and X -= L_IJ W_J,:
+      // (rows above), each thread taking 4 x 4 blocks: two 128-bit loads of
+      // panel values per 16 FMAs, then a vectorised read-modify-write of S.
       if (Nt > 0) {
-        const int ra = (Nt + 15) / 16, rb = (jn + 15) / 16, nc = (Nt + 63) / 64;
-        const int tasks = (ra + rb) * nc;
-        for (int task = warp; task < tasks; task += nwarps) {
-          const int strip = task / nc, cs = task % nc;
-          const bool lower = strip < ra;
-          const int r0 = lower ? jn + strip * 16 : (strip - ra) * 16;
-          const int rlim = lower ? d : jn;
-          const int cbase = jn + cs * 64;
-          if (lower && cbase > r0 + 15) continue;   // tile above the diagonal
-          const int col0 = cbase + lane, col1 = col0 + 32;
+        const int nbc = (Nt + 3) / 4;              // 4-column blocks over [jn, d)
+        const int nbl = nbc * (nbc + 1) / 2;       // lower blocks: block row >= block column
+        const int nbw = ((jn + 3) / 4) * nbc;      // W blocks: rows [0, jn) x columns [jn, d)
+        for (int b = tid; b < nbl + nbw; b += blockDim.x) {
+          int r0, c0, rlim;
+          bool lower;
+          if (b < nbl) {
+            int br = (int)((sqrtf(8.f * (float)b + 1.f) - 1.f) * 0.5f);
+            while ((br + 1) * (br + 2) / 2 <= b) ++br;
+            while (br * (br + 1) / 2 > b) --br;
+            r0 = jn + 4 * br;
+            c0 = jn + 4 * (b - br * (br + 1) / 2);
+            rlim = d;
+            lower = true;
+          } else {
+            const int w = b - nbl;
+            r0 = 4 * (w / nbc);
+            c0 = jn + 4 * (w % nbc);
+            rlim = jn;
+            lower = false;
+          }
           const T* Ar = lower ? PT : WT;
-          T acc0[16], acc1[16];
+          T acc[4][4];
 #pragma unroll
-          for (int rr = 0; rr < 16; ++rr) acc0[rr] = acc1[rr] = 0;
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = 0;
 #pragma unroll
           for (int k = 0; k < NB; ++k) {
-            T av[16];
+            T av[4], bv[4];
+            ld4(&Ar[k * PTLD + r0], av);
+            ld4(&PT[k * PTLD + c0], bv);
 #pragma unroll
-            for (int q = 0; q < 16; q += 4) ld4(&Ar[k * PTLD + r0 + q], &av[q]);
-            const T b0 = col0 < d ? PT[k * PTLD + col0] : (T)0;
-            const T b1 = col1 < d ? PT[k * PTLD + col1] : (T)0;
+            for (int i = 0; i < 4; ++i)
 #pragma unroll
-            for (int rr = 0; rr < 16; ++rr) {
-              acc0[rr] += av[rr] * b0;
-              acc1[rr] += av[rr] * b1;
-            }
+              for (int j = 0; j < 4; ++j) acc[i][j] += av[i] * bv[j];
           }
 #pragma unroll
-          for (int rr = 0; rr < 16; ++rr) {
-            const int r = r0 + rr;
+          for (int i = 0; i < 4; ++i) {
+            const int r = r0 + i;
             if (r >= rlim) continue;
-            if (col0 < d && (!lower || col0 <= r)) S[(size_t)r * LDS + col0] -= acc0[rr];
-            if (col1 < d && (!lower || col1 <= r)) S[(size_t)r * LDS + col1] -= acc1[rr];
+            T sv[4];
+            ld4(&S[(size_t)r * LDS + c0], sv);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              const int c = c0 + j;
+              if (c < d && (!lower || c <= r)) sv[j] -= acc[i][j];
+            }
+            st4(&S[(size_t)r * LDS + c0], sv);
           }
         }
       }
