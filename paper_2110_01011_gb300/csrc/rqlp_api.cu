@@ -289,7 +289,8 @@ class Plan {
     CK(transpose_small(d, Rb_, ld, Ts_, ld, st));
     CK(ops_.orth_final(Ts_, ld, d, Ph_, ld, Ts2_, Rh_, 2));
     CK(write_L(d, Rh_, ld, out.L, out.ldl, &ops_.scal[1], st));
-    // P = P~ P^
+    // P = P~ P^ (FP32: P's entries are ~sqrt(d) times smaller than |P~| |P^|,
+    // more than the tensor cores' accumulation leaves room for)
     CK(gemm_f32_ex(false, n, d, d, Pt_, ld, Ph_, ld, out.P, out.ldp, 1, nullptr, nullptr, nullptr, kGateNone,
                    false, st));
     return finish_diag(ops_.scal, diag, info, st);
