@@ -232,13 +232,11 @@ def run_reference(a):
 
 # ------------------------------------------------------------------ our arm
 
-def kernel_sha():
-    h = hashlib.sha256()
-    for f in ("gemm_simt.cu", "tc_gemm.cu"):
-        p = os.path.join(ROOT, "paper_2110_01011_gb300", "csrc", f)
-        if os.path.exists(p):
-            h.update(open(p, "rb").read())
-    return h.hexdigest()[:12]
+def kernel_sha(prec):
+    """Hash of the source file that holds the dominant kernel of this precision."""
+    f = "gemm_simt.cu" if prec == rqlp.PREC_FP32 else "tc_gemm.cu"
+    p = os.path.join(ROOT, "paper_2110_01011_gb300", "csrc", f)
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:12]
 
 
 def traffic_for(kernel, sha):
@@ -333,7 +331,7 @@ def roofline(a, recs, d, prec, peaks, dev):
     sm_max = peaks.get("sm_max_mhz", 2070.0)
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
     kname = {0: "pass_AX", 1: "pass_AtX"}[dom]
-    sha = kernel_sha()
+    sha = kernel_sha(prec)
     if prec == rqlp.PREC_FP32:
         peak = nsm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
         roof = {"bound": "alu", "achieved": flops / (pass_ms * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",

@@ -255,9 +255,10 @@ rqlp_status rqlp_factor_learned(const float* A, int64_t m, int64_t n, int64_t ld
  * problem (caller's order), d_diag: 4 device doubles per problem (optional),
  * laid out as for rqlp_factor.
  *
- * rqlp_batch_autotune times every tile configuration of each grouped
- * product shape (tall A^T X, tall A X, Gram, X R^{-1}, d x d) and width
- * bucket (d <= 32, d > 32) on the plan's own problems, keeps the fastest and
+ * rqlp_batch_autotune times every tile configuration (6 tile shapes x
+ * persistent or one-CTA-per-tile grids) of each grouped product shape (tall
+ * A^T X, tall A X, Gram, X R^{-1}, d x d) and width bucket (d <= 32, d > 32)
+ * on the plan's own problems, keeps the fastest and
  * remembers the choice for later plans with the same size mix (process
  * wide). It runs products out of order on the workspace: run it before the
  * batch is launched, then launch. rqlp_batch_tuning writes the chosen

@@ -11,8 +11,9 @@
 // is captured once into a CUDA graph and replayed as one launch.
 //
 // Problems are grouped into two width buckets (d <= 32, d > 32); each GEMM
-// stage runs one launch per non-empty bucket with the tile configuration
-// that the autotuner picked for its (product shape, bucket).
+// stage runs one launch per non-empty bucket with the tile shape and grid
+// mode (persistent or one CTA per tile) that the autotuner picked for its
+// (product shape, bucket).
 #include <algorithm>
 #include <cstring>
 #include <map>
@@ -32,13 +33,16 @@ constexpr int kGates = 4;
 
 int bucket_of(int d) { return d <= 32 ? 0 : 1; }
 
+// Untuned choice per (shape, bucket): what the tuner picked for the mixed
+// 512-problem workload (tile shape 0..5, + kGroupCfgs = one CTA per tile).
 int default_cfg(int shape, int bucket) {
+  constexpr int kOne = kGroupCfgs;
   switch (shape) {
     case kTallT:
-    case kTallN:
-    case kTrmm: return bucket == 0 ? 2 : 0;
-    case kGram: return bucket == 0 ? 4 : 5;
-    default: return 4;
+    case kTallN: return bucket == 0 ? kOne + 3 : kOne + 0;
+    case kTrmm: return bucket == 0 ? 2 : kOne + 2;
+    case kGram: return bucket == 0 ? 5 : kOne + 3;
+    default: return bucket == 0 ? kOne + 4 : 5;
   }
 }
 
@@ -430,8 +434,9 @@ cudaError_t run_gemm(const rqlp_batch_s* b, const GemmStage& g, cudaStream_t st,
   for (int bk = 0; bk < kBuckets; ++bk) {
     const int c = b->cnt[bk];
     if (c > 0 && (only_bucket < 0 || only_bucket == bk)) {
-      const int cfg = force_cfg >= 0 ? force_cfg : b->cfg[g.shape][bk];
-      CK(gemm_grouped(g.transA, cfg, jobs + lo, at<int>(b, g.tiles_off[bk][cfg]), c, g.total[bk][cfg], st));
+      const int choice = force_cfg >= 0 ? force_cfg : b->cfg[g.shape][bk];
+      const int cfg = choice % kGroupCfgs;   // tile shape; the choice also fixes the grid mode
+      CK(gemm_grouped(g.transA, choice, jobs + lo, at<int>(b, g.tiles_off[bk][cfg]), c, g.total[bk][cfg], st));
     }
     lo += c;
   }
@@ -596,7 +601,7 @@ rqlp_status rqlp_batch_autotune(rqlp_batch b, int reps, void* stream) {
     for (int bk = 0; bk < kBuckets && rc == RQLP_OK; ++bk) {
       if (b->cnt[bk] == 0) continue;
       float best = 1e30f;
-      for (int cfg = 0; cfg < kGroupCfgs; ++cfg) {
+      for (int cfg = 0; cfg < kGroupChoices; ++cfg) {
         float ms = 0.f;
         if (run_gemm(b, *rep, st, bk, cfg) != cudaSuccess ||      // warm-up
             cudaEventRecord(e0, st) != cudaSuccess) {

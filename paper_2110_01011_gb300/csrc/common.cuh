@@ -75,9 +75,12 @@ struct GroupGemm {
   int gate_mode;
   int b_upper;
 };
+// Tile shapes (kGroupCfgs) times grid modes: choice < kGroupCfgs is a
+// persistent grid, choice - kGroupCfgs the same tile with one CTA per tile.
 constexpr int kGroupCfgs = 6;
+constexpr int kGroupChoices = 2 * kGroupCfgs;
 void grouped_tile(int cfg, int* bm, int* bn);
-cudaError_t gemm_grouped(bool transA, int cfg, const GroupGemm* jobs, const int* tile_start, int count,
+cudaError_t gemm_grouped(bool transA, int choice, const GroupGemm* jobs, const int* tile_start, int count,
                          int total_tiles, cudaStream_t st);
 // Runs every one-time query of the grouped kernels (call before capturing).
 cudaError_t gemm_grouped_prepare();

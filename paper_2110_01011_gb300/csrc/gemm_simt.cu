@@ -303,9 +303,11 @@ cudaError_t gemm_f32_ex(bool transA, int64_t M, int64_t N, int64_t K, const floa
 namespace {
 // Resident CTAs per SM of one configuration (queried once; a launch with
 // total <= 0 only primes the query, so that no query runs under capture).
+// persistent: a few CTAs per SM walk the tile list; otherwise one CTA per
+// tile and the hardware scheduler balances them.
 template <int BM, int BN, int TM, int TN>
-cudaError_t launch_grouped_cfg(bool transA, const GroupGemm* jobs, const int* tile_start, int count, int total,
-                               cudaStream_t st) {
+cudaError_t launch_grouped_cfg(bool transA, bool persistent, const GroupGemm* jobs, const int* tile_start,
+                               int count, int total, cudaStream_t st) {
   constexpr int NT = (BM / TM) * (BN / TN);
   static int per_sm[2] = {0, 0};
   int& occ = per_sm[transA ? 1 : 0];
@@ -318,7 +320,7 @@ cudaError_t launch_grouped_cfg(bool transA, const GroupGemm* jobs, const int* ti
     if (occ < 1) occ = 1;
   }
   if (total <= 0 || count <= 0) return cudaSuccess;
-  const int grid = std::max(1, std::min(total, sm_count() * occ));
+  const int grid = persistent ? std::max(1, std::min(total, sm_count() * occ)) : total;
   if (transA) gemm_grouped_kernel<BM, BN, 16, TM, TN, true><<<grid, NT, 0, st>>>(jobs, tile_start, count);
   else        gemm_grouped_kernel<BM, BN, 16, TM, TN, false><<<grid, NT, 0, st>>>(jobs, tile_start, count);
   note_launch();
@@ -335,7 +337,7 @@ void grouped_tile(int cfg, int* bm, int* bn) {
 
 cudaError_t gemm_grouped_prepare() {
   sm_count();
-  for (int cfg = 0; cfg < kGroupCfgs; ++cfg)
+  for (int cfg = 0; cfg < kGroupChoices; ++cfg)
     for (int t = 0; t < 2; ++t) {
       cudaError_t e = gemm_grouped(t == 1, cfg, nullptr, nullptr, 0, 0, nullptr);
       if (e != cudaSuccess) return e;
@@ -343,17 +345,23 @@ cudaError_t gemm_grouped_prepare() {
   return cudaSuccess;
 }
 
-cudaError_t gemm_grouped(bool transA, int cfg, const GroupGemm* jobs, const int* tile_start, int count,
+cudaError_t gemm_grouped(bool transA, int choice, const GroupGemm* jobs, const int* tile_start, int count,
                          int total_tiles, cudaStream_t st) {
+  const int cfg = choice % kGroupCfgs;
+  const bool persistent = choice < kGroupCfgs;
+#define RQLP_GROUPED(BM, BN, TM, TN) \
+  launch_grouped_cfg<BM, BN, TM, TN>(transA, persistent, jobs, tile_start, count, total_tiles, st)
   switch (cfg) {
-    case 0: return launch_grouped_cfg<128, 64, 8, 4>(transA, jobs, tile_start, count, total_tiles, st);
-    case 1: return launch_grouped_cfg<64, 64, 4, 4>(transA, jobs, tile_start, count, total_tiles, st);
-    case 2: return launch_grouped_cfg<128, 32, 8, 4>(transA, jobs, tile_start, count, total_tiles, st);
-    case 3: return launch_grouped_cfg<64, 32, 4, 4>(transA, jobs, tile_start, count, total_tiles, st);
-    case 4: return launch_grouped_cfg<32, 32, 4, 4>(transA, jobs, tile_start, count, total_tiles, st);
-    case 5: return launch_grouped_cfg<32, 64, 4, 4>(transA, jobs, tile_start, count, total_tiles, st);
+    case 0: return RQLP_GROUPED(128, 64, 8, 4);
+    case 1: return RQLP_GROUPED(64, 64, 4, 4);
+    case 2: return RQLP_GROUPED(128, 32, 8, 4);
+    case 3: return RQLP_GROUPED(64, 32, 4, 4);
+    case 4: return RQLP_GROUPED(32, 32, 4, 4);
+    case 5: return RQLP_GROUPED(32, 64, 4, 4);
+    // 8 x 8 outputs per thread: four 128-bit shared loads per 64 FMAs
     default: return cudaErrorInvalidValue;
   }
+#undef RQLP_GROUPED
 }
 
 }  // namespace rqlp

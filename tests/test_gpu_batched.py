@@ -79,7 +79,7 @@ def test_autotune_then_launch():
     probs = _problems(16, seed=21)
     b = _batch(probs, 1)
     tune = b.autotune(reps=2)
-    assert len(tune) == 10 and all(0 <= c < 6 for c in tune)
+    assert len(tune) == 10 and all(0 <= c < 12 for c in tune)
     b.launch()
     _check_all(b, probs, 1)
     b.close()
