@@ -234,7 +234,7 @@ def run_reference(a):
 
 def kernel_sha(prec):
     """Hash of the source file that holds the dominant kernel of this precision."""
-    f = "gemm_simt.cu" if prec == rqlp.PREC_FP32 else "tc_gemm.cu"
+    f = "gemm_simt.cu" if prec == 0 else "tc_gemm.cu"   # 0: FP32 form
     p = os.path.join(ROOT, "paper_2110_01011_gb300", "csrc", f)
     return hashlib.sha256(open(p, "rb").read()).hexdigest()[:12]
 

@@ -62,12 +62,12 @@ __device__ void post_error(int* info, int code, int detail) {
 }
 
 __device__ void write_identity(int d, float* R, float* Rinv, int64_t ldr) {
-  for (int e = threadIdx.x; e < d * d; e += blockDim.x) {
-    const int i = e / d, l = e % d;
-    const float v = i == l ? 1.f : 0.f;
-    R[i * ldr + l] = v;
-    Rinv[i * ldr + l] = v;
-  }
+  for (int i = threadIdx.x >> 5; i < d; i += blockDim.x >> 5)
+    for (int l = threadIdx.x & 31; l < d; l += 32) {
+      const float v = i == l ? 1.f : 0.f;
+      R[i * ldr + l] = v;
+      Rinv[i * ldr + l] = v;
+    }
 }
 
 // The factorisation of one problem by the whole CTA (any multiple of 32
@@ -84,7 +84,8 @@ __device__ __forceinline__ void chol_body(int d, const float* __restrict__ G, in
   T* PT = gS != nullptr ? dyn : dyn + (size_t)d * LDS;
   T* WT = PT + NB * PTLD;
   __shared__ T gdiag[kMaxD], wdiag[kMaxD];
-  __shared__ T Dinv[NB][NB + 1], rdiag[NB];
+  __shared__ __align__(32) T Dinv[NB][NB];   // D = L_JJ^{-1}, zero above the diagonal and beyond jb
+  __shared__ T rdiag[NB];
   __shared__ T s_red[32];
   __shared__ int s_fail;
 
@@ -113,13 +114,29 @@ __device__ __forceinline__ void chol_body(int d, const float* __restrict__ G, in
   int fail = -1;
   for (int attempt = 0; attempt < 2; ++attempt) {
     const T sh = attempt == 0 ? (T)0 : shift;
-    for (int e = tid; e < d * d; e += blockDim.x) {
-      const int i = e / d, j = e % d;
-      T v = 0;
-      if (j <= i) v = (T)G[(int64_t)i * ldg + j] + (i == j ? sh : (T)0);
-      S[(size_t)i * LDS + j] = v;
+    // Lower triangle of G (+ sh I) into S, zeros above: a warp per pair of
+    // rows, lanes over columns, all of a pair's loads issued before its stores.
+    for (int i0 = 2 * warp; i0 < d; i0 += 2 * nwarps) {
+      T v[2][kMaxD / 32];
+#pragma unroll
+      for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int t = 0; t < kMaxD / 32; ++t) {
+          const int i = i0 + r, j = lane + 32 * t;
+          v[r][t] = (i < d && j <= i) ? (T)G[(int64_t)i * ldg + j] : (T)0;
+        }
+#pragma unroll
+      for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int t = 0; t < kMaxD / 32; ++t) {
+          const int i = i0 + r, j = lane + 32 * t;
+          if (i < d && j < d) {
+            const T x = v[r][t] + (j == i ? sh : (T)0);
+            S[(size_t)i * LDS + j] = x;
+            if (j == i) gdiag[i] = x;
+          }
+        }
     }
-    for (int i = tid; i < d; i += blockDim.x) gdiag[i] = (T)G[(int64_t)i * ldg + i] + sh;
     __syncthreads();
     fail = -1;
     for (int j0 = 0; j0 < d; j0 += NB) {
@@ -131,7 +148,13 @@ __device__ __forceinline__ void chol_body(int d, const float* __restrict__ G, in
       if (warp == 0) {
         T l[NB];
 #pragma unroll
-        for (int k = 0; k < NB; ++k) l[k] = (lane < jb && k <= lane) ? S[(size_t)(j0 + lane) * LDS + j0 + k] : (T)0;
+        for (int k = 0; k < NB; k += 4) {
+          if (lane < jb) ld4(&S[(size_t)(j0 + lane) * LDS + j0 + k], &l[k]);
+          else l[k] = l[k + 1] = l[k + 2] = l[k + 3] = (T)0;
+        }
+#pragma unroll
+        for (int k = 0; k < NB; ++k)
+          if (k > lane) l[k] = (T)0;
         int f = -1;
 #pragma unroll
         for (int j = 0; j < NB; ++j) {
@@ -164,9 +187,10 @@ __device__ __forceinline__ void chol_body(int d, const float* __restrict__ G, in
             const T ri = rdiag[i];
             x[i] = (i < c || i >= jb) ? (T)0 : (i == c ? ri : -s * ri);
           }
+          if (c < NB) {
 #pragma unroll
-          for (int i = 0; i < NB; ++i)
-            if (c < jb && i < jb) Dinv[i][c] = x[i];
+            for (int i = 0; i < NB; ++i) Dinv[i][c] = (c < jb && i < jb) ? x[i] : (T)0;
+          }
         }
         if (lane == 0) s_fail = f;
       }
@@ -177,54 +201,75 @@ __device__ __forceinline__ void chol_body(int d, const float* __restrict__ G, in
       }
       const int jn = j0 + jb, Nt = d - jn;
       // (2) panel rows below the block, block row of W, and W's diagonal
-      // block. Results are computed in registers and stored afterwards.
-      for (int idx = tid; idx < Nt + jn; idx += blockDim.x) {
+      // block. Two threads per row, one for the even and one for the odd
+      // outputs, each reading rows of D as 128-bit broadcasts; results are
+      // computed in registers and stored afterwards.
+      for (int task = tid; task < 2 * (Nt + jn); task += blockDim.x) {
+        const int idx = task >> 1, h = task & 1;
         if (idx < Nt) {
           const int i = jn + idx;
-          T v[NB], o[NB];
+          T v[NB], o[NB / 2];
 #pragma unroll
           for (int k = 0; k < NB; k += 4) ld4(&S[(size_t)i * LDS + j0 + k], &v[k]);
 #pragma unroll
-          for (int c = 0; c < NB; ++c) {
+          for (int q = 0; q < NB / 2; ++q) {
+            const int c = 2 * q + h;
             T s2 = 0;
 #pragma unroll
-            for (int k = 0; k <= c; ++k) s2 += v[k] * Dinv[c][k];
-            o[c] = s2;
+            for (int k = 0; k < NB; k += 4) {
+              if (k <= 2 * q + 1) {   // D is zero beyond the diagonal
+                T dv[4];
+                ld4(&Dinv[c][k], dv);
+                s2 += v[k] * dv[0] + v[k + 1] * dv[1] + v[k + 2] * dv[2] + v[k + 3] * dv[3];
+              }
+            }
+            o[q] = s2;
           }
 #pragma unroll
-          for (int c = 0; c < NB; ++c) PT[c * PTLD + i] = o[c];
-#pragma unroll
-          for (int k = 0; k < NB; k += 4) st4(&S[(size_t)i * LDS + j0 + k], &o[k]);
+          for (int q = 0; q < NB / 2; ++q) {
+            const int c = 2 * q + h;
+            PT[c * PTLD + i] = o[q];
+            S[(size_t)i * LDS + j0 + c] = o[q];
+          }
         } else {
           const int c = idx - Nt;
           if (c < j0) {
-            T w[NB], o[NB];
-            if (jb == NB) {
+            T w[NB], o[NB / 2];
 #pragma unroll
-              for (int k = 0; k < NB; k += 4) ld4(&S[(size_t)c * LDS + j0 + k], &w[k]);
-            } else {
+            for (int k = 0; k < NB; k += 4) ld4(&S[(size_t)c * LDS + j0 + k], &w[k]);
+            if (jb < NB) {
 #pragma unroll
-              for (int k = 0; k < NB; ++k) w[k] = k < jb ? S[(size_t)c * LDS + j0 + k] : (T)0;
+              for (int k = 0; k < NB; ++k)
+                if (k >= jb) w[k] = (T)0;
             }
 #pragma unroll
-            for (int rr = 0; rr < NB; ++rr) {
+            for (int q = 0; q < NB / 2; ++q) {
+              const int rr = 2 * q + h;
               T s2 = 0;
 #pragma unroll
-              for (int k = 0; k <= rr; ++k) s2 += Dinv[rr][k] * w[k];
-              o[rr] = s2;
+              for (int k = 0; k < NB; k += 4) {
+                if (k <= 2 * q + 1) {
+                  T dv[4];
+                  ld4(&Dinv[rr][k], dv);
+                  s2 += dv[0] * w[k] + dv[1] * w[k + 1] + dv[2] * w[k + 2] + dv[3] * w[k + 3];
+                }
+              }
+              o[q] = s2;
             }
 #pragma unroll
-            for (int rr = 0; rr < NB; ++rr) {
+            for (int q = 0; q < NB / 2; ++q) {
+              const int rr = 2 * q + h;
               if (rr < jb) {
-                S[(size_t)c * LDS + j0 + rr] = o[rr];
-                WT[rr * PTLD + c] = o[rr];
+                S[(size_t)c * LDS + j0 + rr] = o[q];
+                WT[rr * PTLD + c] = o[q];
               }
             }
           } else {
             const int cc = c - j0;
-            wdiag[c] = Dinv[cc][cc];
+            if (h == 0) wdiag[c] = Dinv[cc][cc];
 #pragma unroll
-            for (int rr = 0; rr < NB; ++rr) {
+            for (int q = 0; q < NB / 2; ++q) {
+              const int rr = 2 * q + h;
               if (rr < jb) {
                 const T wv = rr >= cc ? Dinv[rr][cc] : (T)0;
                 if (rr > cc) S[(size_t)c * LDS + j0 + rr] = wv;
@@ -307,10 +352,13 @@ __device__ __forceinline__ void chol_body(int d, const float* __restrict__ G, in
     return;
   }
   // R = L^T (upper); R^{-1} = W^T: strict upper part from S, diagonal from wdiag.
-  for (int e = tid; e < d * d; e += blockDim.x) {
-    const int i = e / d, l = e % d;
-    R[i * ldr + l] = l >= i ? (float)S[(size_t)l * LDS + i] : 0.f;
-    Rinv[i * ldr + l] = l > i ? (float)S[(size_t)i * LDS + l] : (l == i ? (float)wdiag[i] : 0.f);
+  for (int i = warp; i < d; i += nwarps) {   // a warp per row, lanes over columns
+    float* r = R + (int64_t)i * ldr;
+    float* ri = Rinv + (int64_t)i * ldr;
+    for (int l = lane; l < d; l += 32) {
+      r[l] = l >= i ? (float)S[(size_t)l * LDS + i] : 0.f;
+      ri[l] = l > i ? (float)S[(size_t)i * LDS + l] : (l == i ? (float)wdiag[i] : 0.f);
+    }
   }
 }
 
@@ -349,7 +397,7 @@ size_t square_bytes(int d) { return (size_t)d * lds_of(d) * sizeof(T); }
 template <typename T>
 size_t panel_bytes(int d) { return (size_t)2 * NB * ptld_of(d) * sizeof(T); }
 template <typename T>
-size_t static_bytes() { return (2 * kMaxD + NB * (NB + 1) + NB + 32) * sizeof(T) + 64; }
+size_t static_bytes() { return (2 * kMaxD + NB * NB + NB + 32) * sizeof(T) + 96; }
 template <typename T>
 bool square_in_smem(int d) {
   return square_bytes<T>(d) + panel_bytes<T>(d) + static_bytes<T>() <= smem_optin_chol();
