@@ -65,28 +65,96 @@ __device__ void write_identity(int d, float* R, float* Rinv, int64_t ldr) {
   for (int i = threadIdx.x >> 5; i < d; i += blockDim.x >> 5)
     for (int l = threadIdx.x & 31; l < d; l += 32) {
       const float v = i == l ? 1.f : 0.f;
-      R[i * ldr + l] = v;
+      if (R != nullptr) R[i * ldr + l] = v;
       Rinv[i * ldr + l] = v;
     }
 }
 
-// The factorisation of one problem by the whole CTA (any multiple of 32
-// threads up to kThreads). gS: the square buffer in global memory, or nullptr
-// for shared memory.
+// Trailing update tiles of the panel that ends at column jn: lower: G_II -= L_IJ L_IJ^T over
+// rows and columns [jn, d), c <= r (Ar = PT); else X -= L_IJ W_J,: over rows
+// [0, jn), columns [jn, d) (Ar = WT). A warp takes a 32 x 16 tile (tiles w0,
+// w0 + ws, ...), each lane a 4 x 4 block (lanes 8 x 4 over the tile): one k
+// step reads 128 contiguous bytes of Ar and 64 of PT for the warp's 512
+// FMAs, then a vectorised read-modify-write of S. Lower tiles: row strip q of
+// 32 rows needs the column strips of 16 up to its diagonal (2 q + 2 of them).
 template <typename T>
+__device__ __forceinline__ void trailing_tiles(T* S, int LDS, const T* Ar, const T* PT, int d, int jn, bool lower,
+                                               int w0, int ws, int lane) {
+  const int PTLD = ptld_of(d), Nt = d - jn;
+  if (Nt <= 0 || w0 < 0) return;
+  const int nct = (Nt + 15) / 16;             // column strips over [jn, d)
+  int ntiles = 0;
+  if (lower) {
+    const int nrs = (Nt + 31) / 32;           // row strips over [jn, d)
+    for (int q = 0; q < nrs; ++q) ntiles += min(2 * q + 2, nct);
+  } else {
+    ntiles = ((jn + 31) / 32) * nct;
+  }
+  for (int t = w0; t < ntiles; t += ws) {
+    int tr, tc, rlim;
+    if (lower) {
+      int q = 0, acc0 = 0;
+      while (acc0 + min(2 * q + 2, nct) <= t) acc0 += min(2 * q++ + 2, nct);
+      tr = jn + 32 * q;
+      tc = jn + 16 * (t - acc0);
+      rlim = d;
+    } else {
+      tr = 32 * (t / nct);
+      tc = jn + 16 * (t % nct);
+      rlim = jn;
+    }
+    const int r0 = tr + 4 * (lane >> 2), c0 = tc + 4 * (lane & 3);
+    if (r0 < rlim && c0 < d && (!lower || c0 <= r0 + 3)) {
+      T acc[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0;
+#pragma unroll
+      for (int k = 0; k < NB; ++k) {
+        T av[4], bv[4];
+        ld4(&Ar[k * PTLD + r0], av);
+        ld4(&PT[k * PTLD + c0], bv);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] += av[i] * bv[j];
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int r = r0 + i;
+        if (r >= rlim) continue;
+        T sv[4];
+        ld4(&S[(size_t)r * LDS + c0], sv);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int c = c0 + j;
+          if (c < d && (!lower || c <= r)) sv[j] -= acc[i][j];
+        }
+        st4(&S[(size_t)r * LDS + c0], sv);
+      }
+    }
+  }
+}
+
+// The factorisation of one problem by the whole CTA (any multiple of 32
+// threads up to kThreads). gS: the square buffer in global memory (used
+// when !kShared).
+template <typename T, bool kShared>
 __device__ __forceinline__ void chol_body(int d, const float* __restrict__ G, int64_t ldg, float* __restrict__ R,
                                           float* __restrict__ Rinv, int64_t ldr, int* info, double* shift_count,
                                           int* gate_out, const int* gate_in, T* gS) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int LDS = lds_of(d), PTLD = ptld_of(d);
   T* dyn = reinterpret_cast<T*>(smem_raw);
-  T* S = gS != nullptr ? gS : dyn;
-  T* PT = gS != nullptr ? dyn : dyn + (size_t)d * LDS;
+  // kShared: S at the start of shared memory, so every access to it is a
+  // shared-memory access; otherwise S = gS in global memory.
+  T* S = kShared ? dyn : gS;
+  T* PT = kShared ? dyn + (size_t)d * LDS : dyn;
   T* WT = PT + NB * PTLD;
-  __shared__ T gdiag[kMaxD], wdiag[kMaxD];
-  __shared__ __align__(32) T Dinv[NB][NB];   // D = L_JJ^{-1}, zero above the diagonal and beyond jb
-  __shared__ T rdiag[NB];
-  __shared__ T s_red[32];
+  __shared__ __align__(32) T gdiag[kMaxD];
+  __shared__ T wdiag[kMaxD];
+  __shared__ T rdiag[NB];   // 1 / L_jj of the current diagonal block
   __shared__ int s_fail;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
@@ -96,37 +164,25 @@ __device__ __forceinline__ void chol_body(int d, const float* __restrict__ G, in
     return;
   }
 
-  T tr = 0;
-  for (int i = tid; i < d; i += blockDim.x) tr += (T)G[(int64_t)i * ldg + i];
-  for (int o = 16; o > 0; o >>= 1) tr += __shfl_down_sync(0xffffffffu, tr, o);
-  if (lane == 0) s_red[warp] = tr;
-  __syncthreads();
-  T trace = 0;
-  for (int w = 0; w < nwarps; ++w) trace += s_red[w];
-  if (!isfinite(trace)) {
-    if (tid == 0) post_error(info, RQLP_ERR_NONFINITE, 0);
-    write_identity(d, R, Rinv, ldr);
-    return;
-  }
-  const T shift = (T)(100.0 * d) * Eps<T>::u * trace;
   const T rel_tol = (T)64 * Eps<T>::u;
-
+  T shift = 0;
   int fail = -1;
   for (int attempt = 0; attempt < 2; ++attempt) {
     const T sh = attempt == 0 ? (T)0 : shift;
-    // Lower triangle of G (+ sh I) into S, zeros above: a warp per pair of
-    // rows, lanes over columns, all of a pair's loads issued before its stores.
-    for (int i0 = 2 * warp; i0 < d; i0 += 2 * nwarps) {
-      T v[2][kMaxD / 32];
+    // Lower triangle of G (+ sh I) into S, zeros above: a warp per group of
+    // four rows, lanes over columns, all of a group's loads issued before
+    // its stores.
+    for (int i0 = 4 * warp; i0 < d; i0 += 4 * nwarps) {
+      T v[4][kMaxD / 32];
 #pragma unroll
-      for (int r = 0; r < 2; ++r)
+      for (int r = 0; r < 4; ++r)
 #pragma unroll
         for (int t = 0; t < kMaxD / 32; ++t) {
           const int i = i0 + r, j = lane + 32 * t;
           v[r][t] = (i < d && j <= i) ? (T)G[(int64_t)i * ldg + j] : (T)0;
         }
 #pragma unroll
-      for (int r = 0; r < 2; ++r)
+      for (int r = 0; r < 4; ++r)
 #pragma unroll
         for (int t = 0; t < kMaxD / 32; ++t) {
           const int i = i0 + r, j = lane + 32 * t;
@@ -138,204 +194,145 @@ __device__ __forceinline__ void chol_body(int d, const float* __restrict__ G, in
         }
     }
     __syncthreads();
+    if (attempt == 0) {   // trace(G), reduced by every warp in the same order
+      T tr = 0;
+      for (int i = lane; i < d; i += 32) tr += gdiag[i];
+      for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
+      if (!isfinite(tr)) {
+        if (tid == 0) post_error(info, RQLP_ERR_NONFINITE, 0);
+        write_identity(d, R, Rinv, ldr);
+        return;
+      }
+      shift = (T)(100.0 * d) * Eps<T>::u * tr;
+    }
     fail = -1;
+    // Panel loop. Phase B of panel J: warp 0 factors the diagonal block while
+    // the other warps finish the previous panel's update of the rows above
+    // (X -= L_IJ W_J,:, rows [0, j0)); the two touch disjoint parts of S.
     for (int j0 = 0; j0 < d; j0 += NB) {
       const int jb = min(NB, d - j0);
-      // (1) diagonal block, warp 0 (lane = row): left-looking Cholesky, row j
-      // of L_JJ broadcast by shuffles, one reciprocal square root per column;
-      // then D = L_JJ^{-1} with lane = column, rows of L_JJ broadcast the same
-      // way. Everything stays in registers until the results are stored.
+      const int jn = j0 + jb, Nt = d - jn;
       if (warp == 0) {
-        T l[NB];
+        // (1) L_JJ, lane = row, right-looking: column t is scaled by
+        // 1 / sqrt(pivot), then every later column c takes l_it l_ct (l_ct
+        // from lane c by a shuffle). Only column t + 1's update lies on the
+        // path to the next pivot. Branch-free; entries above the diagonal are
+        // cleared before the store.
+        T l[NB], gd[NB];
 #pragma unroll
         for (int k = 0; k < NB; k += 4) {
           if (lane < jb) ld4(&S[(size_t)(j0 + lane) * LDS + j0 + k], &l[k]);
           else l[k] = l[k + 1] = l[k + 2] = l[k + 3] = (T)0;
+          ld4(&gdiag[j0 + k], &gd[k]);
+        }
+        int f = -1;
+#pragma unroll
+        for (int t = 0; t < NB; ++t) {
+          const T piv = __shfl_sync(0xffffffffu, l[t], t);
+          const bool live = t < jb;
+          const bool ok = piv > rel_tol * gd[t] && isfinite(piv);
+          f = (f < 0 && live && !ok) ? j0 + t : f;
+          const T rl = rsqrt(ok ? piv : (T)1);
+          if (lane == 0) rdiag[t] = rl;
+          l[t] = lane == t ? piv * rl : (lane > t ? l[t] * rl : (T)0);
+#pragma unroll
+          for (int c = t + 1; c < NB; ++c) l[c] -= l[t] * __shfl_sync(0xffffffffu, l[t], c);
         }
 #pragma unroll
         for (int k = 0; k < NB; ++k)
           if (k > lane) l[k] = (T)0;
-        int f = -1;
+        if (f < 0 && lane < jb) {   // zeros above the diagonal: W's block there is written in (2)
 #pragma unroll
-        for (int j = 0; j < NB; ++j) {
-          if (j < jb && f < 0) {
-            T s = l[j];                       // a_ij - sum_{t<j} l_it l_jt
-#pragma unroll
-            for (int t = 0; t < j; ++t) s -= l[t] * __shfl_sync(0xffffffffu, l[t], j);
-            const T piv = __shfl_sync(0xffffffffu, s, j);
-            if (!(piv > rel_tol * gdiag[j0 + j]) || !isfinite(piv)) {
-              f = j0 + j;
-            } else {
-              const T rl = rsqrt(piv);
-              if (lane == 0) rdiag[j] = rl;
-              l[j] = lane == j ? piv * rl : (lane > j ? s * rl : (T)0);
-            }
-          }
-        }
-        if (f < 0) {
-#pragma unroll
-          for (int k = 0; k < NB; ++k)
-            if (lane < jb && k <= lane) S[(size_t)(j0 + lane) * LDS + j0 + k] = l[k];
-          __syncwarp();
-          const int c = lane;   // column of D: x[i] = D_ic
-          T x[NB];
-#pragma unroll
-          for (int i = 0; i < NB; ++i) {
-            T s = 0;
-#pragma unroll
-            for (int t = 0; t < i; ++t) s += __shfl_sync(0xffffffffu, l[t], i) * x[t];
-            const T ri = rdiag[i];
-            x[i] = (i < c || i >= jb) ? (T)0 : (i == c ? ri : -s * ri);
-          }
-          if (c < NB) {
-#pragma unroll
-            for (int i = 0; i < NB; ++i) Dinv[i][c] = (c < jb && i < jb) ? x[i] : (T)0;
-          }
+          for (int k = 0; k < NB; k += 4) st4(&S[(size_t)(j0 + lane) * LDS + j0 + k], &l[k]);
         }
         if (lane == 0) s_fail = f;
+      }
+      // The update of the rows above goes to the warps that do not share warp
+      // 0's scheduler (warp % 4 != 0), so that the serial factor issues alone.
+      if (j0 > 0) {
+        if (nwarps >= 8) {
+          if ((warp & 3) != 0)
+            trailing_tiles<T>(S, LDS, WT, PT, d, j0, false, (warp >> 2) * 3 + (warp & 3) - 1, (nwarps >> 2) * 3, lane);
+        } else if (warp > 0 || nwarps == 1) {
+          trailing_tiles<T>(S, LDS, WT, PT, d, j0, false, nwarps > 1 ? warp - 1 : 0, max(nwarps - 1, 1), lane);
+        }
       }
       __syncthreads();
       if (s_fail >= 0) {
         fail = s_fail;
         break;
       }
-      const int jn = j0 + jb, Nt = d - jn;
-      // (2) panel rows below the block, block row of W, and W's diagonal
-      // block. Two threads per row, one for the even and one for the odd
-      // outputs, each reading rows of D as 128-bit broadcasts; results are
-      // computed in registers and stored afterwards.
-      for (int task = tid; task < 2 * (Nt + jn); task += blockDim.x) {
-        const int idx = task >> 1, h = task & 1;
-        if (idx < Nt) {
-          const int i = jn + idx;
-          T v[NB], o[NB / 2];
+      // (2) o = L_JJ^{-1} v by forward substitution, a thread per vector:
+      // panel rows below (v = G_IJ row, o = L_IJ row -> S and PT), rows of
+      // W's block row J (v = the eliminated identity's column, o -> S and
+      // WT) and W's diagonal block (v = unit vector, o = column of D).
+      for (int idx = tid; idx < Nt + jn; idx += blockDim.x) {
+        T v[NB];
+        int src = -1;   // row of S that holds v, or -1 for a unit vector
+        if (idx < Nt) src = jn + idx;
+        else if (idx - Nt < j0) src = idx - Nt;
+        const int cc = idx - Nt - j0;   // diagonal-block column (unit vector e_cc)
+        if (src >= 0) {
 #pragma unroll
-          for (int k = 0; k < NB; k += 4) ld4(&S[(size_t)i * LDS + j0 + k], &v[k]);
+          for (int k = 0; k < NB; k += 4) ld4(&S[(size_t)src * LDS + j0 + k], &v[k]);
+          if (jb < NB) {
 #pragma unroll
-          for (int q = 0; q < NB / 2; ++q) {
-            const int c = 2 * q + h;
-            T s2 = 0;
-#pragma unroll
-            for (int k = 0; k < NB; k += 4) {
-              if (k <= 2 * q + 1) {   // D is zero beyond the diagonal
-                T dv[4];
-                ld4(&Dinv[c][k], dv);
-                s2 += v[k] * dv[0] + v[k + 1] * dv[1] + v[k + 2] * dv[2] + v[k + 3] * dv[3];
-              }
-            }
-            o[q] = s2;
-          }
-#pragma unroll
-          for (int q = 0; q < NB / 2; ++q) {
-            const int c = 2 * q + h;
-            PT[c * PTLD + i] = o[q];
-            S[(size_t)i * LDS + j0 + c] = o[q];
+            for (int k = 0; k < NB; ++k)
+              if (k >= jb) v[k] = (T)0;
           }
         } else {
-          const int c = idx - Nt;
-          if (c < j0) {
-            T w[NB], o[NB / 2];
 #pragma unroll
-            for (int k = 0; k < NB; k += 4) ld4(&S[(size_t)c * LDS + j0 + k], &w[k]);
-            if (jb < NB) {
+          for (int k = 0; k < NB; ++k) v[k] = k == cc ? (T)1 : (T)0;
+        }
+        T o[NB];
 #pragma unroll
-              for (int k = 0; k < NB; ++k)
-                if (k >= jb) w[k] = (T)0;
+        for (int c = 0; c < NB; ++c) {
+          if (c < jb) {
+            const T* lr = &S[(size_t)(j0 + c) * LDS + j0];
+            T sacc = v[c];
+#pragma unroll
+            for (int k = 0; k < c; k += 4) {
+              T lv[4];
+              ld4(&lr[k], lv);
+#pragma unroll
+              for (int u = 0; u < 4; ++u)
+                if (k + u < c) sacc -= lv[u] * o[k + u];
             }
-#pragma unroll
-            for (int q = 0; q < NB / 2; ++q) {
-              const int rr = 2 * q + h;
-              T s2 = 0;
-#pragma unroll
-              for (int k = 0; k < NB; k += 4) {
-                if (k <= 2 * q + 1) {
-                  T dv[4];
-                  ld4(&Dinv[rr][k], dv);
-                  s2 += dv[0] * w[k] + dv[1] * w[k + 1] + dv[2] * w[k + 2] + dv[3] * w[k + 3];
-                }
-              }
-              o[q] = s2;
-            }
-#pragma unroll
-            for (int q = 0; q < NB / 2; ++q) {
-              const int rr = 2 * q + h;
-              if (rr < jb) {
-                S[(size_t)c * LDS + j0 + rr] = o[q];
-                WT[rr * PTLD + c] = o[q];
-              }
-            }
+            o[c] = sacc * rdiag[c];
           } else {
-            const int cc = c - j0;
-            if (h == 0) wdiag[c] = Dinv[cc][cc];
+            o[c] = (T)0;
+          }
+        }
+        if (idx < Nt) {
+          const int i = jn + idx;
 #pragma unroll
-            for (int q = 0; q < NB / 2; ++q) {
-              const int rr = 2 * q + h;
-              if (rr < jb) {
-                const T wv = rr >= cc ? Dinv[rr][cc] : (T)0;
-                if (rr > cc) S[(size_t)c * LDS + j0 + rr] = wv;
-                WT[rr * PTLD + c] = wv;
-              }
+          for (int c = 0; c < NB; ++c) PT[c * PTLD + i] = o[c];
+#pragma unroll
+          for (int k = 0; k < NB; k += 4) st4(&S[(size_t)i * LDS + j0 + k], &o[k]);
+        } else if (src >= 0) {
+#pragma unroll
+          for (int rr = 0; rr < NB; ++rr) {
+            if (rr < jb) {
+              S[(size_t)src * LDS + j0 + rr] = o[rr];
+              WT[rr * PTLD + src] = o[rr];
+            }
+          }
+        } else {
+          const int c = j0 + cc;
+          wdiag[c] = rdiag[cc];   // = o[cc]
+#pragma unroll
+          for (int rr = 0; rr < NB; ++rr) {
+            if (rr < jb) {
+              if (rr > cc) S[(size_t)c * LDS + j0 + rr] = o[rr];
+              WT[rr * PTLD + c] = o[rr];
             }
           }
         }
       }
       __syncthreads();
-      // (3) trailing updates G_II -= L_IJ L_IJ^T (lower part) and X -= L_IJ W_J,:
-      // (rows above), each thread taking 4 x 4 blocks: two 128-bit loads of
-      // panel values per 16 FMAs, then a vectorised read-modify-write of S.
-      if (Nt > 0) {
-        const int nbc = (Nt + 3) / 4;              // 4-column blocks over [jn, d)
-        const int nbl = nbc * (nbc + 1) / 2;       // lower blocks: block row >= block column
-        const int nbw = ((jn + 3) / 4) * nbc;      // W blocks: rows [0, jn) x columns [jn, d)
-        for (int b = tid; b < nbl + nbw; b += blockDim.x) {
-          int r0, c0, rlim;
-          bool lower;
-          if (b < nbl) {
-            int br = (int)((sqrtf(8.f * (float)b + 1.f) - 1.f) * 0.5f);
-            while ((br + 1) * (br + 2) / 2 <= b) ++br;
-            while (br * (br + 1) / 2 > b) --br;
-            r0 = jn + 4 * br;
-            c0 = jn + 4 * (b - br * (br + 1) / 2);
-            rlim = d;
-            lower = true;
-          } else {
-            const int w = b - nbl;
-            r0 = 4 * (w / nbc);
-            c0 = jn + 4 * (w % nbc);
-            rlim = jn;
-            lower = false;
-          }
-          const T* Ar = lower ? PT : WT;
-          T acc[4][4];
-#pragma unroll
-          for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) acc[i][j] = 0;
-#pragma unroll
-          for (int k = 0; k < NB; ++k) {
-            T av[4], bv[4];
-            ld4(&Ar[k * PTLD + r0], av);
-            ld4(&PT[k * PTLD + c0], bv);
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-              for (int j = 0; j < 4; ++j) acc[i][j] += av[i] * bv[j];
-          }
-#pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const int r = r0 + i;
-            if (r >= rlim) continue;
-            T sv[4];
-            ld4(&S[(size_t)r * LDS + c0], sv);
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-              const int c = c0 + j;
-              if (c < d && (!lower || c <= r)) sv[j] -= acc[i][j];
-            }
-            st4(&S[(size_t)r * LDS + c0], sv);
-          }
-        }
-      }
+      // (3) trailing update G_II -= L_IJ L_IJ^T of the lower part; the rows
+      // above follow in the next panel's phase B.
+      if (Nt > 0) trailing_tiles<T>(S, LDS, PT, PT, d, jn, true, warp, nwarps, lane);
       __syncthreads();
     }
     if (fail < 0) break;
@@ -353,20 +350,20 @@ __device__ __forceinline__ void chol_body(int d, const float* __restrict__ G, in
   }
   // R = L^T (upper); R^{-1} = W^T: strict upper part from S, diagonal from wdiag.
   for (int i = warp; i < d; i += nwarps) {   // a warp per row, lanes over columns
-    float* r = R + (int64_t)i * ldr;
+    float* r = R != nullptr ? R + (int64_t)i * ldr : nullptr;
     float* ri = Rinv + (int64_t)i * ldr;
     for (int l = lane; l < d; l += 32) {
-      r[l] = l >= i ? (float)S[(size_t)l * LDS + i] : 0.f;
+      if (R != nullptr) r[l] = l >= i ? (float)S[(size_t)l * LDS + i] : 0.f;
       ri[l] = l > i ? (float)S[(size_t)i * LDS + l] : (l == i ? (float)wdiag[i] : 0.f);
     }
   }
 }
 
-template <typename T>
+template <typename T, bool kShared>
 __global__ void __launch_bounds__(kThreads)
 chol_blocked_kernel(int d, const float* __restrict__ G, int64_t ldg, float* __restrict__ R, float* __restrict__ Rinv,
                     int64_t ldr, int* info, double* shift_count, int* gate_out, const int* gate_in, T* gS) {
-  chol_body<T>(d, G, ldg, R, Rinv, ldr, info, shift_count, gate_out, gate_in, gS);
+  chol_body<T, kShared>(d, G, ldg, R, Rinv, ldr, info, shift_count, gate_out, gate_in, gS);
 }
 
 // One CTA per problem of a batch; every square buffer in shared memory.
@@ -376,7 +373,7 @@ chol_batched_kernel(const CholJob* __restrict__ jobs, int count) {
   const int b = blockIdx.x;
   if (b >= count) return;
   const CholJob j = jobs[b];
-  chol_body<T>(j.d, j.G, j.ldg, j.R, j.Rinv, j.ldr, j.info, j.shift_count, j.gate_out, j.gate_in, nullptr);
+  chol_body<T, true>(j.d, j.G, j.ldg, j.R, j.Rinv, j.ldr, j.info, j.shift_count, j.gate_out, j.gate_in, nullptr);
 }
 
 size_t smem_optin_chol() {
@@ -397,7 +394,7 @@ size_t square_bytes(int d) { return (size_t)d * lds_of(d) * sizeof(T); }
 template <typename T>
 size_t panel_bytes(int d) { return (size_t)2 * NB * ptld_of(d) * sizeof(T); }
 template <typename T>
-size_t static_bytes() { return (2 * kMaxD + NB * NB + NB + 32) * sizeof(T) + 96; }
+size_t static_bytes() { return (2 * kMaxD + NB) * sizeof(T) + 96; }
 template <typename T>
 bool square_in_smem(int d) {
   return square_bytes<T>(d) + panel_bytes<T>(d) + static_bytes<T>() <= smem_optin_chol();
@@ -408,16 +405,22 @@ cudaError_t launch(int d, const float* G, int64_t ldg, float* R, float* Rinv, in
                    double* shift_count, int* gate_out, const int* gate_in, void* gstore, cudaStream_t st) {
   static bool configured = false;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(chol_blocked_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(smem_optin_chol() - static_bytes<T>()));
+    const int cap = (int)(smem_optin_chol() - static_bytes<T>());
+    cudaError_t e = cudaFuncSetAttribute(chol_blocked_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(chol_blocked_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
     if (e != cudaSuccess) return e;
     configured = true;
   }
   const bool in_smem = square_in_smem<T>(d);
   if (!in_smem && gstore == nullptr) return cudaErrorInvalidValue;
   const size_t dyn = panel_bytes<T>(d) + (in_smem ? square_bytes<T>(d) : 0);
-  chol_blocked_kernel<T><<<1, kThreads, dyn, st>>>(d, G, ldg, R, Rinv, ldr, info, shift_count, gate_out, gate_in,
-                                                    in_smem ? nullptr : reinterpret_cast<T*>(gstore));
+  if (in_smem)
+    chol_blocked_kernel<T, true><<<1, kThreads, dyn, st>>>(d, G, ldg, R, Rinv, ldr, info, shift_count, gate_out,
+                                                           gate_in, nullptr);
+  else
+    chol_blocked_kernel<T, false><<<1, kThreads, dyn, st>>>(d, G, ldg, R, Rinv, ldr, info, shift_count, gate_out,
+                                                            gate_in, reinterpret_cast<T*>(gstore));
   note_launch();
   return cudaGetLastError();
 }

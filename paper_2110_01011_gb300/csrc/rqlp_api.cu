@@ -63,7 +63,7 @@ class Ops {
   // gates[0] is raised if the Cholesky had to shift.
   cudaError_t gram_chol(const float* X, int64_t ldx, int64_t rows) {
     CK(gram(X, ldx, rows, nullptr));
-    return chol(0, &gates[0], nullptr);
+    return chol(0, &gates[0], nullptr, true);
   }
   // out = X R0^{-1} with the inverse already in slot 0. For a prefix of the
   // columns the leading block of the triangular inverse is the inverse of the
@@ -112,9 +112,11 @@ class Ops {
     return gemm_f32_ex(false, rows, d_, d_, X, ldx, Rinv, ld_, out, ldout, 1, nullptr, nullptr, gate,
                        gate ? kGateCopy : kGateNone, true, st_);
   }
-  cudaError_t chol(int slot, int* gate_out, const int* gate_in) {
-    return chol_inv(d_, G_, ld_, R_[slot], Ri_[slot], ld_, info_, &scal[2], gate_out, gate_in, cstore_,
-                    o_.small_fp64 != 0, st_);
+  // want_r: also write R (slot) besides R^{-1}; the passes that only
+  // orthonormalise need the inverse alone.
+  cudaError_t chol(int slot, int* gate_out, const int* gate_in, bool want_r) {
+    return chol_inv(d_, G_, ld_, want_r ? R_[slot] : nullptr, Ri_[slot], ld_, info_, &scal[2], gate_out, gate_in,
+                    cstore_, o_.small_fp64 != 0, st_);
   }
   // One CholeskyQR pass (shifted on breakdown) on the tensor cores: out =
   // X R^{-1}; gate_out raised if the Cholesky shifted. R only has to
@@ -124,11 +126,11 @@ class Ops {
   // leading-diagonal error of L on the 20000^2 class); six products bring it
   // to the FP32 product's level.
   cudaError_t tc_cqr(const float* X, int64_t ldx, int64_t rows, float* out, int64_t ldout, int slot,
-                     int* gate_out) {
+                     int* gate_out, bool want_r) {
     tcs_.reset();
     CK(tcs_.split(X, rows, d_, ldx, nullptr, st_));
     CK(tcs_.gram(G_, ld_, info_, st_));
-    CK(chol(slot, gate_out, nullptr));
+    CK(chol(slot, gate_out, nullptr, want_r));
     return tcs_.pass(false, X, rows, d_, ldx, Ri_[slot], ld_, d_, out, ldout, nullptr, info_, st_, true);
   }
   // One CholeskyQR pass (shifted on breakdown): out = X R^{-1}. have_r0: the
@@ -136,9 +138,9 @@ class Ops {
   cudaError_t orth_inter(const float* X, int64_t ldx, int64_t rows, float* out, int64_t ldout,
                          bool have_r0 = false) {
     if (have_r0) return apply_r0(X, ldx, rows, out, ldout);
-    if (tc_on_ && rows > (int64_t)d_) return tc_cqr(X, ldx, rows, out, ldout, 0, nullptr);
+    if (tc_on_ && rows > (int64_t)d_) return tc_cqr(X, ldx, rows, out, ldout, 0, nullptr, false);
     CK(gram(X, ldx, rows, nullptr));
-    CK(chol(0, nullptr, nullptr));
+    CK(chol(0, nullptr, nullptr, false));
     return trmm(X, ldx, rows, Ri_[0], out, ldout, nullptr);
   }
   // CholeskyQR2 plus a third pass gated on a shifted Cholesky (shifted
@@ -147,22 +149,23 @@ class Ops {
   cudaError_t orth_final(float* X, int64_t ldx, int64_t rows, float* out, int64_t ldout, float* tmp,
                          float* Racc, int slot, bool have_r0 = false) {
     int* g = &gates[slot];
+    const bool want_r = Racc != nullptr;
     if (have_r0) {   // first pass from the probe's R (slot 0, gate in gates[0])
       CK(apply_r0(X, ldx, rows, tmp, ld_));
     } else if (tc_on_ && rows > (int64_t)d_) {
       // First pass on the tensor cores (BF16x3 Gram, exact-mode X R^{-1});
       // the second pass, which sets the orthogonality, stays in FP32.
-      CK(tc_cqr(X, ldx, rows, tmp, ld_, 0, g));
+      CK(tc_cqr(X, ldx, rows, tmp, ld_, 0, g, want_r));
     } else {
       CK(gram(X, ldx, rows, nullptr));
-      CK(chol(0, g, nullptr));
+      CK(chol(0, g, nullptr, want_r));
       CK(trmm(X, ldx, rows, Ri_[0], tmp, ld_, nullptr));
     }
     CK(gram(tmp, ld_, rows, nullptr));
-    CK(chol(1, g, nullptr));
+    CK(chol(1, g, nullptr, want_r));
     CK(trmm(tmp, ld_, rows, Ri_[1], X, ldx, nullptr));
     CK(gram(X, ldx, rows, g));
-    CK(chol(2, nullptr, g));
+    CK(chol(2, nullptr, g, want_r));
     CK(trmm(X, ldx, rows, Ri_[2], out, ldout, g));
     if (Racc != nullptr) {
       CK(gemm_f32_ex(false, d_, d_, d_, R_[1], ld_, R_[0], ld_, Ra_, ld_, 1, nullptr, nullptr, nullptr,
