@@ -3,18 +3,21 @@
 // (R^{-1} = W^T).
 //
 // Blocked right-looking elimination on the augmented matrix [G | I] with
-// 16-column panels:
-//   (1) one warp factors the 16 x 16 diagonal block (left-looking, row per
-//       lane, rows of L_JJ broadcast by shuffles) and inverts it (column per
-//       lane, same broadcasts): L_JJ, D = L_JJ^{-1};
-//   (2) panel L_IJ = G_IJ D^T for the rows below, and the block row of W:
-//       W_J,: = D X_J,: (X = the eliminated identity, W_JJ = D);
+// 16-column panels J:
+//   (1) warp 0 factors the 16 x 16 diagonal block L_JJ (row per lane,
+//       right-looking, column t's entries broadcast by shuffles);
+//   (2) forward substitutions o = L_JJ^{-1} v, a thread per vector: the
+//       panel L_IJ = G_IJ L_JJ^{-T} for the rows below, the block row of W
+//       (W_J,: = L_JJ^{-1} X_J,:, X = the eliminated identity) and its
+//       diagonal block L_JJ^{-1};
 //   (3) trailing updates G_II -= L_IJ L_IJ^T (lower part) and
-//       X_I,: -= L_IJ W_J,: for the rows below.
-// Step (3) gives each thread 4 x 4 blocks of outputs, with the panel operands
-// in transposed shared-memory buffers (one 128-bit load of row values and one
-// of column values per 16 FMAs). L lives in the lower triangle of one square buffer and
-// W^T in its strict upper triangle (W's diagonal in a side array).
+//       X_:J' -= L_IJ W_J,: for the rows above the next panel. The latter only
+//       feeds later block rows of W, so it runs during the next panel's step
+//       (1), on the warps that do not share warp 0's scheduler.
+// Step (3) gives each warp 32 x 16 tiles and each lane 4 x 4 blocks, with the
+// panel operands in transposed shared-memory buffers. L lives in the lower
+// triangle of one square buffer and W^T in its strict upper triangle (W's
+// diagonal in a side array).
 //
 // A pivot that is not clearly positive restarts the elimination on G + s I
 // (shifted CholeskyQR, Fukaya et al. 2020) and raises the caller's gate flag;
