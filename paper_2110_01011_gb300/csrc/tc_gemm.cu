@@ -16,7 +16,10 @@
 // times larger relative to the result.
 //
 // Data flow per factorisation: split_a_kernel writes A_hi, A_lo once (and
-// ||A||_F^2); prep_x_kernel writes X_hi^T, X_lo^T (d x K, K-major) before
+// ||A||_F^2) in 64-column panels: panel c / 64 holds rows 0..m-1 of those
+// 64 columns, 128 bytes per row, so that each part of an A tile is one TMA
+// box (A^T X: 32 rows of two panels; A X: 128 rows of one panel);
+// prep_x_kernel writes X_hi^T, X_lo^T (d x K, K-major) before
 // every pass; tc_pass_kernel streams A tiles through shared memory with TMA
 // and issues tcgen05.mma from one thread. A tile whose K range is split over
 // several CTAs (stream-K) is finished by the CTA that arrives last on the
@@ -46,22 +49,27 @@ namespace {
 using bf16 = __nv_bfloat16;
 
 constexpr int BM = 128;              // MMA M: output rows per tile (TMEM lanes)
-constexpr int BK = 32;               // K per pipeline stage (64 bytes of BF16)
+constexpr int BK = 32;               // K per pipeline stage of the Gram kernel (64 bytes of BF16)
 constexpr int kThreads = 192;        // 6 warps
 constexpr int kMaxStages = 8;
 constexpr long long kWaitLimit = 4000000000LL;   // cycles (~2 s) before a wait gives up
-constexpr uint32_t kABytes = BM * BK * 2;        // one BF16 A tile (8 KB)
+constexpr uint32_t kABytes = BM * BK * 2;        // one BF16 A tile of the Gram kernel (8 KB)
+// K per pipeline stage of a pass: 64 (128-byte rows, 128B swizzle) where at
+// least three such stages fit in shared memory, else 32 (64-byte rows, 64B
+// swizzle). Larger TMA boxes stream A faster (measured: 7.1 vs 5.2 TB/s of
+// A_hi + A_lo in the A^T X order at d = 64), but the pipeline needs stages in
+// flight: at d = 224 only two K = 64 stages fit, and K = 32 with five is as fast.
 constexpr int kMaxSlots = 16;                    // partial tiles summed from a cached slot list
 // The FP32 accumulation of tcgen05.mma in TMEM loses a little of every add in
 // the same direction: over K = 20000 a pass shrinks by ~1.5e-6 relative to
 // its partial sums, which the cancelling small-singular-value columns of
 // A P~ turn into ~1e-4 of their own size (and into the leading diagonal of
-// L). Accumulation chains in TMEM are therefore cut every kChunk k-blocks
+// L). Accumulation chains in TMEM are therefore cut every kChunkK of K
 // (K = 4096); the epilogue adds the chunks in FP32 with round-to-nearest.
 // The error falls linearly with the chunk (leading diagonal of L on the
 // 20000^2 class: 4.2e-5, 2.1e-5, 9.4e-6 at K = 8192, 4096, 2048) and the time
 // rises ~3% per halving.
-constexpr int kChunk = 128;
+constexpr int kChunkK = 4096;
 
 struct TcArgs {
   int M, K, d, npad, kblocks, tiles, G, stages;
@@ -94,16 +102,16 @@ __host__ __device__ inline int unit_owner(long long u, long long units, int G) {
 }
 
 // End of the accumulation chunk that starts at unit u (a CTA's range [.., u1)).
-__device__ inline long long chunk_end(long long u, long long u1, int KB) {
+__device__ inline long long chunk_end(long long u, long long u1, int KB, int chunk) {
   const long long t_end = (u / KB + 1) * (long long)KB;
-  return min(min(u1, t_end), u + kChunk);
+  return min(min(u1, t_end), u + chunk);
 }
 
 __device__ void post_timeout(int* info) {
   if (info != nullptr && atomicCAS(info, 0, RQLP_ERR_TIMEOUT) == 0) info[1] = 0;
 }
 
-template <bool MN_A>
+template <bool MN_A, int BKP>
 __global__ void __launch_bounds__(kThreads, 1)
 tc_pass_kernel(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUtensorMap tmAlo,
                const __grid_constant__ CUtensorMap tmXhi, const __grid_constant__ CUtensorMap tmXlo,
@@ -155,8 +163,13 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant_
   // Stage layout: A_hi, A_lo[, A_lo2], X_hi[, X_lo[, X_lo2]].
   const bool ex = a.exact != 0;
   const int nx = ex ? 3 : ((*a.xlo_nonzero) ? 2 : 1);
-  const uint32_t xbytes = (uint32_t)a.npad * BK * 2;
-  const uint32_t xoff = (ex ? 3u : 2u) * kABytes;
+  constexpr uint32_t kAP = BM * BKP * 2;   // one BF16 A tile
+  constexpr int kChunk = kChunkK / BKP;
+  constexpr uint32_t kRow = BKP * 2;        // bytes of a K-major row: the swizzle span
+  constexpr uint32_t kSbo = 8 * kRow;       // 8-row swizzle atom of the K-major operands
+  constexpr uint32_t kSw = BKP == 64 ? tc::kSwizzle128 : tc::kSwizzle64;
+  const uint32_t xbytes = (uint32_t)a.npad * BKP * 2;
+  const uint32_t xoff = (ex ? 3u : 2u) * kAP;
 
   if (warp == 4 && lane == 0) {
     // ------------------------------------------------ TMA producer
@@ -177,23 +190,20 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant_
       const int t = (int)(u / KB), kb = (int)(u % KB);
       unsigned char* base = smem + (size_t)stage * a.stage_bytes;
       tc::mbar_expect_tx(&full[stage], xoff + (uint32_t)nx * xbytes);
-      if (MN_A) {
-        tc::tma_load_2d(base, &tmAhi, &full[stage], t * BM, kb * BK);
-        tc::tma_load_2d(base + kABytes / 2, &tmAhi, &full[stage], t * BM + 64, kb * BK);
-        tc::tma_load_2d(base + kABytes, &tmAlo, &full[stage], t * BM, kb * BK);
-        tc::tma_load_2d(base + kABytes + kABytes / 2, &tmAlo, &full[stage], t * BM + 64, kb * BK);
-        if (ex) {
-          tc::tma_load_2d(base + 2 * kABytes, &tmAlo2, &full[stage], t * BM, kb * BK);
-          tc::tma_load_2d(base + 2 * kABytes + kABytes / 2, &tmAlo2, &full[stage], t * BM + 64, kb * BK);
-        }
-      } else {
-        tc::tma_load_2d(base, &tmAhi, &full[stage], kb * BK, t * BM);
-        tc::tma_load_2d(base + kABytes, &tmAlo, &full[stage], kb * BK, t * BM);
-        if (ex) tc::tma_load_2d(base + 2 * kABytes, &tmAlo2, &full[stage], kb * BK, t * BM);
+      // A maps are 3-D over the panel layout: {column in panel, row, panel}.
+      if (MN_A) {   // 64 rows (K) of panels 2t and 2t + 1 (M), one box
+        tc::tma_load_3d(base, &tmAhi, &full[stage], 0, kb * BKP, 2 * t);
+        tc::tma_load_3d(base + kAP, &tmAlo, &full[stage], 0, kb * BKP, 2 * t);
+        if (ex) tc::tma_load_3d(base + 2 * kAP, &tmAlo2, &full[stage], 0, kb * BKP, 2 * t);
+      } else {      // 128 rows (M) x BKP columns (K) of panel kb BKP / 64
+        const int kx = (kb * BKP) & 63, kp = (kb * BKP) >> 6;
+        tc::tma_load_3d(base, &tmAhi, &full[stage], kx, t * BM, kp);
+        tc::tma_load_3d(base + kAP, &tmAlo, &full[stage], kx, t * BM, kp);
+        if (ex) tc::tma_load_3d(base + 2 * kAP, &tmAlo2, &full[stage], kx, t * BM, kp);
       }
-      tc::tma_load_2d(base + xoff, &tmXhi, &full[stage], kb * BK, 0);
-      if (nx >= 2) tc::tma_load_2d(base + xoff + xbytes, &tmXlo, &full[stage], kb * BK, 0);
-      if (nx == 3) tc::tma_load_2d(base + xoff + 2 * xbytes, &tmXlo2, &full[stage], kb * BK, 0);
+      tc::tma_load_2d(base + xoff, &tmXhi, &full[stage], kb * BKP, 0);
+      if (nx >= 2) tc::tma_load_2d(base + xoff + xbytes, &tmXlo, &full[stage], kb * BKP, 0);
+      if (nx == 3) tc::tma_load_2d(base + xoff + 2 * xbytes, &tmXlo2, &full[stage], kb * BKP, 0);
     }
     if (!ok) post_timeout(a.info);
     // Drain: every load this thread started has landed before the CTA exits.
@@ -206,7 +216,7 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant_
     bool ok = true;
     long long u = u0;
     while (u < u1 && ok) {
-      const long long seg_begin = u, seg_end = chunk_end(u, u1, KB);
+      const long long seg_begin = u, seg_end = chunk_end(u, u1, KB, kChunk);
       const int ab = seg & 1;
       if (!tc::mbar_wait(&acce[ab], (uint32_t)(((seg >> 1) & 1) ^ 1), kWaitLimit)) { ok = false; break; }
       tc::tc_fence_after();
@@ -216,23 +226,23 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant_
         if (!tc::mbar_wait(&full[stage], (uint32_t)((consumed / S) & 1), kWaitLimit)) { ok = false; break; }
         tc::tc_fence_after();
         const uint32_t base = tc::smem_u32(smem + (size_t)stage * a.stage_bytes);
-        const uint32_t ahi = base, alo = base + kABytes, alo2 = base + 2 * kABytes, xhi = base + xoff,
+        const uint32_t ahi = base, alo = base + kAP, alo2 = base + 2 * kAP, xhi = base + xoff,
                        xlo = xhi + xbytes, xlo2 = xlo + xbytes;
 #pragma unroll
-        for (int ks = 0; ks < BK / 16; ++ks) {
+        for (int ks = 0; ks < BKP / 16; ++ks) {
           uint64_t dah, dal, dal2;
-          if (MN_A) {   // MN-major, 128B swizzle: 16 k-rows = two 1024-byte atoms
-            dah = tc::smem_desc(ahi + ks * 2048, kABytes / 2, 1024, tc::kSwizzle128);
-            dal = tc::smem_desc(alo + ks * 2048, kABytes / 2, 1024, tc::kSwizzle128);
-            dal2 = tc::smem_desc(alo2 + ks * 2048, kABytes / 2, 1024, tc::kSwizzle128);
-          } else {      // K-major, 64B swizzle: 16 k-columns = 32 bytes into the row
-            dah = tc::smem_desc(ahi + ks * 32, 16, 512, tc::kSwizzle64);
-            dal = tc::smem_desc(alo + ks * 32, 16, 512, tc::kSwizzle64);
-            dal2 = tc::smem_desc(alo2 + ks * 32, 16, 512, tc::kSwizzle64);
+          if (MN_A) {   // MN-major, 128B swizzle: 16 k-rows = two 1024-byte atoms; panels kAP / 2 apart
+            dah = tc::smem_desc(ahi + ks * 2048, kAP / 2, 1024, tc::kSwizzle128);
+            dal = tc::smem_desc(alo + ks * 2048, kAP / 2, 1024, tc::kSwizzle128);
+            dal2 = tc::smem_desc(alo2 + ks * 2048, kAP / 2, 1024, tc::kSwizzle128);
+          } else {      // K-major: 16 k-columns = 32 bytes into the row
+            dah = tc::smem_desc(ahi + ks * 32, 16, kSbo, kSw);
+            dal = tc::smem_desc(alo + ks * 32, 16, kSbo, kSw);
+            dal2 = tc::smem_desc(alo2 + ks * 32, 16, kSbo, kSw);
           }
-          const uint64_t dxh = tc::smem_desc(xhi + ks * 32, 16, 512, tc::kSwizzle64);
-          const uint64_t dxl = tc::smem_desc(xlo + ks * 32, 16, 512, tc::kSwizzle64);
-          const uint64_t dxl2 = tc::smem_desc(xlo2 + ks * 32, 16, 512, tc::kSwizzle64);
+          const uint64_t dxh = tc::smem_desc(xhi + ks * 32, 16, kSbo, kSw);
+          const uint64_t dxl = tc::smem_desc(xlo + ks * 32, 16, kSbo, kSw);
+          const uint64_t dxl2 = tc::smem_desc(xlo2 + ks * 32, 16, kSbo, kSw);
           const uint32_t acc = (u > seg_begin || ks > 0) ? 1u : 0u;
           tc::mma_bf16(d_tmem, dah, dxh, a.idesc, acc);
           if (nx >= 2) tc::mma_bf16(d_tmem, dah, dxl, a.idesc, 1u);
@@ -259,7 +269,7 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant_
     long long u = u0;
     while (u < u1) {
       const int t = (int)(u / KB);
-      const long long seg_begin = u, seg_end = chunk_end(u, u1, KB);
+      const long long seg_begin = u, seg_end = chunk_end(u, u1, KB, kChunk);
       // This CTA's part of tile t, and where the chunk sits in it.
       const long long tb = std::max(u0, (long long)t * KB), te = std::min(u1, (long long)(t + 1) * KB);
       const bool whole = tb == (long long)t * KB && te == (long long)(t + 1) * KB;
@@ -445,9 +455,9 @@ tc_gram_kernel(const __grid_constant__ CUtensorMap tmHi, const __grid_constant__
       if (!tc::mbar_wait(&empty[stage], (uint32_t)((issued / S) & 1) ^ 1u, kWaitLimit)) { ok = false; break; }
       unsigned char* base = smem + (size_t)stage * a.stage_bytes;
       tc::mbar_expect_tx(&full[stage], 2 * half);
-      for (int b = 0; b < a.nbox; ++b) {
-        tc::tma_load_2d(base + b * 4096, &tmHi, &full[stage], b * 64, (int)(kb * BK));
-        tc::tma_load_2d(base + half + b * 4096, &tmLo, &full[stage], b * 64, (int)(kb * BK));
+      for (int b = 0; b < a.nbox; ++b) {   // panel b, 32 rows
+        tc::tma_load_3d(base + b * 4096, &tmHi, &full[stage], 0, (int)(kb * BK), b);
+        tc::tma_load_3d(base + half + b * 4096, &tmLo, &full[stage], 0, (int)(kb * BK), b);
       }
     }
     if (!ok) post_timeout(a.info);
@@ -527,12 +537,13 @@ __global__ void tc_gram_reduce_kernel(const float* __restrict__ part, int G, int
   }
 }
 
-// A (m x n FP32) -> A_hi, A_lo (BF16, ld ldb, padding columns zero) and ||A||_F^2.
+// A (m x n FP32) -> A_hi, A_lo (BF16) and ||A||_F^2, in 64-column panels:
+// element (r, c) at ((c / 64) m + r) 64 + c % 64, columns n..npan*64-1 zero.
 // lo2 (optional) receives bf16(A - A_hi - A_lo); both differences are exact in FP32.
 __global__ void split_a_kernel(const float* __restrict__ A, long long m, long long n, long long lda, bool vec,
-                               bf16* __restrict__ hi, bf16* __restrict__ lo, bf16* __restrict__ lo2, long long ldb,
+                               bf16* __restrict__ hi, bf16* __restrict__ lo, bf16* __restrict__ lo2, long long npan,
                                double* sumsq) {
-  const long long cpr = ldb / 8, total = m * cpr;
+  const long long cpr = npan * 8, total = m * cpr;
   float s = 0.f, comp = 0.f;
   for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
@@ -559,9 +570,10 @@ __global__ void split_a_kernel(const float* __restrict__ A, long long m, long lo
       l2[i] = __float2bfloat16_rn(r1 - __bfloat162float(l[i]));
       ss = fmaf(x[i], x[i], ss);
     }
-    *reinterpret_cast<uint4*>(hi + r * ldb + c0) = *reinterpret_cast<const uint4*>(h);
-    *reinterpret_cast<uint4*>(lo + r * ldb + c0) = *reinterpret_cast<const uint4*>(l);
-    if (lo2 != nullptr) *reinterpret_cast<uint4*>(lo2 + r * ldb + c0) = *reinterpret_cast<const uint4*>(l2);
+    const long long o = ((c0 >> 6) * m + r) * 64 + (c0 & 63);
+    *reinterpret_cast<uint4*>(hi + o) = *reinterpret_cast<const uint4*>(h);
+    *reinterpret_cast<uint4*>(lo + o) = *reinterpret_cast<const uint4*>(l);
+    if (lo2 != nullptr) *reinterpret_cast<uint4*>(lo2 + o) = *reinterpret_cast<const uint4*>(l2);
     const float y = ss - comp, tt = s + y;
     comp = (tt - s) - y;
     s = tt;
@@ -646,14 +658,29 @@ bool make_map(CUtensorMap* map, const void* base, long long inner, long long out
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// 3-D BF16 tensor map over the 64-column panel layout of m rows: dims {64,
+// m, panels}, box {bi, bo, bp}.
+bool make_panel_map(CUtensorMap* map, const void* base, long long m, long long panels, int bi, int bo, int bp,
+                    CUtensorMapSwizzle sw) {
+  EncodeFn fn = encode_fn();
+  if (fn == nullptr) return false;
+  cuuint64_t dims[3] = {64, (cuuint64_t)m, (cuuint64_t)panels};
+  cuuint64_t strides[2] = {128, (cuuint64_t)(m * 128)};
+  cuuint32_t box[3] = {(cuuint32_t)bi, (cuuint32_t)bo, (cuuint32_t)bp};
+  cuuint32_t es[3] = {1, 1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 int npad_of(int d) { return (int)round_up(std::max(d, 16), 16); }
 uint32_t tmem_cols_of(int npad) {
   uint32_t need = 2u * (uint32_t)npad, c = 32;
   while (c < need) c <<= 1;
   return c;
 }
-uint32_t stage_bytes_of(int npad, bool exact = false) {
-  return (exact ? 3u : 2u) * kABytes + (exact ? 3u : 2u) * (uint32_t)npad * BK * 2;
+uint32_t stage_bytes_of(int npad, bool exact, int bkp) {
+  return (exact ? 3u : 2u) * (uint32_t)(BM * bkp * 2) + (exact ? 3u : 2u) * (uint32_t)npad * bkp * 2;
 }
 
 size_t smem_optin_tc() {
@@ -669,25 +696,28 @@ size_t smem_optin_tc() {
   return v;
 }
 
-int stages_of(int npad, bool exact = false) {
+// Pipeline stages of a pass (>= 1; the exact mode's stages at d = 256 hold
+// one at a time, which its short K does not need more than).
+int stages_of(int npad, bool exact, int bkp) {
   const size_t avail = smem_optin_tc() - 1024 - 512;
-  int s = (int)(avail / stage_bytes_of(npad, exact));
-  return std::max(2, std::min(kMaxStages, s));
+  int s = (int)(avail / stage_bytes_of(npad, exact, bkp));
+  return std::max(1, std::min(kMaxStages, s));
 }
+int pass_bk(int npad, bool exact) { return stages_of(npad, exact, 64) >= 3 ? 64 : 32; }
 
-template <bool MN_A>
+template <bool MN_A, int BKP>
 cudaError_t launch_pass(const CUtensorMap& ah, const CUtensorMap& al, const CUtensorMap& xh,
                         const CUtensorMap& xl, const CUtensorMap& al2, const CUtensorMap& xl2, const TcArgs& a,
                         cudaStream_t st) {
   const size_t smem = (size_t)a.stages * a.stage_bytes + 1024 + 512;
   static bool configured = false;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(tc_pass_kernel<MN_A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(tc_pass_kernel<MN_A, BKP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)(smem_optin_tc()));
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  tc_pass_kernel<MN_A><<<a.G, kThreads, smem, st>>>(ah, al, xh, xl, al2, xl2, a);
+  tc_pass_kernel<MN_A, BKP><<<a.G, kThreads, smem, st>>>(ah, al, xh, xl, al2, xl2, a);
   note_launch();
   return cudaGetLastError();
 }
@@ -712,7 +742,7 @@ void TcEngine::layout(Arena& ar, int64_t rows_cap, int64_t cols_cap, int d_cap, 
   cols_cap_ = cols_cap;
   d_cap_ = d_cap;
   k_cap_ = k_cap;
-  ldb_ = round_up(cols_cap, 8);
+  ldb_ = round_up(cols_cap, 64);   // whole 64-column panels
   G_ = sm_count();
   const int npad = npad_of(d_cap);
   Ahi_ = ar.take<uint16_t>((size_t)(rows_cap * ldb_));
@@ -734,10 +764,11 @@ cudaError_t TcEngine::split(const float* A, int64_t rows, int64_t cols, int64_t 
                             cudaStream_t st) {
   if (rows > rows_cap_ || cols > cols_cap_) return cudaErrorInvalidValue;
   const bool vec = (reinterpret_cast<uintptr_t>(A) % 16 == 0) && (lda % 4 == 0);
-  const long long total = rows * (ldb_ / 8);
+  const long long npan = cdiv(cols, 64);
+  const long long total = rows * npan * 8;
   const int blocks = (int)std::min<long long>(cdiv(total, 256), (long long)G_ * 8);
   split_a_kernel<<<blocks, 256, 0, st>>>(A, rows, cols, lda, vec, reinterpret_cast<bf16*>(Ahi_),
-                                         reinterpret_cast<bf16*>(Alo_), reinterpret_cast<bf16*>(Alo2_), ldb_,
+                                         reinterpret_cast<bf16*>(Alo_), reinterpret_cast<bf16*>(Alo2_), npan,
                                          sumsq);
   note_launch();
   cudaError_t e = cudaGetLastError();
@@ -780,18 +811,21 @@ cudaError_t TcEngine::pass(bool transA, const float* A, int64_t m, int64_t n, in
   // the low parts'.
   const uint16_t* A3 = exact ? Alo2_ : Alo_;
   const uint16_t* X3 = exact ? Xlo2_ : Xlo_;
-  if (transA) {   // op(A) = A^T: MN-major tiles, box 64 (j) x 32 (i), 128B swizzle
-    ok = make_map(&ah, Ahi_, n, m, ldb_, 64, BK, CU_TENSOR_MAP_SWIZZLE_128B) &&
-         make_map(&al, Alo_, n, m, ldb_, 64, BK, CU_TENSOR_MAP_SWIZZLE_128B) &&
-         make_map(&al2, A3, n, m, ldb_, 64, BK, CU_TENSOR_MAP_SWIZZLE_128B);
-  } else {        // op(A) = A: K-major tiles, box 32 (j) x 128 (i), 64B swizzle
-    ok = make_map(&ah, Ahi_, n, m, ldb_, BK, BM, CU_TENSOR_MAP_SWIZZLE_64B) &&
-         make_map(&al, Alo_, n, m, ldb_, BK, BM, CU_TENSOR_MAP_SWIZZLE_64B) &&
-         make_map(&al2, A3, n, m, ldb_, BK, BM, CU_TENSOR_MAP_SWIZZLE_64B);
+  const long long npan = cdiv(n, 64);
+  const int bkp = pass_bk(npad_, exact);
+  const CUtensorMapSwizzle ksw = bkp == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
+  if (transA) {   // op(A) = A^T: MN-major tiles, box 64 (j) x 32 (i) x 2 panels, 128B swizzle
+    ok = make_panel_map(&ah, Ahi_, m, npan, 64, bkp, 2, CU_TENSOR_MAP_SWIZZLE_128B) &&
+         make_panel_map(&al, Alo_, m, npan, 64, bkp, 2, CU_TENSOR_MAP_SWIZZLE_128B) &&
+         make_panel_map(&al2, A3, m, npan, 64, bkp, 2, CU_TENSOR_MAP_SWIZZLE_128B);
+  } else {        // op(A) = A: K-major tiles, box bkp (j) x 128 (i), swizzle = the row
+    ok = make_panel_map(&ah, Ahi_, m, npan, bkp, BM, 1, ksw) &&
+         make_panel_map(&al, Alo_, m, npan, bkp, BM, 1, ksw) &&
+         make_panel_map(&al2, A3, m, npan, bkp, BM, 1, ksw);
   }
-  ok = ok && make_map(&xh, Xhi_, K, d, ldk, BK, npad_, CU_TENSOR_MAP_SWIZZLE_64B) &&
-       make_map(&xl, Xlo_, K, d, ldk, BK, npad_, CU_TENSOR_MAP_SWIZZLE_64B) &&
-       make_map(&xl2, X3, K, d, ldk, BK, npad_, CU_TENSOR_MAP_SWIZZLE_64B);
+  ok = ok && make_map(&xh, Xhi_, K, d, ldk, bkp, npad_, ksw) &&
+       make_map(&xl, Xlo_, K, d, ldk, bkp, npad_, ksw) &&
+       make_map(&xl2, X3, K, d, ldk, bkp, npad_, ksw);
   if (!ok) return cudaErrorInvalidValue;
 
   TcArgs a;
@@ -799,20 +833,20 @@ cudaError_t TcEngine::pass(bool transA, const float* A, int64_t m, int64_t n, in
   a.K = (int)K;
   a.d = d;
   a.npad = npad_;
-  a.kblocks = (int)cdiv(K, BK);
+  a.kblocks = (int)cdiv(K, bkp);
   a.tiles = (int)cdiv(M, BM);
   a.units = (long long)a.tiles * a.kblocks;
   a.G = (int)std::min<long long>(G_, a.units);
   // Short K (e.g. X R^{-1} with K = d): split tiles would cost more in the
   // epilogue than they save, so give each CTA whole tiles.
   a.tpc = 0;
-  if (a.kblocks <= 16) {
+  if (a.kblocks <= 1024 / bkp) {
     a.tpc = (int)cdiv(a.tiles, G_);
     a.G = (int)cdiv(a.tiles, a.tpc);
   }
   a.vec_out = ((reinterpret_cast<uintptr_t>(out) % 16) == 0 && ldout % 4 == 0) ? 1 : 0;
   a.exact = exact ? 1 : 0;
-  a.stages = stages_of(npad_, exact);
+  a.stages = stages_of(npad_, exact, bkp);
   a.out = out;
   a.ldo = ldout;
   a.part = part_;
@@ -820,12 +854,16 @@ cudaError_t TcEngine::pass(bool transA, const float* A, int64_t m, int64_t n, in
   a.xlo_nonzero = flag_;
   a.info = info;
   a.idesc = tc::idesc_bf16(BM, npad_, transA, false);
-  a.stage_bytes = stage_bytes_of(npad_, exact);
+  a.stage_bytes = stage_bytes_of(npad_, exact, bkp);
   a.tmem_cols = tmem_cols_of(npad_);
   const bool prof = profiled_ && profiling_on();
   if (prof) profile_mark_begin(st);
-  e = transA ? launch_pass<true>(ah, al, xh, xl, al2, xl2, a, st)
-             : launch_pass<false>(ah, al, xh, xl, al2, xl2, a, st);
+  if (bkp == 64)
+    e = transA ? launch_pass<true, 64>(ah, al, xh, xl, al2, xl2, a, st)
+               : launch_pass<false, 64>(ah, al, xh, xl, al2, xl2, a, st);
+  else
+    e = transA ? launch_pass<true, 32>(ah, al, xh, xl, al2, xl2, a, st)
+               : launch_pass<false, 32>(ah, al, xh, xl, al2, xl2, a, st);
   if (prof) profile_mark_end(st, transA ? 1 : 0);
   return e;
 }
@@ -854,8 +892,8 @@ cudaError_t TcEngine::gram(float* Gout, int64_t ldg, int* info, cudaStream_t st)
     a.tmem_cols = c;
   }
   CUtensorMap hi, lo;
-  if (!make_map(&hi, Ahi_, cols, m_, ldb_, 64, BK, CU_TENSOR_MAP_SWIZZLE_128B) ||
-      !make_map(&lo, Alo_, cols, m_, ldb_, 64, BK, CU_TENSOR_MAP_SWIZZLE_128B))
+  if (!make_panel_map(&hi, Ahi_, m_, cdiv(cols, 64), 64, BK, 1, CU_TENSOR_MAP_SWIZZLE_128B) ||
+      !make_panel_map(&lo, Alo_, m_, cdiv(cols, 64), 64, BK, 1, CU_TENSOR_MAP_SWIZZLE_128B))
     return cudaErrorInvalidValue;
   static bool configured = false;
   if (!configured) {
