@@ -70,6 +70,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched form")
     ap.add_argument("--batch", type=int, default=512)
     ap.add_argument("--no-autotune", action="store_true", help="batched leg: default tile shapes")
+    ap.add_argument("--batched-precision", default="both", choices=["both", "fp32", "bf16x3"],
+                    help="batched leg: FP32 products, BF16x3 tensor-core passes, or both (value = BF16x3)")
     ap.add_argument("--sample", type=int, default=0,
                     help="rows/cols of the oracle's sample block (0 = default for the workload)")
     return ap.parse_args()
@@ -355,7 +357,8 @@ def roofline(a, recs, d, prec, peaks, dev):
 
 def batched_leg(a, ctx):
     """512 uneven problems (m in [256, 4096], n in [256, 2048], k in [8, 64],
-    p = 5, q = 1) as one graph launch after autotuning."""
+    p = 5, q = 1) as one graph launch after autotuning, with the passes over
+    A as grouped BF16x3 tensor-core passes and/or as FP32 products."""
     import torch
 
     from paper_2110_01011_gb300 import inputs, rqlp
@@ -364,24 +367,39 @@ def batched_leg(a, ctx):
     As = [inputs.low_rank_matrix_reflect(pr.m, pr.n, pr.sigma(), pr.seed, ctx.dev) for pr in probs]
     Os = [inputs.omega_torch(pr.m, pr.d, pr.seed + 1, ctx.dev) for pr in probs]
     gen_s = time.perf_counter() - t0
-    b = rqlp.Batch(As, Os, [pr.k for pr in probs], [pr.p for pr in probs], probs[0].q)
-    tune = None if a.no_autotune else b.autotune(reps=2)
-    for _ in range(max(1, a.warmup)):
-        b.launch()
-    ctx.barrier()
-    l0 = rqlp.rqlp_kernel_launches()
-    reps = max(3, a.steps)
-    ms = time_steps(ctx, b.launch, reps)
-    launches = (rqlp.rqlp_kernel_launches() - l0) // reps
-    bad = int((b.info[:, 0] != 0).sum().item())
     q = probs[0].q
     abytes = sum((2 * q + 2) * pr.m * pr.n * 4 for pr in probs)
-    out = {"problems": len(probs), "ms_per_batch": ms, "value": ctx.world * abytes / (ms * 1e-3) / 1e9,
-           "unit": "GB/s", "problems_per_s": ctx.world * len(probs) / (ms * 1e-3), "A_bytes_per_batch": abytes,
-           "graph_kernels": launches, "tuning": tune, "nonzero_status": bad, "generate_s": gen_s,
-           "workload": f"{len(probs)} problems, m in [256,4096], n in [256,2048], k in [8,64], p=5, q={q}, "
-                       "half exp / half poly spectra, FP32"}
-    b.close()
+
+    def one(prec):
+        b = rqlp.Batch(As, Os, [pr.k for pr in probs], [pr.p for pr in probs], q, precision=prec)
+        tune = None if a.no_autotune else b.autotune(reps=2)
+        for _ in range(max(1, a.warmup)):
+            b.launch()
+        ctx.barrier()
+        l0 = rqlp.rqlp_kernel_launches()
+        reps = max(3, a.steps)
+        ms = time_steps(ctx, b.launch, reps)
+        launches = (rqlp.rqlp_kernel_launches() - l0) // reps
+        bad = int((b.info[:, 0] != 0).sum().item())
+        res = {"ms_per_batch": ms, "value": ctx.world * abytes / (ms * 1e-3) / 1e9, "unit": "GB/s",
+               "problems_per_s": ctx.world * len(probs) / (ms * 1e-3), "graph_kernels": launches, "tuning": tune,
+               "nonzero_status": bad}
+        b.close()
+        return res
+
+    runs = {}
+    if a.batched_precision in ("both", "bf16x3"):
+        runs["bf16x3"] = one(rqlp.PREC_BF16X3)
+    if a.batched_precision in ("both", "fp32"):
+        runs["fp32"] = one(rqlp.PREC_FP32)
+    head = "bf16x3" if "bf16x3" in runs else "fp32"
+    out = dict(runs[head])
+    out.update({"problems": len(probs), "A_bytes_per_batch": abytes, "generate_s": gen_s, "precision": head,
+                "workload": f"{len(probs)} problems, m in [256,4096], n in [256,2048], k in [8,64], p=5, q={q}, "
+                            "half exp / half poly spectra"})
+    if head == "bf16x3" and "fp32" in runs:
+        out["fp32"] = runs["fp32"]
+        out["speedup_vs_fp32"] = runs["fp32"]["ms_per_batch"] / runs["bf16x3"]["ms_per_batch"]
     del As, Os
     torch.cuda.empty_cache()
     return out
@@ -482,7 +500,8 @@ def main():
         if rank == 0:
             line = {"metric": "batched Rand-QLP A-pass GB/s", "value": bt["value"], "unit": "GB/s", "n_gpus": world,
                     "steps": max(3, a.steps), "warmup": max(1, a.warmup), "ms_per_step": bt["ms_per_batch"],
-                    "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                    "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                    "dtype": "bf16x3" if bt["precision"] == "bf16x3" else "f32",
                     "data": "synthetic", "config": {"workload": bt["workload"], "l2": "inputs larger than L2"},
                     "clocks": clocks, "batched": bt}
             print(json.dumps(line), flush=True)

@@ -238,7 +238,14 @@ rqlp_status rqlp_factor_learned(const float* A, int64_t m, int64_t n, int64_t ld
 
 /* ---- Batched form: many independent problems, each with its own sizes,
  * k, p and buffers (one q for the batch), factored by the chain of
- * rqlp_factor in plain FP32 (RQLP_PREC_BF16X3 -> RQLP_ERR_UNSUPPORTED).
+ * rqlp_factor. opts->precision: RQLP_PREC_FP32 (every product in FP32), or
+ * RQLP_PREC_BF16X3: the passes over A run as grouped tensor-core passes over
+ * BF16 halves of every A (split once per launch into the workspace, which
+ * then also holds the halves, the pass operands' halves and eight tensor
+ * maps per problem), the d-wide products in FP32; RQLP_ERR_UNSUPPORTED on a
+ * device without the tensor-core path. The split form's pass error is
+ * ~2^-16 of |A| |X|, so an |L_ii| near sigma_i carries up to about
+ * 2^-15 sigma_1 / sigma_i of its own size.
  *
  * A batch plan is built once on the host: it lays out the caller's
  * workspace, writes the per-problem job tables into it (one synchronous

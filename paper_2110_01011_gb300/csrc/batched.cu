@@ -18,10 +18,12 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <queue>
 #include <new>
 #include <vector>
 
 #include "common.cuh"
+#include "tc_gemm.cuh"
 
 namespace rqlp {
 namespace {
@@ -46,13 +48,22 @@ int default_cfg(int shape, int bucket) {
   }
 }
 
-// Per-problem device buffers (in the workspace).
+// Per-problem device buffers (in the workspace). The BF16x3 form adds A's
+// halves in 64-column panels, the pass operand's halves (X^T, d x ldk) and
+// eight tensor maps (see tc_grouped.cu).
 struct Bufs {
   float *Y, *Z, *Pt, *T1, *G, *R[3], *Ri[3], *Ra, *Rb, *Rh, *Ts, *Ts2, *Ph;
   double* scal;
   int* gates;
   int64_t ld;
+  uint16_t *Ahi = nullptr, *Alo = nullptr, *XTh = nullptr, *XTl = nullptr;
+  int64_t ldk = 0;
+  char* maps = nullptr;     // 8 x kTcMapBytes
+  int* flag = nullptr;      // X low part nonzero (per pass)
 };
+// Tensor maps of one problem, in this order.
+enum TcMap { kMapAhiT, kMapAloT, kMapAhiN, kMapAloN, kMapXhiM, kMapXloM, kMapXhiN, kMapXloN, kTcMaps };
+constexpr int kMaxTcCtas = 1024;
 
 struct GemmStage {
   bool transA;
@@ -63,10 +74,25 @@ struct GemmStage {
   bool gated;
 };
 
+// A grouped tensor-core pass (BF16x3 form): prep of X, then the pass.
+struct TcStage {
+  bool transA;
+  size_t jobs_off;        // TcGJob[count]
+  size_t prep_off;        // PrepJob[count]
+  size_t prep_start_off;  // int[count + 1]
+  int prep_total;
+  size_t units_off;       // int2[units]
+  size_t cta_off;         // int[kMaxTcCtas + 1]
+  int G;
+  int npad_max;
+};
+
 struct Stage {
-  enum Kind { kInit, kGemm, kChol, kTranspose, kWriteL, kFinish } kind;
-  int gemm = -1;         // index into gemms
-  size_t jobs_off = 0;   // CholJob[] or SmallJob[]
+  enum Kind { kInit, kGemm, kChol, kTranspose, kWriteL, kFinish, kSplit, kTc } kind;
+  int gemm = -1;         // index into gemms / tcs
+  size_t jobs_off = 0;   // CholJob[], SmallJob[] or SplitJob[]
+  size_t start_off = 0;  // kSplit: int[count + 1] block prefix
+  int total = 0;         // kSplit: blocks
 };
 
 }  // namespace
@@ -80,6 +106,11 @@ struct rqlp_batch_s {
   char* dev = nullptr;                       // plan area in the workspace
   std::vector<rqlp::Stage> stages;
   std::vector<rqlp::GemmStage> gemms;
+  std::vector<rqlp::TcStage> tcs;
+  int* flags = nullptr;                      // TC form: one int per problem (bucket order)
+  int* info0 = nullptr;                      // status row that a timed-out grouped pass reports to
+  std::vector<char> maps_h;                  // TC form: host copy of the tensor maps
+  char* maps_d = nullptr;
   int cfg[rqlp::kShapes][rqlp::kBuckets];
   cudaStream_t cap = nullptr;                // capture stream
   cudaGraph_t graph = nullptr;
@@ -125,6 +156,8 @@ struct Builder {
   double* diag;                          // caller order, 4 doubles (optional)
   Stager& sg;
 
+  bool tc;                               // BF16x3: passes over A on the tensor cores
+
   int* info_of(int i) const { return info + 2 * (int64_t)orig[i]; }
 
   int n() const { return (int)pr.size(); }
@@ -169,6 +202,107 @@ struct Builder {
     Stage s;
     s.kind = kind;
     s.jobs_off = sg.put(jobs.data(), jobs.size());
+    b->stages.push_back(s);
+  }
+
+  // BF16 halves of every A (and ||A||_F^2), once per factorisation.
+  void split_stage() {
+    std::vector<SplitJob> js;
+    std::vector<int> st(n() + 1, 0);
+    for (int i = 0; i < n(); ++i) {
+      SplitJob j{};
+      j.A = pr[i].A;
+      j.lda = pr[i].lda;
+      j.m = pr[i].m;
+      j.n = pr[i].n;
+      j.npan = cdiv(pr[i].n, 64);
+      j.hi = bf[i].Ahi;
+      j.lo = bf[i].Alo;
+      j.sumsq = &bf[i].scal[0];
+      j.vec = (reinterpret_cast<uintptr_t>(pr[i].A) % 16 == 0 && pr[i].lda % 4 == 0) ? 1 : 0;
+      js.push_back(j);
+      st[i + 1] = st[i] + tc_split_blocks(pr[i].m, pr[i].n);
+    }
+    Stage s;
+    s.kind = Stage::kSplit;
+    s.jobs_off = sg.put(js.data(), js.size());
+    s.start_off = sg.put(st.data(), st.size());
+    s.total = st[n()];
+    b->stages.push_back(s);
+  }
+  // One grouped tensor-core pass: out(i) = op(A_i) X(i). The (problem, tile)
+  // units go longest first onto the least loaded CTA.
+  template <typename XF, typename LF, typename OF>
+  void tc_pass(bool transA, XF X, LF ldx, OF out) {
+    TcStage ts{};
+    ts.transA = transA;
+    std::vector<TcGJob> js;
+    std::vector<PrepJob> ps;
+    std::vector<int> pst(n() + 1, 0);
+    std::vector<std::pair<long long, int2>> units;
+    ts.npad_max = 16;
+    for (int i = 0; i < n(); ++i) {
+      const int di = d(i), np = tc_npad(di);
+      const int64_t M = transA ? pr[i].n : pr[i].m, K = transA ? pr[i].m : pr[i].n;
+      ts.npad_max = std::max(ts.npad_max, np);
+      TcGJob j{};
+      const char* mp = bf[i].maps;
+      j.mAhi = mp + (transA ? kMapAhiT : kMapAhiN) * kTcMapBytes;
+      j.mAlo = mp + (transA ? kMapAloT : kMapAloN) * kTcMapBytes;
+      j.mXhi = mp + (transA ? kMapXhiM : kMapXhiN) * kTcMapBytes;
+      j.mXlo = mp + (transA ? kMapXloM : kMapXloN) * kTcMapBytes;
+      j.out = out(i);
+      j.ldo = bf[i].ld;
+      j.M = (int)M;
+      j.d = di;
+      j.npad = np;
+      j.kblocks = (int)cdiv(K, 32);
+      j.vec_out = (reinterpret_cast<uintptr_t>(j.out) % 16 == 0 && j.ldo % 4 == 0) ? 1 : 0;
+      j.idesc = tc_idesc(np, transA);
+      j.xlo_nonzero = bf[i].flag;
+      js.push_back(j);
+      PrepJob p{};
+      p.X = X(i);
+      p.ldx = ldx(i);
+      p.K = K;
+      p.d = di;
+      p.th = bf[i].XTh;
+      p.tl = bf[i].XTl;
+      p.ldk = bf[i].ldk;
+      p.flag = bf[i].flag;
+      ps.push_back(p);
+      pst[i + 1] = pst[i] + tc_prep_blocks(K, di);
+      for (int t = 0; t < (int)cdiv(M, 128); ++t) units.push_back({(long long)j.kblocks * (np + 64), int2{i, t}});
+    }
+    std::stable_sort(units.begin(), units.end(), [](const auto& a, const auto& c) { return a.first > c.first; });
+    const int G = (int)std::max<size_t>(1, std::min<size_t>(units.size(), std::min(kMaxTcCtas, sm_count())));
+    std::vector<std::vector<int2>> per(G);
+    std::priority_queue<std::pair<long long, int>, std::vector<std::pair<long long, int>>, std::greater<>> load;
+    for (int c = 0; c < G; ++c) load.push({0, c});
+    for (const auto& u : units) {
+      auto top = load.top();
+      load.pop();
+      per[top.second].push_back(u.second);
+      load.push({top.first + u.first, top.second});
+    }
+    std::vector<int2> flat;
+    std::vector<int> cs(kMaxTcCtas + 1, 0);
+    for (int c = 0; c < G; ++c) {
+      cs[c] = (int)flat.size();
+      flat.insert(flat.end(), per[c].begin(), per[c].end());
+    }
+    for (int c = G; c <= kMaxTcCtas; ++c) cs[c] = (int)flat.size();
+    ts.jobs_off = sg.put(js.data(), js.size());
+    ts.prep_off = sg.put(ps.data(), ps.size());
+    ts.prep_start_off = sg.put(pst.data(), pst.size());
+    ts.prep_total = pst[n()];
+    ts.units_off = sg.put(flat.data(), flat.size());
+    ts.cta_off = sg.put(cs.data(), cs.size());
+    ts.G = G;
+    Stage s;
+    s.kind = Stage::kTc;
+    s.gemm = (int)b->tcs.size();
+    b->tcs.push_back(ts);
     b->stages.push_back(s);
   }
 
@@ -286,8 +420,12 @@ struct Builder {
     }
     small(Stage::kInit, sj);
 
-    // Y = A^T Omega (Algorithm 1 step 3); ||A||_F^2 rides along.
-    {
+    // Y = A^T Omega (Algorithm 1 step 3); ||A||_F^2 rides along (or comes
+    // with the split in the BF16x3 form).
+    if (tc) {
+      split_stage();
+      tc_pass(true, [&](int i) { return pr[i].Omega; }, [&](int i) { return pr[i].ldo; }, Y);
+    } else {
       std::vector<GroupGemm> js;
       for (int i = 0; i < n(); ++i) {
         GroupGemm j = job(pr[i].A, pr[i].lda, pr[i].Omega, pr[i].ldo, bf[i].Y, bf[i].ld, pr[i].n, d(i), pr[i].m);
@@ -297,12 +435,20 @@ struct Builder {
       gemm(true, kTallT, js, false);
     }
     auto passN = [&](auto X, auto out) {   // out (m x d) = A X
+      if (tc) {
+        tc_pass(false, X, ld, out);
+        return;
+      }
       std::vector<GroupGemm> js;
       for (int i = 0; i < n(); ++i)
         js.push_back(job(pr[i].A, pr[i].lda, X(i), bf[i].ld, out(i), bf[i].ld, pr[i].m, d(i), pr[i].n));
       gemm(false, kTallN, js, false);
     };
     auto passT = [&](auto X, auto out) {   // out (n x d) = A^T X
+      if (tc) {
+        tc_pass(true, X, ld, out);
+        return;
+      }
       std::vector<GroupGemm> js;
       for (int i = 0; i < n(); ++i)
         js.push_back(job(pr[i].A, pr[i].lda, X(i), bf[i].ld, out(i), bf[i].ld, pr[i].n, d(i), pr[i].m));
@@ -348,7 +494,7 @@ struct Builder {
   }
 };
 
-Bufs take_bufs(Arena& ar, const rqlp_problem& p) {
+Bufs take_bufs(Arena& ar, const rqlp_problem& p, bool tc) {
   Bufs f{};
   const int d = p.k + p.p;
   f.ld = round_up(d, 4);
@@ -370,7 +516,30 @@ Bufs take_bufs(Arena& ar, const rqlp_problem& p) {
   f.Ph = ar.take<float>(dd);
   f.scal = ar.take<double>(4);
   f.gates = ar.take<int>(kGates);
+  if (tc) {
+    const int64_t cols = round_up(p.n, 64);
+    f.Ahi = ar.take<uint16_t>(p.m * cols);
+    f.Alo = ar.take<uint16_t>(p.m * cols);
+    f.ldk = round_up(tall, 8);
+    f.XTh = ar.take<uint16_t>(d * f.ldk);
+    f.XTl = ar.take<uint16_t>(d * f.ldk);
+  }
   return f;
+}
+
+// The eight tensor maps of one problem (host encoding; false on failure).
+bool encode_maps(const Bufs& f, const rqlp_problem& p, char* out) {
+  const int d = p.k + p.p, np = tc_npad(d);
+  const long long npan = cdiv(p.n, 64);
+  auto at_map = [&](int k) { return out + k * kTcMapBytes; };
+  return tc_panel_map(at_map(kMapAhiT), f.Ahi, p.m, npan, 64, 32, 2, true) &&
+         tc_panel_map(at_map(kMapAloT), f.Alo, p.m, npan, 64, 32, 2, true) &&
+         tc_panel_map(at_map(kMapAhiN), f.Ahi, p.m, npan, 32, 128, 1, false) &&
+         tc_panel_map(at_map(kMapAloN), f.Alo, p.m, npan, 32, 128, 1, false) &&
+         tc_map2d(at_map(kMapXhiM), f.XTh, p.m, d, f.ldk, 32, np, false) &&
+         tc_map2d(at_map(kMapXloM), f.XTl, p.m, d, f.ldk, 32, np, false) &&
+         tc_map2d(at_map(kMapXhiN), f.XTh, p.n, d, f.ldk, 32, np, false) &&
+         tc_map2d(at_map(kMapXloN), f.XTl, p.n, d, f.ldk, 32, np, false);
 }
 
 bool valid_problem(const rqlp_problem& p) {
@@ -401,21 +570,43 @@ size_t layout(rqlp_batch_s* b, int count, const rqlp_problem* probs, Arena& ar, 
   std::vector<int> ord = bucket_order(count, probs, b->cnt);
   std::vector<rqlp_problem> pr;
   std::vector<Bufs> bf;
+  const bool tc = b->opts.precision == RQLP_PREC_BF16X3;
+  int* flags = nullptr;
+  char* maps = nullptr;
+  if (tc) {
+    flags = ar.take<int>(count);
+    maps = ar.take<char>((size_t)count * kTcMaps * kTcMapBytes);
+  }
+  b->flags = flags;
+  b->maps_d = maps;
+  b->info0 = d_info;
+  b->maps_h.clear();
   b->dmax = 0;
   for (int bk = 0; bk < kBuckets; ++bk)
     for (int t = 0; t < 3; ++t) b->sums[bk][t] = 0;
   for (int i : ord) {
     const int d = probs[i].k + probs[i].p, bk = bucket_of(d);
     pr.push_back(probs[i]);
-    bf.push_back(take_bufs(ar, probs[i]));
+    bf.push_back(take_bufs(ar, probs[i], tc));
+    if (tc) {
+      const size_t pos = bf.size() - 1;
+      bf.back().flag = ar.dry ? nullptr : flags + pos;
+      bf.back().maps = ar.dry ? nullptr : maps + pos * kTcMaps * kTcMapBytes;
+    }
     b->dmax = std::max(b->dmax, d);
     b->sums[bk][0] += probs[i].m;
     b->sums[bk][1] += probs[i].n;
     b->sums[bk][2] += d;
   }
+  if (tc && !ar.dry) {
+    b->maps_h.assign((size_t)count * kTcMaps * kTcMapBytes, 0);
+    for (size_t i = 0; i < bf.size(); ++i)
+      if (!encode_maps(bf[i], pr[i], b->maps_h.data() + i * kTcMaps * kTcMapBytes)) b->maps_h.clear();
+  }
   b->stages.clear();
   b->gemms.clear();
-  Builder bd{b, pr, bf, ord, d_info, d_diag, sg};
+  b->tcs.clear();
+  Builder bd{b, pr, bf, ord, d_info, d_diag, sg, tc};
   bd.build();
   char* plan = ar.take<char>(sg.h.size() + 256);
   b->dev = ar.dry ? nullptr : plan;
@@ -453,6 +644,17 @@ cudaError_t run_stages(const rqlp_batch_s* b, cudaStream_t st) {
       case Stage::kTranspose: CK(transpose_batched(at<SmallJob>(b, s.jobs_off), b->count, st)); break;
       case Stage::kWriteL: CK(write_L_batched(at<SmallJob>(b, s.jobs_off), b->count, st)); break;
       case Stage::kFinish: CK(finish_diag_batched(at<SmallJob>(b, s.jobs_off), b->count, st)); break;
+      case Stage::kSplit:
+        CK(split_grouped(at<SplitJob>(b, s.jobs_off), at<int>(b, s.start_off), b->count, s.total, st));
+        break;
+      case Stage::kTc: {
+        const TcStage& t = b->tcs[s.gemm];
+        CK(cudaMemsetAsync(b->flags, 0, sizeof(int) * b->count, st));
+        CK(prep_grouped(at<PrepJob>(b, t.prep_off), at<int>(b, t.prep_start_off), b->count, t.prep_total, st));
+        CK(tc_grouped_pass(t.transA, at<TcGJob>(b, t.jobs_off), at<int2>(b, t.units_off), at<int>(b, t.cta_off),
+                           t.G, t.npad_max, b->info0, st));
+        break;
+      }
     }
   }
   return cudaSuccess;
@@ -474,7 +676,8 @@ rqlp_opts resolve_opts(const rqlp_opts* o) {
 
 bool valid_batch(int count, const rqlp_problem* probs, int q, const rqlp_opts& o) {
   if (count <= 0 || probs == nullptr || q < 0 || q > 64) return false;
-  if (o.precision != RQLP_PREC_FP32 || (o.small_fp64 != 0 && o.small_fp64 != 1)) return false;
+  if ((o.precision != RQLP_PREC_FP32 && o.precision != RQLP_PREC_BF16X3) || (o.small_fp64 != 0 && o.small_fp64 != 1))
+    return false;
   for (int i = 0; i < 6; ++i)
     if (o.reserved[i] != 0) return false;
   for (int i = 0; i < count; ++i)
@@ -507,7 +710,7 @@ rqlp_status rqlp_batch_create(int count, const rqlp_problem* probs, int q, void*
   if (out == nullptr) return RQLP_ERR_ARG;
   *out = nullptr;
   const rqlp_opts o = resolve_opts(opts);
-  if (o.precision != RQLP_PREC_FP32 && o.precision == RQLP_PREC_BF16X3) return RQLP_ERR_UNSUPPORTED;
+  if (o.precision == RQLP_PREC_BF16X3 && !tc_supported(nullptr, 0, nullptr, 0)) return RQLP_ERR_UNSUPPORTED;
   if (!valid_batch(count, probs, q, o) || d_info == nullptr) return RQLP_ERR_ARG;
   if (!chol_batched_fits(RQLP_BATCH_MAX_D, o.small_fp64 != 0)) return RQLP_ERR_UNSUPPORTED;
   const size_t need = rqlp_batch_workspace_bytes(count, probs, q, &o);
@@ -533,8 +736,17 @@ rqlp_status rqlp_batch_create(int count, const rqlp_problem* probs, int q, void*
         for (int bk = 0; bk < kBuckets; ++bk) b->cfg[s][bk] = it->second[s * kBuckets + bk];
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const bool tc = o.precision == RQLP_PREC_BF16X3;
+  if (tc && b->maps_h.empty()) {   // a tensor map was rejected
+    delete b;
+    return RQLP_ERR_UNSUPPORTED;
+  }
   if (gemm_grouped_prepare() != cudaSuccess ||
       chol_inv_batched(nullptr, 0, 0, o.small_fp64 != 0, st) != cudaSuccess ||
+      (tc && (tc_grouped_pass(true, nullptr, nullptr, nullptr, 0, 16, nullptr, st) != cudaSuccess ||
+              tc_grouped_pass(false, nullptr, nullptr, nullptr, 0, 16, nullptr, st) != cudaSuccess ||
+              cudaMemcpyAsync(b->maps_d, b->maps_h.data(), b->maps_h.size(), cudaMemcpyHostToDevice, st) !=
+                  cudaSuccess)) ||
       cudaMemcpyAsync(b->dev, sg.h.data(), sg.h.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess ||
       cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {

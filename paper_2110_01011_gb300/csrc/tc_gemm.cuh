@@ -48,4 +48,55 @@ class TcEngine {
   bool profiled_ = false;
 };
 
+// ---------------------------------------------------------------- grouped passes (batched form)
+// One problem's pass in a grouped launch: out (M x d) = op(A) X with the
+// problem's tensor maps (CUtensorMap, in device memory): A_hi, A_lo over the
+// panel layout (box {64, 32, 2} for op(A) = A^T, {32, 128, 1} for A) and
+// X_hi^T, X_lo^T (box {32, npad}).
+struct TcGJob {
+  const void* mAhi;
+  const void* mAlo;
+  const void* mXhi;
+  const void* mXlo;
+  float* out;
+  long long ldo;
+  int M, d, npad, kblocks, vec_out;
+  uint32_t idesc;
+  const int* xlo_nonzero;   // raised by prep_grouped when X has a low part
+};
+struct SplitJob {           // A (m x n) -> panels of A_hi, A_lo; sumsq += ||A||_F^2
+  const float* A;
+  long long lda, m, n, npan;
+  void* hi;
+  void* lo;
+  double* sumsq;
+  int vec;                  // A 16-byte aligned with lda % 4 == 0
+};
+struct PrepJob {            // X (K x d) -> X_hi^T, X_lo^T (d x ldk)
+  const float* X;
+  long long ldx, K;
+  int d;
+  void* th;
+  void* tl;
+  long long ldk;
+  int* flag;
+};
+constexpr size_t kTcMapBytes = 128;   // sizeof(CUtensorMap)
+int tc_split_blocks(long long m, long long n);
+int tc_prep_blocks(long long K, int d);
+// start: count + 1 block prefix sums (tc_split_blocks / tc_prep_blocks).
+cudaError_t split_grouped(const SplitJob* jobs, const int* start, int count, int total_blocks, cudaStream_t st);
+cudaError_t prep_grouped(const PrepJob* jobs, const int* start, int count, int total_blocks, cudaStream_t st);
+// units: (job, 128-row tile) pairs; CTA c takes units cta_start[c] .. cta_start[c + 1] - 1.
+// G = 0 only configures the kernel (call before capturing).
+cudaError_t tc_grouped_pass(bool transA, const TcGJob* jobs, const int2* units, const int* cta_start, int G,
+                            int npad_max, int* info, cudaStream_t st);
+// Host encoders of the tensor maps above (false when the encoder is missing
+// or rejects the arguments).
+bool tc_panel_map(void* map, const void* base, long long m, long long panels, int bi, int bo, int bp, bool sw128);
+bool tc_map2d(void* map, const void* base, long long inner, long long outer, long long pitch, int bi, int bo,
+              bool sw128);
+int tc_npad(int d);
+uint32_t tc_idesc(int npad, bool a_mn_major);   // tcgen05.mma kind::f16, M = 128, BF16 in, FP32 accumulate
+
 }  // namespace rqlp

@@ -1,0 +1,389 @@
+// Grouped tensor-core passes for the batched form (BF16x3): the passes over
+// every problem's A of one step of the chain (Y = A^T X or Z = A X) in one
+// launch.
+//
+// Per problem the batch plan holds A's BF16 halves in the 64-column panel
+// layout of the single-problem engine (written once by split_grouped_kernel),
+// the halves of the pass's X operand (X_hi^T, X_lo^T, K-major, written before
+// every pass by prep_grouped_kernel) and eight tensor maps in device memory
+// (A for both orientations, X for K = m and K = n). A work unit is one
+// 128-row tile of one problem's output over that problem's whole K; the host
+// balances the units over the CTAs (longest first, onto the least loaded
+// CTA), so no tile is split and no CTA waits for another. Inside a CTA the
+// pipeline is the single-problem pass kernel's: one TMA warp, one MMA warp
+// (tcgen05.mma, M = 128, N = the problem's round16(d), FP32 accumulators in
+// two TMEM buffers, chains cut every K = 4096), four epilogue warps. Every
+// wait is bounded.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "tc_gemm.cuh"
+#include "tc_ptx.cuh"
+
+namespace rqlp {
+namespace {
+
+using bf16 = __nv_bfloat16;
+
+constexpr int BM = 128;
+constexpr int BK = 32;                            // K per stage: 64-byte rows, 64B swizzle (K-major)
+constexpr uint32_t kABytes = BM * BK * 2;         // one BF16 part of an A tile (8 KB)
+constexpr int kThreads = 192;
+constexpr int kMaxStages = 8;
+constexpr int kChunkKB = 4096 / BK;               // k-blocks per accumulation chain
+constexpr long long kWaitLimit = 4000000000LL;    // cycles (~2 s)
+
+__device__ void post_timeout(int* info) {
+  if (info != nullptr && atomicCAS(info, 0, RQLP_ERR_TIMEOUT) == 0) info[1] = 0;
+}
+
+template <bool MN_A>
+__global__ void __launch_bounds__(kThreads, 1)
+tc_grouped_kernel(const TcGJob* __restrict__ jobs, const int2* __restrict__ units, const int* __restrict__ cta_start,
+                  int stages, uint32_t stage_bytes, uint32_t xslot, int npad_max, uint32_t tmem_cols, int* info) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int S = stages;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)S * stage_bytes);
+  uint64_t* empty = full + S;
+  uint64_t* accf = empty + S;
+  uint64_t* acce = accf + 2;
+  uint64_t* done = acce + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  int* epi_ok = reinterpret_cast<int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ub = cta_start[blockIdx.x], ue = cta_start[blockIdx.x + 1];
+  if (ub >= ue) return;   // no units (uniform over the CTA)
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&accf[b], 1);
+      tc::mbar_init(&acce[b], 4 * 32);
+    }
+    tc::mbar_init(done, 1);
+    tc::fence_barrier_init();
+  }
+  if (warp == 5) {
+    tc::tmem_alloc(tmem_slot, tmem_cols);
+    tc::tmem_relinquish();
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 4 && lane == 0) {
+    // ------------------------------------------------ TMA producer
+    long long issued = 0;
+    bool ok = true;
+    for (int ui = ub; ui < ue && ok; ++ui) {
+      const int2 un = units[ui];
+      const TcGJob& j = jobs[un.x];
+      const int t = un.y;
+      const CUtensorMap* mah = static_cast<const CUtensorMap*>(j.mAhi);
+      const CUtensorMap* mal = static_cast<const CUtensorMap*>(j.mAlo);
+      const CUtensorMap* mxh = static_cast<const CUtensorMap*>(j.mXhi);
+      const CUtensorMap* mxl = static_cast<const CUtensorMap*>(j.mXlo);
+      const int nx = (*j.xlo_nonzero) ? 2 : 1;
+      const uint32_t xb = (uint32_t)j.npad * BK * 2;
+      for (int kb = 0; kb < j.kblocks; ++kb, ++issued) {
+        const int stage = (int)(issued % S);
+        const uint32_t par = (uint32_t)((issued / S) & 1);
+        if (!tc::mbar_wait(&empty[stage], par ^ 1u, kWaitLimit)) { ok = false; break; }
+        unsigned char* base = smem + (size_t)stage * stage_bytes;
+        tc::mbar_expect_tx(&full[stage], 2 * kABytes + (uint32_t)nx * xb);
+        if (MN_A) {   // 32 rows (K) of panels 2t and 2t + 1 (M)
+          tc::tma_load_3d(base, mah, &full[stage], 0, kb * BK, 2 * t);
+          tc::tma_load_3d(base + kABytes, mal, &full[stage], 0, kb * BK, 2 * t);
+        } else {      // 128 rows (M) x 32 columns (K) of panel kb / 2
+          const int kx = (kb & 1) * BK, kp = kb >> 1;
+          tc::tma_load_3d(base, mah, &full[stage], kx, t * BM, kp);
+          tc::tma_load_3d(base + kABytes, mal, &full[stage], kx, t * BM, kp);
+        }
+        tc::tma_load_2d(base + 2 * kABytes, mxh, &full[stage], kb * BK, 0);
+        if (nx == 2) tc::tma_load_2d(base + 2 * kABytes + xslot, mxl, &full[stage], kb * BK, 0);
+      }
+    }
+    if (!ok) post_timeout(info);
+    for (long long i = issued > S ? issued - S : 0; i < issued; ++i)
+      if (!tc::mbar_wait(&full[i % S], (uint32_t)((i / S) & 1), kWaitLimit)) post_timeout(info);
+  } else if (warp == 5 && lane == 0) {
+    // ------------------------------------------------ MMA issuer
+    long long consumed = 0;
+    int seg = 0;
+    bool ok = true;
+    for (int ui = ub; ui < ue && ok; ++ui) {
+      const TcGJob& j = jobs[units[ui].x];
+      const int nx = (*j.xlo_nonzero) ? 2 : 1;
+      for (int s0 = 0; s0 < j.kblocks && ok; s0 += kChunkKB) {
+        const int s1 = min(j.kblocks, s0 + kChunkKB);
+        const int ab = seg & 1;
+        if (!tc::mbar_wait(&acce[ab], (uint32_t)(((seg >> 1) & 1) ^ 1), kWaitLimit)) { ok = false; break; }
+        tc::tc_fence_after();
+        const uint32_t d_tmem = tmem_base + (uint32_t)(ab * npad_max);
+        for (int kb = s0; kb < s1; ++kb, ++consumed) {
+          const int stage = (int)(consumed % S);
+          if (!tc::mbar_wait(&full[stage], (uint32_t)((consumed / S) & 1), kWaitLimit)) { ok = false; break; }
+          tc::tc_fence_after();
+          const uint32_t base = tc::smem_u32(smem + (size_t)stage * stage_bytes);
+          const uint32_t ahi = base, alo = base + kABytes, xhi = base + 2 * kABytes, xlo = xhi + xslot;
+#pragma unroll
+          for (int ks = 0; ks < BK / 16; ++ks) {
+            uint64_t dah, dal;
+            if (MN_A) {   // MN-major, 128B swizzle: 16 k-rows = two 1024-byte atoms
+              dah = tc::smem_desc(ahi + ks * 2048, kABytes / 2, 1024, tc::kSwizzle128);
+              dal = tc::smem_desc(alo + ks * 2048, kABytes / 2, 1024, tc::kSwizzle128);
+            } else {      // K-major, 64B swizzle: 16 k-columns = 32 bytes into the row
+              dah = tc::smem_desc(ahi + ks * 32, 16, 512, tc::kSwizzle64);
+              dal = tc::smem_desc(alo + ks * 32, 16, 512, tc::kSwizzle64);
+            }
+            const uint64_t dxh = tc::smem_desc(xhi + ks * 32, 16, 512, tc::kSwizzle64);
+            const uint64_t dxl = tc::smem_desc(xlo + ks * 32, 16, 512, tc::kSwizzle64);
+            const uint32_t acc = (kb > s0 || ks > 0) ? 1u : 0u;
+            tc::mma_bf16(d_tmem, dah, dxh, j.idesc, acc);
+            if (nx >= 2) tc::mma_bf16(d_tmem, dah, dxl, j.idesc, 1u);
+            tc::mma_bf16(d_tmem, dal, dxh, j.idesc, 1u);
+          }
+          tc::mma_commit(&empty[stage]);
+        }
+        if (!ok) break;
+        tc::mma_commit(&accf[ab]);
+        ++seg;
+      }
+    }
+    if (!ok) post_timeout(info);
+    tc::mma_commit(done);   // no MMA in flight at teardown
+    if (!tc::mbar_wait(done, 0, kWaitLimit)) post_timeout(info);
+  } else if (warp < 4) {
+    // ------------------------------------------------ epilogue: TMEM -> global
+    const int row = warp * 32 + lane;
+    int seg = 0;
+    bool ok = true;
+    for (int ui = ub; ui < ue && ok; ++ui) {
+      const int2 un = units[ui];
+      const TcGJob& j = jobs[un.x];
+      const long long gm = (long long)un.y * BM + row;
+      float* dst = j.out + gm * j.ldo;
+      const int ncols = gm < j.M ? j.d : 0;
+      const bool vec = j.vec_out != 0;   // out rows 16-byte aligned
+      for (int s0 = 0; s0 < j.kblocks; s0 += kChunkKB) {
+        const int ab = seg & 1;
+        // One thread waits; the verdict is shared so the four warps stay in step.
+        if (threadIdx.x == 0) *epi_ok = tc::mbar_wait(&accf[ab], (uint32_t)((seg >> 1) & 1), kWaitLimit) ? 1 : 0;
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+        if (*epi_ok == 0) {
+          if (threadIdx.x == 0) post_timeout(info);
+          ok = false;
+          break;
+        }
+        tc::tc_fence_after();
+        const uint32_t taddr = tmem_base + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ab * npad_max);
+        const bool first = s0 == 0;
+        for (int c0 = 0; c0 < j.npad; c0 += 16) {   // uniform over the warp (collective TMEM loads)
+          float v[16];
+          tc::tmem_ld16(taddr + (uint32_t)c0, v);
+          if (vec && c0 + 16 <= ncols) {
+            float4* d4 = reinterpret_cast<float4*>(dst + c0);
+            if (!first) {
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {
+                const float4 o = d4[q];
+                v[4 * q] += o.x; v[4 * q + 1] += o.y; v[4 * q + 2] += o.z; v[4 * q + 3] += o.w;
+              }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) d4[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+          } else {
+#pragma unroll
+            for (int i = 0; i < 16; ++i)
+              if (c0 + i < ncols) dst[c0 + i] = first ? v[i] : dst[c0 + i] + v[i];
+          }
+        }
+        tc::tc_fence_before();
+        tc::mbar_arrive(&acce[ab]);
+        ++seg;
+      }
+    }
+  }
+
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  if (warp == 5) tc::tmem_dealloc(tmem_base, tmem_cols);
+}
+
+// Block -> problem: the last b with start[b] <= blk (start has count + 1 entries).
+__device__ __forceinline__ int problem_of(const int* __restrict__ start, int count, int blk) {
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (start[mid] <= blk) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+constexpr int kSplitGroups = 2048;   // 8-element groups per block (256 threads x 8)
+
+// Every problem's A (m x n FP32) -> A_hi, A_lo in 64-column panels (columns
+// n..64 npan - 1 zero) and ||A||_F^2 (added to the problem's scalar).
+__global__ void __launch_bounds__(256)
+split_grouped_kernel(const SplitJob* __restrict__ jobs, const int* __restrict__ start, int count) {
+  const int b = problem_of(start, count, blockIdx.x);
+  const SplitJob j = jobs[b];
+  const long long cpr = j.npan * 8, total = j.m * cpr;
+  const long long g0 = (long long)(blockIdx.x - start[b]) * kSplitGroups;
+  const bool vec = j.vec != 0;
+  bf16* hi = reinterpret_cast<bf16*>(j.hi);
+  bf16* lo = reinterpret_cast<bf16*>(j.lo);
+  float s = 0.f, comp = 0.f;
+  for (int it = 0; it < kSplitGroups / 256; ++it) {
+    const long long g = g0 + it * 256 + threadIdx.x;
+    if (g >= total) break;
+    const long long r = g / cpr, c0 = (g % cpr) * 8;
+    const float* src = j.A + r * j.lda + c0;
+    float x[8];
+    if (vec && c0 + 8 <= j.n) {
+      const float4 p = *reinterpret_cast<const float4*>(src);
+      const float4 q = *reinterpret_cast<const float4*>(src + 4);
+      x[0] = p.x; x[1] = p.y; x[2] = p.z; x[3] = p.w; x[4] = q.x; x[5] = q.y; x[6] = q.z; x[7] = q.w;
+    } else {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) x[i] = (c0 + i < j.n) ? src[i] : 0.f;
+    }
+    __align__(16) bf16 h[8];
+    __align__(16) bf16 l[8];
+    float ss = 0.f;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      h[i] = __float2bfloat16_rn(x[i]);
+      l[i] = __float2bfloat16_rn(x[i] - __bfloat162float(h[i]));
+      ss = fmaf(x[i], x[i], ss);
+    }
+    const long long o = ((c0 >> 6) * j.m + r) * 64 + (c0 & 63);
+    *reinterpret_cast<uint4*>(hi + o) = *reinterpret_cast<const uint4*>(h);
+    *reinterpret_cast<uint4*>(lo + o) = *reinterpret_cast<const uint4*>(l);
+    const float y = ss - comp, tt = s + y;
+    comp = (tt - s) - y;
+    s = tt;
+  }
+  __shared__ double red[8];
+  double v = (double)s - (double)comp;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0 && j.sumsq != nullptr) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += red[w];
+    atomicAdd(j.sumsq, t);
+  }
+}
+
+// Every problem's X (K x d FP32) -> X_hi^T, X_lo^T (d x ldk BF16, K-major);
+// the problem's flag is raised when the low part is nonzero. One block per
+// 32 x 32 tile: tiles of problem b are numbered from start[b], row tiles
+// fastest.
+__global__ void __launch_bounds__(256)
+prep_grouped_kernel(const PrepJob* __restrict__ jobs, const int* __restrict__ start, int count) {
+  __shared__ float tile[32][33];
+  const int b = problem_of(start, count, blockIdx.x);
+  const PrepJob j = jobs[b];
+  const int local = blockIdx.x - start[b];
+  const int rtiles = (int)((j.K + 31) / 32);   // rows past K are read as zeros by the TMA
+  const long long r0 = (long long)(local % rtiles) * 32;
+  const int c0 = (local / rtiles) * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int i = ty; i < 32; i += 8) {
+    const long long r = r0 + i;
+    const int c = c0 + tx;
+    tile[i][tx] = (r < j.K && c < j.d) ? j.X[r * j.ldx + c] : 0.f;
+  }
+  __syncthreads();
+  bool any = false;
+  bf16* th = reinterpret_cast<bf16*>(j.th);
+  bf16* tl = reinterpret_cast<bf16*>(j.tl);
+  for (int i = ty; i < 32; i += 8) {
+    const int c = c0 + i;
+    const long long r = r0 + tx;
+    if (c < j.d && r < j.K) {
+      const float x = tile[tx][i];
+      const bf16 h = __float2bfloat16_rn(x);
+      const bf16 l = __float2bfloat16_rn(x - __bfloat162float(h));
+      th[(long long)c * j.ldk + r] = h;
+      tl[(long long)c * j.ldk + r] = l;
+      any |= __bfloat162float(l) != 0.f;
+    }
+  }
+  if (__syncthreads_or(any) && threadIdx.x == 0 && *(volatile int*)j.flag == 0) atomicOr(j.flag, 1);
+}
+
+size_t smem_optin() {
+  static size_t v = 0;
+  if (v == 0) {
+    int dev = 0, x = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&x, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess && x > 0)
+      v = (size_t)x;
+    else
+      v = 227 * 1024;
+  }
+  return v;
+}
+
+template <bool MN_A>
+cudaError_t launch_grouped(const TcGJob* jobs, const int2* units, const int* cta_start, int G, int npad_max,
+                           int* info, cudaStream_t st) {
+  const uint32_t xslot = (uint32_t)npad_max * BK * 2;
+  const uint32_t stage_bytes = 2 * kABytes + 2 * xslot;
+  const size_t avail = smem_optin() - 1024 - 512;
+  const int S = std::max(1, std::min(kMaxStages, (int)(avail / stage_bytes)));
+  uint32_t tmem_cols = 32;
+  while (tmem_cols < 2u * (uint32_t)npad_max) tmem_cols <<= 1;
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(tc_grouped_kernel<MN_A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem_optin());
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  if (G <= 0) return cudaSuccess;   // configuration only
+  const size_t smem = (size_t)S * stage_bytes + 1024 + 512;
+  tc_grouped_kernel<MN_A><<<G, kThreads, smem, st>>>(jobs, units, cta_start, S, stage_bytes, xslot, npad_max,
+                                                     tmem_cols, info);
+  note_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int tc_split_blocks(long long m, long long n) { return (int)cdiv(m * cdiv(n, 64) * 8, kSplitGroups); }
+int tc_prep_blocks(long long K, int d) { return (int)(cdiv(K, 32) * cdiv(d, 32)); }
+
+cudaError_t split_grouped(const SplitJob* jobs, const int* start, int count, int total_blocks, cudaStream_t st) {
+  if (count <= 0 || total_blocks <= 0) return cudaSuccess;
+  split_grouped_kernel<<<total_blocks, 256, 0, st>>>(jobs, start, count);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t prep_grouped(const PrepJob* jobs, const int* start, int count, int total_blocks, cudaStream_t st) {
+  if (count <= 0 || total_blocks <= 0) return cudaSuccess;
+  prep_grouped_kernel<<<total_blocks, 256, 0, st>>>(jobs, start, count);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t tc_grouped_pass(bool transA, const TcGJob* jobs, const int2* units, const int* cta_start, int G,
+                            int npad_max, int* info, cudaStream_t st) {
+  return transA ? launch_grouped<true>(jobs, units, cta_start, G, npad_max, info, st)
+                : launch_grouped<false>(jobs, units, cta_start, G, npad_max, info, st);
+}
+
+}  // namespace rqlp

@@ -506,9 +506,11 @@ class Batch:
     """A batch plan over CUDA FP32 row-major matrices: As[i] (m_i x n_i),
     Omegas[i] (m_i x (k_i + p_i)), one q. Allocates the outputs, the
     per-problem info/diag rows and the workspace with torch; ``launch()``
-    replays the captured graph, ``run()`` launches the kernels one by one."""
+    replays the captured graph, ``run()`` launches the kernels one by one.
+    precision: PREC_FP32, or PREC_BF16X3 (the passes over A as grouped
+    tensor-core passes over BF16 halves)."""
 
-    def __init__(self, As, Omegas, ks, ps, q, small_fp64=False):
+    def __init__(self, As, Omegas, ks, ps, q, small_fp64=False, precision=PREC_FP32):
         import torch
         self.count = len(As)
         dev = As[0].device
@@ -527,7 +529,7 @@ class Batch:
             arr[i] = Problem(A.data_ptr(), m, n, A.stride(0), O.data_ptr(), O.stride(0), k, p, Q.data_ptr(),
                              Q.stride(0), L.data_ptr(), L.stride(0), P.data_ptr(), P.stride(0))
         self.probs = arr
-        self.opts = _opts(PREC_FP32, small_fp64)
+        self.opts = _opts(precision, small_fp64)
         nb = rqlp_batch_workspace_bytes(self.count, arr, q, self.opts)
         if nb == 0:
             raise RqlpError(1, "rqlp_batch_workspace_bytes")

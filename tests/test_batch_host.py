@@ -41,4 +41,17 @@ def test_invalid_batch_arguments():
     a = _arr([_prob(300, 200, 20, 5)])
     assert rqlp.rqlp_batch_workspace_bytes(0, a, 1) == 0
     assert rqlp.rqlp_batch_workspace_bytes(1, a, -1) == 0
-    assert rqlp.rqlp_batch_workspace_bytes(1, a, 1, rqlp._opts(rqlp.PREC_BF16X3)) == 0
+    assert rqlp.rqlp_batch_workspace_bytes(1, a, 1, rqlp._opts(7)) == 0          # unknown precision
+
+
+def test_split_form_workspace_holds_the_halves():
+    """The BF16x3 batch adds A's BF16 halves (64-column panels), the pass
+    operand's halves and the tensor maps to the FP32 batch's workspace."""
+    a = _arr([_prob(300, 200, 20, 5), _prob(500, 100, 40, 5)])
+    fp32 = rqlp.rqlp_batch_workspace_bytes(2, a, 1)
+    split = rqlp.rqlp_batch_workspace_bytes(2, a, 1, rqlp._opts(rqlp.PREC_BF16X3))
+    halves = 2 * 2 * (300 * 256 + 500 * 128)                 # A_hi + A_lo, BF16
+    xt = 2 * 2 * (25 * 304 + 45 * 504)                      # X_hi^T + X_lo^T, d x round8(max(m, n))
+    maps = 2 * 8 * 128
+    assert split - fp32 >= halves + xt + maps
+    assert split - fp32 <= halves + xt + maps + 64 * 1024     # + the grouped passes' plan tables

@@ -13,8 +13,11 @@ from paper_2110_01011_gb300 import inputs, rqlp
 
 pytestmark = pytest.mark.gpu
 
+# d = 160 and 161 sit on either side of the tensor-core pass's switch from
+# K = 64 to K = 32 per pipeline stage (three K = 64 stages fit up to d = 160).
 SHAPES = [(300, 200, 13), (129, 257, 16), (1000, 777, 25), (777, 1000, 37),
-          (2500, 1300, 210), (4100, 300, 64), (640, 512, 256), (97, 53, 1)]
+          (2500, 1300, 210), (4100, 300, 64), (640, 512, 256), (97, 53, 1),
+          (1500, 900, 160), (900, 1500, 161)]
 
 
 def _run(A, X, trans, prec):
