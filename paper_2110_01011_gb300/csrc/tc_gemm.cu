@@ -724,18 +724,6 @@ cudaError_t launch_pass(const CUtensorMap& ah, const CUtensorMap& al, const CUte
 
 }  // namespace
 
-bool tc_panel_map(void* map, const void* base, long long m, long long panels, int bi, int bo, int bp, bool sw128) {
-  return make_panel_map(static_cast<CUtensorMap*>(map), base, m, panels, bi, bo, bp,
-                        sw128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B);
-}
-bool tc_map2d(void* map, const void* base, long long inner, long long outer, long long pitch, int bi, int bo,
-              bool sw128) {
-  return make_map(static_cast<CUtensorMap*>(map), base, inner, outer, pitch, bi, bo,
-                  sw128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B);
-}
-int tc_npad(int d) { return npad_of(d); }
-uint32_t tc_idesc(int npad, bool a_mn_major) { return tc::idesc_bf16(BM, npad, a_mn_major, false); }
-
 bool tc_supported(const float* A, int64_t lda, const float* Omega, int64_t ldo) {
   (void)A; (void)lda; (void)Omega; (void)ldo;
   int dev = 0, major = 0, minor = 0;

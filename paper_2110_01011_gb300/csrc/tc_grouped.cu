@@ -18,6 +18,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "tc_gemm.cuh"
 #include "tc_ptx.cuh"
@@ -361,7 +362,58 @@ cudaError_t launch_grouped(const TcGJob* jobs, const int2* units, const int* cta
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- host: tensor maps
+using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeFn encoder() {
+  static EncodeFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeFn>(p);
+  });
+  return fn;
+}
+
+// BF16 tensor map of `rank` dims (innermost first), byte strides of dims 1.., box.
+bool encode(void* map, const void* base, int rank, const cuuint64_t* dims, const cuuint64_t* strides,
+            const cuuint32_t* box, bool sw128) {
+  EncodeFn fn = encoder();
+  if (fn == nullptr) return false;
+  cuuint32_t es[3] = {1, 1, 1};
+  return fn(static_cast<CUtensorMap*>(map), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)rank,
+            const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            sw128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 }  // namespace
+
+static_assert(sizeof(CUtensorMap) == kTcMapBytes, "tensor map size");
+
+bool tc_panel_map(void* map, const void* base, long long m, long long panels, int bi, int bo, int bp, bool sw128) {
+  const cuuint64_t dims[3] = {64, (cuuint64_t)m, (cuuint64_t)panels};
+  const cuuint64_t strides[2] = {128, (cuuint64_t)(m * 128)};
+  const cuuint32_t box[3] = {(cuuint32_t)bi, (cuuint32_t)bo, (cuuint32_t)bp};
+  return encode(map, base, 3, dims, strides, box, sw128);
+}
+
+bool tc_map2d(void* map, const void* base, long long inner, long long outer, long long pitch, int bi, int bo,
+              bool sw128) {
+  const cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
+  const cuuint64_t strides[1] = {(cuuint64_t)(pitch * 2)};
+  const cuuint32_t box[2] = {(cuuint32_t)bi, (cuuint32_t)bo};
+  return encode(map, base, 2, dims, strides, box, sw128);
+}
+
+int tc_npad(int d) { return (int)round_up(std::max(d, 16), 16); }
+uint32_t tc_idesc(int npad, bool a_mn_major) { return tc::idesc_bf16(BM, npad, a_mn_major, false); }
 
 int tc_split_blocks(long long m, long long n) { return (int)cdiv(m * cdiv(n, 64) * 8, kSplitGroups); }
 int tc_prep_blocks(long long K, int d) { return (int)(cdiv(K, 32) * cdiv(d, 32)); }
