@@ -420,18 +420,17 @@ def e2e_learned(a, ctx, A, Om, params, target, prec, steps, warmup):
     ws = torch.empty(nb + 256, dtype=torch.uint8, device=dev)
     out = (torch.empty(a.m, w, device=dev), torch.empty(w, w, device=dev), torch.empty(a.n, w, device=dev),
            torch.empty(2, dtype=torch.int32, device=dev), torch.empty(4, dtype=torch.float64, device=dev))
-    d_used = [w]
 
     def step():
         dA.copy_(hA, non_blocking=True)
         dO.copy_(hO, non_blocking=True)
         Q, L, P, info, diag, qp = rqlp.factor_learned(dA, a.k, dO, params, target, precision=prec, workspace=ws,
                                                       out=out)
-        d = a.k + qp[1]
-        d_used[0] = d
-        hQ[:, :d].copy_(Q, non_blocking=True)
-        hL[:d, :d].copy_(L, non_blocking=True)
-        hP[:, :d].copy_(P, non_blocking=True)
+        # The factors are the leading d columns of the k + 20 wide output
+        # buffers: one contiguous copy per buffer (the caller reads [:, :d]).
+        hQ.copy_(out[0], non_blocking=True)
+        hL.copy_(out[1], non_blocking=True)
+        hP.copy_(out[2], non_blocking=True)
         torch.cuda.current_stream().synchronize()
         return qp
 
@@ -443,9 +442,8 @@ def e2e_learned(a, ctx, A, Om, params, target, prec, steps, warmup):
         qp = step()
     ctx.barrier()
     dt = ctx.max_over_ranks((time.perf_counter() - t0) / steps)
-    d = d_used[0]
     h2d = 4 * (a.m * a.n + a.m * w)
-    d2h = 4 * (a.m * d + d * d + a.n * d)
+    d2h = 4 * (a.m * w + w * w + a.n * w)
     return {"value": ctx.world * (2 * qp[0] + 2) * a.m * a.n * 4 / dt / 1e9, "unit": "GB/s", "ms_per_step": dt * 1e3,
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "api": "rqlp_factor_learned + pinned copies"}
 
