@@ -110,7 +110,7 @@ def tail2(a):
     return float((sig[a.k:] ** 2).sum()) + 1e-12 * a.m
 
 
-class Judge:
+class Accuracy:
     """Accuracy of a factorisation from its P, evaluated directly in FP64:
     ||A - A P_j P_j^T||_F for the leading j = k columns (the excess rank-k
     error eps = that / (sum_{i>k} sigma_i^2)^(1/2) - 1) and for all d columns
@@ -518,7 +518,7 @@ def main():
     form = "learned" if params is not None else "fixed"
 
     compare = {}
-    judge = Judge(a, A)
+    acc = Accuracy(a, A)
     # The plain FP32 form with the fixed (2, 10): its time and the accuracy the
     # learned form is asked to match.
     target = None
@@ -528,7 +528,7 @@ def main():
         step32()
         ctx.barrier()
         ms32 = time_steps(ctx, step32, 3)
-        acc32 = judge(out32[2])
+        acc32 = acc(out32[2])
         compare.update({"fp32_fixed_qp": [2, 10] if form == "learned" else [a.q, a.p], "fp32_ms_per_step": ms32,
                         "fp32_rel_residual": acc32["rel_residual"], "fp32_excess_error": acc32["excess_error"]})
         target = min(max(acc32["excess_error"], 1e-3), 0.5)
@@ -571,7 +571,7 @@ def main():
     roof, sha = roofline(a, recs, d, prec, peaks, dev)
 
     compare.update({"form": ("learned_" if form == "learned" else "fixed_") + ("fp32" if prec == 0 else "bf16x3"),
-                    "qp": [q_used, p_used], **judge(out[2])})
+                    "qp": [q_used, p_used], **acc(out[2])})
     if target is not None:
         compare["requested_excess_error"] = target
     if "fp32_ms_per_step" in compare:
@@ -582,7 +582,7 @@ def main():
         s16()
         ctx.barrier()
         compare["bf16x3_fixed_ms_per_step"] = time_steps(ctx, s16, 3)
-        acc16 = judge(o16[2])
+        acc16 = acc(o16[2])
         compare["bf16x3_fixed_excess_error"] = acc16["excess_error"]
         compare["bf16x3_fixed_rel_residual"] = acc16["rel_residual"]
         del s16, o16
@@ -609,7 +609,7 @@ def main():
                "sample": f"FP64 oracle chain on the leading {S}x{S} block of the workload's A "
                          f"(q={q_used}, d={d}), {dt:.1f} s"}
 
-    del A, Om, judge
+    del A, Om, acc
     torch.cuda.empty_cache()
     batched = None if a.no_batched else batched_leg(a, ctx)
 

@@ -1,6 +1,6 @@
 """FP64 CPU oracle for Rand-QLP -- TEST INFRASTRUCTURE ONLY.
 
-Plain, slow, obviously correct numpy (float64) implementations that judge the
+Plain, slow, obviously correct numpy (float64) implementations that check the
 CUDA path: the factorisation chain (``rqlp_oracle``), a one-sided Jacobi SVD
 for brute-force pins (``jacobi_svd``), the bounds of Theorems 1-3
 (``bounds``) and the reference MLP used by the learned (q, p) predictor

@@ -1,6 +1,6 @@
 """FP64 CPU oracle for Rand-QLP (arXiv 2110.01011).
 
-TEST INFRASTRUCTURE ONLY. This module is the parity judge for the CUDA path;
+TEST INFRASTRUCTURE ONLY. This module is the parity reference for the CUDA path;
 only tests, the smoke check and the benchmark's CPU-baseline leg may import it.
 The product path never calls it and shares no code with it.
 
