@@ -253,6 +253,10 @@ def traffic_for(kernel, sha):
 
 
 class Ctx:
+    """Ranks of one job (one process per GPU; replicas, no data-path
+    collective): a barrier that also drains the device, and the maximum of a
+    per-rank time over the ranks."""
+
     def __init__(self, world, rank, dev):
         self.world, self.rank, self.dev = world, rank, dev
 
@@ -261,7 +265,8 @@ class Ctx:
         import torch.distributed as dist
         if self.world > 1:
             dist.barrier()
-        torch.cuda.synchronize()
+        if self.dev.type == "cuda":
+            torch.cuda.synchronize(self.dev)
 
     def max_over_ranks(self, x):
         import torch
