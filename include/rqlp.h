@@ -65,7 +65,13 @@ typedef struct {
   int precision;   /* rqlp_precision                                          */
   int small_fp64;  /* 1: d x d Cholesky factors in FP64 (slow on GB300);       */
                    /* 0: FP32 with an automatic diagonal shift on breakdown    */
-  int reserved[6]; /* must be zero                                            */
+  int test_stall;  /* fault-injection hook for tests, 0 in normal use: with    */
+                   /* the BF16X3 batched form, 1 makes CTA 0 of the batch's   */
+                   /* first grouped pass over A withhold its first stage's    */
+                   /* loads, so that its bounded waits run out (~2 s each)    */
+                   /* and the first problem's status row reports              */
+                   /* RQLP_ERR_TIMEOUT; must be 0 for every other entry point */
+  int reserved[5]; /* must be zero                                            */
 } rqlp_opts;
 
 /* d_info layout written by rqlp_factor (2 ints): [0] = rqlp_status of the

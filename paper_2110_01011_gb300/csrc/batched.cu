@@ -85,6 +85,7 @@ struct TcStage {
   size_t cta_off;         // int[kMaxTcCtas + 1]
   int G;
   int npad_max;
+  int stall;              // test hook: CTA 0 withholds its first stage (first pass only)
 };
 
 struct Stage {
@@ -299,6 +300,7 @@ struct Builder {
     ts.units_off = sg.put(flat.data(), flat.size());
     ts.cta_off = sg.put(cs.data(), cs.size());
     ts.G = G;
+    ts.stall = (b->opts.test_stall != 0 && b->tcs.empty()) ? 1 : 0;
     Stage s;
     s.kind = Stage::kTc;
     s.gemm = (int)b->tcs.size();
@@ -652,7 +654,7 @@ cudaError_t run_stages(const rqlp_batch_s* b, cudaStream_t st) {
         CK(cudaMemsetAsync(b->flags, 0, sizeof(int) * b->count, st));
         CK(prep_grouped(at<PrepJob>(b, t.prep_off), at<int>(b, t.prep_start_off), b->count, t.prep_total, st));
         CK(tc_grouped_pass(t.transA, at<TcGJob>(b, t.jobs_off), at<int2>(b, t.units_off), at<int>(b, t.cta_off),
-                           t.G, t.npad_max, b->info0, st));
+                           t.G, t.npad_max, b->info0, t.stall, st));
         break;
       }
     }
@@ -678,7 +680,8 @@ bool valid_batch(int count, const rqlp_problem* probs, int q, const rqlp_opts& o
   if (count <= 0 || probs == nullptr || q < 0 || q > 64) return false;
   if ((o.precision != RQLP_PREC_FP32 && o.precision != RQLP_PREC_BF16X3) || (o.small_fp64 != 0 && o.small_fp64 != 1))
     return false;
-  for (int i = 0; i < 6; ++i)
+  if (o.test_stall != 0 && (o.test_stall != 1 || o.precision != RQLP_PREC_BF16X3)) return false;
+  for (int i = 0; i < 5; ++i)
     if (o.reserved[i] != 0) return false;
   for (int i = 0; i < count; ++i)
     if (!valid_problem(probs[i])) return false;
@@ -743,8 +746,8 @@ rqlp_status rqlp_batch_create(int count, const rqlp_problem* probs, int q, void*
   }
   if (gemm_grouped_prepare() != cudaSuccess ||
       chol_inv_batched(nullptr, 0, 0, o.small_fp64 != 0, st) != cudaSuccess ||
-      (tc && (tc_grouped_pass(true, nullptr, nullptr, nullptr, 0, 16, nullptr, st) != cudaSuccess ||
-              tc_grouped_pass(false, nullptr, nullptr, nullptr, 0, 16, nullptr, st) != cudaSuccess ||
+      (tc && (tc_grouped_pass(true, nullptr, nullptr, nullptr, 0, 16, nullptr, 0, st) != cudaSuccess ||
+              tc_grouped_pass(false, nullptr, nullptr, nullptr, 0, 16, nullptr, 0, st) != cudaSuccess ||
               cudaMemcpyAsync(b->maps_d, b->maps_h.data(), b->maps_h.size(), cudaMemcpyHostToDevice, st) !=
                   cudaSuccess)) ||
       cudaMemcpyAsync(b->dev, sg.h.data(), sg.h.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||

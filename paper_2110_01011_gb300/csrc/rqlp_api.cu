@@ -318,7 +318,8 @@ rqlp_opts resolve(const rqlp_opts* o) {
 bool valid_opts(const rqlp_opts& o) {
   if (o.precision != RQLP_PREC_FP32 && o.precision != RQLP_PREC_BF16X3) return false;
   if (o.small_fp64 != 0 && o.small_fp64 != 1) return false;
-  for (int i = 0; i < 6; ++i)
+  if (o.test_stall != 0) return false;   // the hook is the batched form's only
+  for (int i = 0; i < 5; ++i)
     if (o.reserved[i] != 0) return false;
   return true;
 }

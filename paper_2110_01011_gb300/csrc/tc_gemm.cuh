@@ -89,8 +89,10 @@ cudaError_t split_grouped(const SplitJob* jobs, const int* start, int count, int
 cudaError_t prep_grouped(const PrepJob* jobs, const int* start, int count, int total_blocks, cudaStream_t st);
 // units: (job, 128-row tile) pairs; CTA c takes units cta_start[c] .. cta_start[c + 1] - 1.
 // G = 0 only configures the kernel (call before capturing).
+// stall != 0 (fault-injection tests): CTA 0 withholds its first stage's loads,
+// its bounded waits run out and `info` receives RQLP_ERR_TIMEOUT.
 cudaError_t tc_grouped_pass(bool transA, const TcGJob* jobs, const int2* units, const int* cta_start, int G,
-                            int npad_max, int* info, cudaStream_t st);
+                            int npad_max, int* info, int stall, cudaStream_t st);
 // Host encoders of the tensor maps above (false when the encoder is missing
 // or rejects the arguments).
 bool tc_panel_map(void* map, const void* base, long long m, long long panels, int bi, int bo, int bp, bool sw128);

@@ -43,7 +43,8 @@ __device__ void post_timeout(int* info) {
 template <bool MN_A>
 __global__ void __launch_bounds__(kThreads, 1)
 tc_grouped_kernel(const TcGJob* __restrict__ jobs, const int2* __restrict__ units, const int* __restrict__ cta_start,
-                  int stages, uint32_t stage_bytes, uint32_t xslot, int npad_max, uint32_t tmem_cols, int* info) {
+                  int stages, uint32_t stage_bytes, uint32_t xslot, int npad_max, uint32_t tmem_cols, int* info,
+                  int stall) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -99,6 +100,9 @@ tc_grouped_kernel(const TcGJob* __restrict__ jobs, const int2* __restrict__ unit
         const int stage = (int)(issued % S);
         const uint32_t par = (uint32_t)((issued / S) & 1);
         if (!tc::mbar_wait(&empty[stage], par ^ 1u, kWaitLimit)) { ok = false; break; }
+        // Test hook: CTA 0 withholds its first stage; the MMA warp's wait on
+        // it, this thread's later waits and the epilogue's run out and report.
+        if (stall != 0 && blockIdx.x == 0 && issued == 0) continue;
         unsigned char* base = smem + (size_t)stage * stage_bytes;
         tc::mbar_expect_tx(&full[stage], 2 * kABytes + (uint32_t)nx * xb);
         if (MN_A) {   // 32 rows (K) of panels 2t and 2t + 1 (M)
@@ -340,7 +344,7 @@ size_t smem_optin() {
 
 template <bool MN_A>
 cudaError_t launch_grouped(const TcGJob* jobs, const int2* units, const int* cta_start, int G, int npad_max,
-                           int* info, cudaStream_t st) {
+                           int* info, int stall, cudaStream_t st) {
   const uint32_t xslot = (uint32_t)npad_max * BK * 2;
   const uint32_t stage_bytes = 2 * kABytes + 2 * xslot;
   const size_t avail = smem_optin() - 1024 - 512;
@@ -357,7 +361,7 @@ cudaError_t launch_grouped(const TcGJob* jobs, const int2* units, const int* cta
   if (G <= 0) return cudaSuccess;   // configuration only
   const size_t smem = (size_t)S * stage_bytes + 1024 + 512;
   tc_grouped_kernel<MN_A><<<G, kThreads, smem, st>>>(jobs, units, cta_start, S, stage_bytes, xslot, npad_max,
-                                                     tmem_cols, info);
+                                                     tmem_cols, info, stall);
   note_launch();
   return cudaGetLastError();
 }
@@ -433,9 +437,9 @@ cudaError_t prep_grouped(const PrepJob* jobs, const int* start, int count, int t
 }
 
 cudaError_t tc_grouped_pass(bool transA, const TcGJob* jobs, const int2* units, const int* cta_start, int G,
-                            int npad_max, int* info, cudaStream_t st) {
-  return transA ? launch_grouped<true>(jobs, units, cta_start, G, npad_max, info, st)
-                : launch_grouped<false>(jobs, units, cta_start, G, npad_max, info, st);
+                            int npad_max, int* info, int stall, cudaStream_t st) {
+  return transA ? launch_grouped<true>(jobs, units, cta_start, G, npad_max, info, stall, st)
+                : launch_grouped<false>(jobs, units, cta_start, G, npad_max, info, stall, st);
 }
 
 }  // namespace rqlp

@@ -45,7 +45,8 @@ EXPORTED = ["rqlp_default_opts", "rqlp_workspace_bytes", "rqlp_factor", "rqlp_ho
 
 class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("small_fp64", ctypes.c_int),
-                ("reserved", ctypes.c_int * 6)]
+                ("test_stall", ctypes.c_int),
+                ("reserved", ctypes.c_int * 5)]
 
 
 class Problem(ctypes.Structure):
@@ -510,7 +511,7 @@ class Batch:
     precision: PREC_FP32, or PREC_BF16X3 (the passes over A as grouped
     tensor-core passes over BF16 halves)."""
 
-    def __init__(self, As, Omegas, ks, ps, q, small_fp64=False, precision=PREC_FP32):
+    def __init__(self, As, Omegas, ks, ps, q, small_fp64=False, precision=PREC_FP32, test_stall=False):
         import torch
         self.count = len(As)
         dev = As[0].device
@@ -530,6 +531,7 @@ class Batch:
                              Q.stride(0), L.data_ptr(), L.stride(0), P.data_ptr(), P.stride(0))
         self.probs = arr
         self.opts = _opts(precision, small_fp64)
+        self.opts.test_stall = 1 if test_stall else 0
         nb = rqlp_batch_workspace_bytes(self.count, arr, q, self.opts)
         if nb == 0:
             raise RqlpError(1, "rqlp_batch_workspace_bytes")

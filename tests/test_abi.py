@@ -42,7 +42,7 @@ def test_host_only_calls(lib):
     assert "breakdown" in rqlp.rqlp_status_string(3).lower()
     o = rqlp.rqlp_default_opts()
     assert o.precision == rqlp.PREC_FP32 and o.small_fp64 == 0
-    assert list(o.reserved) == [0] * 6
+    assert o.test_stall == 0 and list(o.reserved) == [0] * 5
 
 
 @pytest.mark.parametrize("m,n,k,p,q", [(0, 10, 1, 0, 0), (10, 10, 0, 1, 0), (10, 10, 8, 3, 0),
@@ -62,6 +62,9 @@ def test_workspace_grows_with_size(lib):
 def test_bad_opts_rejected(lib):
     o = rqlp.rqlp_default_opts()
     o.reserved[0] = 1
+    assert rqlp.rqlp_workspace_bytes(100, 100, 5, 5, 0, o) == 0
+    o = rqlp.rqlp_default_opts()
+    o.test_stall = 1                 # the fault-injection hook belongs to the batched form only
     assert rqlp.rqlp_workspace_bytes(100, 100, 5, 5, 0, o) == 0
     o = rqlp.rqlp_default_opts()
     o.precision = 7

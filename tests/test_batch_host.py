@@ -55,3 +55,15 @@ def test_split_form_workspace_holds_the_halves():
     maps = 2 * 8 * 128
     assert split - fp32 >= halves + xt + maps
     assert split - fp32 <= halves + xt + maps + 64 * 1024     # + the grouped passes' plan tables
+
+
+def test_stall_hook_only_for_split_batches():
+    a = _arr([_prob(300, 200, 20, 5)])
+    o = rqlp._opts(rqlp.PREC_BF16X3)
+    o.test_stall = 1
+    assert rqlp.rqlp_batch_workspace_bytes(1, a, 1, o) > 0
+    o.test_stall = 2
+    assert rqlp.rqlp_batch_workspace_bytes(1, a, 1, o) == 0
+    o = rqlp._opts(rqlp.PREC_FP32)
+    o.test_stall = 1
+    assert rqlp.rqlp_batch_workspace_bytes(1, a, 1, o) == 0

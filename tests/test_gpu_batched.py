@@ -32,14 +32,14 @@ def _problems(count, seed, q_rate=3.0, dmax=69, sizes=((40, 500), (40, 400))):
 PRECS = [0, 1]   # rqlp.PREC_FP32, rqlp.PREC_BF16X3
 
 
-def _batch(probs, q, small_fp64=False, precision=0):
+def _batch(probs, q, small_fp64=False, precision=0, test_stall=False):
     import torch
 
     from paper_2110_01011_gb300 import rqlp
     As = [torch.from_numpy(np.ascontiguousarray(A)).cuda() for A, _, _, _ in probs]
     Os = [torch.from_numpy(np.ascontiguousarray(O)).cuda() for _, O, _, _ in probs]
     b = rqlp.Batch(As, Os, [k for _, _, k, _ in probs], [p for _, _, _, p in probs], q, small_fp64=small_fp64,
-                   precision=precision)
+                   precision=precision, test_stall=test_stall)
     return b
 
 
@@ -158,4 +158,23 @@ def test_split_form_large_problems():
     b = _batch(g, 1, precision=1)
     b.launch()
     _check_all(b, g, 1, 1)
+    b.close()
+
+
+def test_withheld_stage_times_out_and_the_context_survives():
+    """Fault injection without a GPU fault: CTA 0 of the first grouped pass
+    withholds its first stage (the test hook), its bounded waits run out
+    (~2 s each), the first problem's status row reports RQLP_ERR_TIMEOUT, the
+    kernel frees what it holds and returns; a normal batch afterwards is
+    correct."""
+    import torch
+    probs = _problems(3, seed=41)
+    b = _batch(probs, 1, precision=1, test_stall=True)
+    b.launch()
+    torch.cuda.synchronize()
+    assert int(b.info[0, 0].item()) == 5          # RQLP_ERR_TIMEOUT
+    b.close()
+    b = _batch(probs, 1, precision=1)
+    b.launch()
+    _check_all(b, probs, 1, 1)
     b.close()
