@@ -637,6 +637,7 @@ cudaError_t run_gemm(const rqlp_batch_s* b, const GemmStage& g, cudaStream_t st,
 }
 
 cudaError_t run_stages(const rqlp_batch_s* b, cudaStream_t st) {
+  Range r("rqlp: batch stages");
   const bool fp64 = b->opts.small_fp64 != 0;
   for (const Stage& s : b->stages) {
     switch (s.kind) {

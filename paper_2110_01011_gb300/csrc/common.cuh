@@ -16,6 +16,15 @@
 
 namespace rqlp {
 
+// NVTX range over the enqueueing of one step of the chain (host side; a
+// no-op unless a profiler attaches).
+struct Range {
+  explicit Range(const char* name);
+  ~Range();
+  Range(const Range&) = delete;
+  Range& operator=(const Range&) = delete;
+};
+
 // Round x up to a multiple of a (a > 0); ceil(x / a).
 __host__ __device__ inline int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 __host__ __device__ inline int64_t cdiv(int64_t x, int64_t a) { return (x + a - 1) / a; }

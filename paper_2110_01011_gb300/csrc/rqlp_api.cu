@@ -236,8 +236,11 @@ class Plan {
   cudaError_t run(const float* A, const float* Om, const Out& out, int* info, double* diag, cudaStream_t st) {
     ops_.bind(st, info);
     CK(ops_.init());
-    // Sketch Y = A^T Omega (Algorithm 1 step 3); ||A||_F^2 rides along.
-    CK(ops_.pass(true, A, d_.m, d_.n, d_.lda, Om, d_.ldo, Y_, ops_.ld(), &ops_.scal[0]));
+    {
+      Range r("rqlp: sketch Y = A^T Omega");
+      // Sketch Y = A^T Omega (Algorithm 1 step 3); ||A||_F^2 rides along.
+      CK(ops_.pass(true, A, d_.m, d_.n, d_.lda, Om, d_.ldo, Y_, ops_.ld(), &ops_.scal[0]));
+    }
     return chain(A, d_.q, out, info, diag, st);
   }
 
@@ -245,6 +248,7 @@ class Plan {
   // all on the device. params == nullptr stops after the features.
   cudaError_t probe(const float* A, const float* Om, double target, const float* params, int* info,
                     cudaStream_t st) {
+    Range r("rqlp: probe sketch, features, (q, p)");
     ops_.bind(st, info);
     CK(ops_.init());
     ops_.set_d(d_.d);
@@ -276,9 +280,13 @@ class Plan {
                     bool have_r0 = false) {
     const int64_t m = d_.m, n = d_.n, lda = d_.lda, ld = ops_.ld();
     const int d = ops_.d();
-    if (q == 0) CK(ops_.orth_final(Y_, ld, n, Pt_, ld, T1_, nullptr, 0, have_r0));
-    else CK(ops_.orth_inter(Y_, ld, n, Pt_, ld, have_r0));
+    {
+      Range r("rqlp: qf(Y)");
+      if (q == 0) CK(ops_.orth_final(Y_, ld, n, Pt_, ld, T1_, nullptr, 0, have_r0));
+      else CK(ops_.orth_inter(Y_, ld, n, Pt_, ld, have_r0));
+    }
     for (int i = 1; i <= q; ++i) {
+      Range r("rqlp: power pass");
       CK(ops_.pass(false, A, m, n, lda, Pt_, ld, Z_, ld, nullptr));   // Z = A P~
       CK(ops_.orth_inter(Z_, ld, m, T1_, ld));                        // Z = qf(Z), one pass
       CK(ops_.pass(true, A, m, n, lda, T1_, ld, Y_, ld, nullptr));    // Y = A^T Z
@@ -286,6 +294,7 @@ class Plan {
       else CK(ops_.orth_inter(Y_, ld, n, Pt_, ld));
     }
     // (Q, R) = qr(A P~)  (Algorithm 1 step 4)
+    Range r("rqlp: qr(A P~), qr(R^T), L, P");
     CK(ops_.pass(false, A, m, n, lda, Pt_, ld, Z_, ld, nullptr));
     CK(ops_.orth_final(Z_, ld, m, out.Q, out.ldq, T1_, Rb_, 1));
     // (P^, R^) = qr(R^T), L = R^^T  (step 5 applied to the d x d factor)

@@ -1,5 +1,8 @@
-// Host-side runtime services of the library: the kernel-launch counter and
-// the optional per-pass event timing used by the benchmark.
+// Host-side runtime services of the library: the kernel-launch counter, the
+// optional per-pass event timing used by the benchmark and NVTX ranges over
+// the steps of the chain.
+#include <nvtx3/nvToolsExt.h>
+
 #include <atomic>
 #include <mutex>
 #include <vector>
@@ -7,6 +10,10 @@
 #include "common.cuh"
 
 namespace rqlp {
+
+Range::Range(const char* name) { nvtxRangePushA(name); }
+Range::~Range() { nvtxRangePop(); }
+
 namespace {
 
 std::atomic<unsigned long long> g_launches{0};
