@@ -199,10 +199,12 @@ def init_params(seed, F=rqlp.MLP_FEATURES, H=rqlp.MLP_HIDDEN):
     return np.concatenate([W1.ravel(), np.zeros(H), W2.ravel(), np.zeros(H), W3.ravel(), np.zeros(8)])
 
 
-def train(X, yq, yp, steps=3000, lr=3e-3, seed=11, device="cuda", val=None, every=50):
+def train(X, yq, yp, steps=3000, lr=3e-3, seed=11, device="cuda", val=None, every=50, init=None):
     """Full-batch Adam with the library's kernels. With val = (Xv, yqv, ypv),
     the parameters of the lowest validation loss (checked every ``every``
-    steps) are returned. Returns (params, curve of (step, loss, val_loss))."""
+    steps) are returned. init: parameters to start from (on standardised
+    features, see unfold_standardisation); Adam's moments start at zero.
+    Returns (params, curve of (step, loss, val_loss))."""
     import torch
     dev = torch.device(device)
 
@@ -214,7 +216,10 @@ def train(X, yq, yp, steps=3000, lr=3e-3, seed=11, device="cuda", val=None, ever
                 torch.from_numpy(np.ascontiguousarray(pa, dtype=np.int32)).to(dev),
                 torch.empty(nb // 4 + 64, dtype=torch.float32, device=dev), nb)
 
-    prm = torch.from_numpy(init_params(seed).astype(np.float32)).to(dev)
+    start = init_params(seed) if init is None else np.asarray(init, dtype=np.float64)
+    if start.size != rqlp.MLP_PARAMS:
+        raise ValueError(f"init: {start.size} parameters, expected {rqlp.MLP_PARAMS}")
+    prm = torch.from_numpy(start.astype(np.float32)).to(dev)
     m1 = torch.zeros_like(prm)
     m2 = torch.zeros_like(prm)
     grad = torch.empty_like(prm)
@@ -260,6 +265,19 @@ def fold_standardisation(params, mu, sd, F=rqlp.MLP_FEATURES, H=rqlp.MLP_HIDDEN)
     b1n = b1 - (mu / sd) @ W1
     p[:F * H] = W1n.ravel()
     p[F * H:F * H + H] = b1n
+    return p
+
+
+def unfold_standardisation(params, mu, sd, F=rqlp.MLP_FEATURES, H=rqlp.MLP_HIDDEN):
+    """Inverse of fold_standardisation: the network on raw x -> the same
+    network on (x - mu) / sd (to resume training from saved weights)."""
+    p = np.asarray(params, dtype=np.float64).copy()
+    W1n = p[:F * H].reshape(F, H)
+    b1n = p[F * H:F * H + H]
+    W1 = W1n * sd[:, None]
+    b1 = b1n + mu @ W1n
+    p[:F * H] = W1.ravel()
+    p[F * H:F * H + H] = b1
     return p
 
 
@@ -347,6 +365,8 @@ def main():
     ap.add_argument("--large", type=int, default=0,
                     help="add this many training matrices with n in [2048, 8192] (and a fifth as many to test)")
     ap.add_argument("--save", action="store_true", help="write data/qp_mlp.f32")
+    ap.add_argument("--resume", default=None,
+                    help="start from saved weights (a qp_mlp.f32); Adam's moments restart from zero")
     a = ap.parse_args()
     import torch
     torch.cuda.set_device(0)
@@ -375,8 +395,9 @@ def main():
     sd = Xtr.std(axis=0)
     sd[sd < 1e-6] = 1.0
     t1 = time.time()
+    init = unfold_standardisation(load_weights(a.resume), mu, sd) if a.resume else None
     params, curve = train((Xtr - mu) / sd, yqtr, yptr, steps=a.steps, lr=a.lr,
-                          val=((Xva - mu) / sd, yqva, ypva))
+                          val=((Xva - mu) / sd, yqva, ypva), init=init)
     t_train = time.time() - t1
     params = fold_standardisation(params, mu, sd)
     ev = evaluate(params, fte, tabte, kte)

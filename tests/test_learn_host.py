@@ -38,6 +38,21 @@ def test_fold_standardisation():
     np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-12)
 
 
+def test_unfold_inverts_fold():
+    """Resuming training: unfolding saved (folded) weights with the new
+    dataset's mu, sd gives the network on standardised features, and folding
+    it back returns the saved weights."""
+    g = inputs.rng(9)
+    saved = g.standard_normal(mo.n_params()) * 0.3
+    X = g.standard_normal((40, mo.N_FEATURES)) * 2.0 - 0.7
+    mu, sd = X.mean(axis=0), X.std(axis=0)
+    theta = learn.unfold_standardisation(saved, mu, sd)
+    ref, _ = mo.forward(saved, X)
+    got, _ = mo.forward(theta, (X - mu) / sd)
+    np.testing.assert_allclose(got, ref, rtol=1e-11, atol=1e-11)
+    np.testing.assert_allclose(learn.fold_standardisation(theta, mu, sd), saved, rtol=1e-12, atol=1e-12)
+
+
 def test_draw_problem_tail_window():
     g = inputs.rng(21)
     for _ in range(20):
