@@ -74,7 +74,17 @@ def parse():
                     help="batched leg: FP32 products, BF16x3 tensor-core passes, or both (value = BF16x3)")
     ap.add_argument("--sample", type=int, default=0,
                     help="rows/cols of the oracle's sample block (0 = default for the workload)")
+    ap.add_argument("--log", default=None, help="also append the JSON line to this JSONL file")
     return ap.parse_args()
+
+
+def emit(a, line):
+    """The run's one JSON line on stdout (and appended to --log)."""
+    text = json.dumps(line)
+    print(text, flush=True)
+    if a.log:
+        with open(a.log, "a") as f:
+            f.write(text + "\n")
 
 
 def workload_name(a):
@@ -229,7 +239,7 @@ def run_reference(a):
             "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
+    emit(a, line)
 
 
 # ------------------------------------------------------------------ our arm
@@ -507,7 +517,7 @@ def main():
                     "dtype": "bf16x3" if bt["precision"] == "bf16x3" else "f32",
                     "data": "synthetic", "config": {"workload": bt["workload"], "l2": "inputs larger than L2"},
                     "clocks": clocks, "batched": bt}
-            print(json.dumps(line), flush=True)
+            emit(a, line)
         if world > 1:
             dist.destroy_process_group()
         return
@@ -633,7 +643,7 @@ def main():
                 "status": status, "clocks": ck, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "compare": compare, "batched": batched,
                 "gpu_launches": launches, "kernel_sha": sha}
-        print(json.dumps(line), flush=True)
+        emit(a, line)
     if world > 1:
         dist.destroy_process_group()
 

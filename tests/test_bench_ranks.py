@@ -59,3 +59,21 @@ def test_reference_arm_other_ranks_exit_without_work(rank):
                        capture_output=True, text=True, timeout=120, env=env, cwd=ROOT)
     assert r.returncode == 0, r.stderr
     assert r.stdout.strip() == ""
+
+
+def test_log_appends_the_json_line(tmp_path):
+    """--log appends the printed JSON line to a JSONL file (reference arm,
+    small oracle sample, CPU)."""
+    import json
+    log = tmp_path / "runs.jsonl"
+    env = dict(os.environ, RANK="0", WORLD_SIZE="1")
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1", "--warmup", "0",
+           "--sample", "300", "--log", str(log)]
+    log.write_text('{"earlier": "run"}\n')
+    r = subprocess.run(cmd, capture_output=True, text=True, timeout=300, env=env, cwd=ROOT)
+    assert r.returncode == 0, r.stderr
+    lines = log.read_text().splitlines()
+    assert len(lines) == 2 and json.loads(lines[0]) == {"earlier": "run"}     # appended, not overwritten
+    rec = json.loads(lines[1])
+    assert rec["impl"] == "reference" and rec["unit"] == "GB/s" and rec["value"] > 0
+    assert json.loads(r.stdout.strip().splitlines()[-1]) == rec
