@@ -275,8 +275,9 @@ rqlp_status rqlp_factor_learned(const float* A, int64_t m, int64_t n, int64_t ld
  * remembers the choice for later plans with the same size mix (process
  * wide). It runs products out of order on the workspace: run it before the
  * batch is launched, then launch. rqlp_batch_tuning writes the chosen
- * configuration ids (shape-major, 2 buckets per shape) and returns their
- * count. */
+ * configuration ids (shape-major, 2 buckets per shape; id = tile shape 0..5,
+ * plus 6 for one CTA per tile) and returns their count. In the BF16X3 form
+ * the tall shapes' ids are unused (those passes run on the tensor cores). */
 #define RQLP_BATCH_MAX_D 128
 typedef struct {
   const float* A; int64_t m, n, lda;
