@@ -119,7 +119,10 @@ rqlp_status rqlp_factor(const float* A, int64_t m, int64_t n, int64_t lda,
  * device, factored, and the factors copied back; the call returns after the
  * stream has been synchronised. workspace (device) must hold
  * rqlp_host_workspace_bytes(...) bytes. h_info (2 ints) and h_diag (4
- * doubles, may be NULL) are host arrays with the layouts above. */
+ * doubles, may be NULL) are host arrays with the layouts above. Every return
+ * after the first copy has been enqueued (error returns included) follows a
+ * synchronisation of the stream, so the host buffers are free for reuse when
+ * the call returns. */
 size_t rqlp_host_workspace_bytes(int64_t m, int64_t n, int k, int p, int q,
                                  const rqlp_opts* opts);
 rqlp_status rqlp_factor_host(const float* hA, int64_t m, int64_t n, int64_t lda,

@@ -464,21 +464,28 @@ rqlp_status rqlp_factor_host(const float* hA, int64_t m, int64_t n, int64_t lda,
   const size_t off = (size_t)round_up((int64_t)ar.off, 256);
   void* core = static_cast<char*>(workspace) + off;
   const size_t F = sizeof(float);
+  // Once a copy from the caller's host buffers is enqueued, every return
+  // waits for the stream first, so no copy is still reading or writing them
+  // when the caller gets control back (error paths included).
+  auto fail = [st](rqlp_status s) {
+    (void)cudaStreamSynchronize(st);
+    return s;
+  };
   if (cudaMemcpy2DAsync(A, n * F, hA, lda * F, n * F, m, cudaMemcpyHostToDevice, st) != cudaSuccess ||
       cudaMemcpy2DAsync(Om, ld * F, hOmega, ldo * F, d * F, m, cudaMemcpyHostToDevice, st) != cudaSuccess)
-    return RQLP_ERR_CUDA;
+    return fail(RQLP_ERR_CUDA);
   rqlp_status s = rqlp_factor(A, m, n, n, k, p, q, Om, ld, Q, ld, L, ld, P, ld, core, ws_bytes - off, info,
                               diag, &o, stream);
-  if (s != RQLP_OK) return s;
+  if (s != RQLP_OK) return fail(s);
   if (cudaMemcpy2DAsync(hQ, ldq * F, Q, ld * F, d * F, m, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaMemcpy2DAsync(hL, ldl * F, L, ld * F, d * F, d, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaMemcpy2DAsync(hP, ldp * F, P, ld * F, d * F, n, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaMemcpyAsync(h_info, info, RQLP_INFO_INTS * sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess)
-    return RQLP_ERR_CUDA;
+    return fail(RQLP_ERR_CUDA);
   if (h_diag != nullptr &&
       cudaMemcpyAsync(h_diag, diag, RQLP_DIAG_DOUBLES * sizeof(double), cudaMemcpyDeviceToHost, st) !=
           cudaSuccess)
-    return RQLP_ERR_CUDA;
+    return fail(RQLP_ERR_CUDA);
   return cudaStreamSynchronize(st) == cudaSuccess ? RQLP_OK : RQLP_ERR_CUDA;
 }
 

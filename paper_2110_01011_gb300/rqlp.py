@@ -13,6 +13,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import re
 
 from . import build as _build
 
@@ -205,7 +206,24 @@ def rqlp_factor_noalloc(A, m, n, lda, k, p, q, Omega, ldo, Q, ldq, L, ldl, P, ld
                                           ctypes.byref(opts) if opts is not None else None, stream))
 
 
-NOALLOC_SCRATCH_BYTES = 16 << 20
+def header_define(name: str) -> int:
+    """Integer value of a ``#define`` in include/rqlp.h (a decimal literal, or
+    ``(a << b)`` with an optional ``u`` suffix), read from the header itself so
+    that the binding carries no second copy of the library's limits."""
+    hdr = os.path.join(_build.ROOT, "include", "rqlp.h")
+    with open(hdr) as f:
+        text = f.read()
+    mt = re.search(r"^#define\s+" + re.escape(name) + r"\s+(.+?)\s*$", text, re.M)
+    if mt is None:
+        raise KeyError(f"{name} is not defined in {hdr}")
+    expr = mt.group(1).replace("u", "").replace("(", "").replace(")", "").strip()
+    parts = [x.strip() for x in expr.split("<<")]
+    if not 1 <= len(parts) <= 2 or not all(x.isdigit() for x in parts):
+        raise ValueError(f"{name}: unsupported expression {mt.group(1)!r}")
+    return int(parts[0]) << (int(parts[1]) if len(parts) == 2 else 0)
+
+
+NOALLOC_SCRATCH_BYTES = header_define("RQLP_NOALLOC_SCRATCH_BYTES")
 
 
 def rqlp_sketch_workspace_bytes(trans, m, n, d, opts=None):

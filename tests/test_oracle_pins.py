@@ -286,3 +286,66 @@ def test_planted_mistakes_are_caught():
     for kind in ("transposed_sketch", "dropped_power_pass", "no_transpose_step5",
                  "rotate_transposed", "unsigned_qr", "power_pass_sign"):
         assert not _pins_pass(_mutant(kind)), kind
+
+
+# ---------------------------------------------------------------- closed forms of the bound helpers
+
+def _planes(a, b, g):
+    """Orthonormal X = [e1, e2] and Y = [cos a e1 + sin a e3, cos b e2 + sin b e4]
+    in R^6, both rotated by one Haar matrix: their canonical angles are a and b
+    (the definitions of section 4.1, Theorem 2, applied to two planes)."""
+    E = np.eye(6)
+    X = E[:, :2]
+    Y = np.stack([np.cos(a) * E[:, 0] + np.sin(a) * E[:, 2], np.cos(b) * E[:, 1] + np.sin(b) * E[:, 3]], axis=1)
+    W = inputs.haar_columns(6, 6, g)
+    return W @ X, W @ Y
+
+
+@pytest.mark.parametrize("a,b", [(0.3, 1.1), (1.2, 0.2), (0.0, 0.0), (np.pi / 2, 0.5), (0.7, 0.7)])
+def test_subspace_sin_closed_form(a, b):
+    g = inputs.rng(311)
+    X, Y = _planes(a, b, g)
+    want = max(np.sin(a), np.sin(b))
+    assert abs(subspace_sin(X, Y) - want) < 1e-13
+    assert abs(subspace_sin(Y, X) - want) < 1e-13          # symmetric for equal dimensions
+    # any orthonormal basis of the same spans gives the same distance
+    G = inputs.haar_columns(2, 2, g)
+    assert abs(subspace_sin(X @ G, Y @ G.T) - want) < 1e-13
+
+
+def test_subspace_sin_rejects_plausible_mistakes():
+    """Candidate definitions a slip could produce disagree with the closed form."""
+    g = inputs.rng(312)
+    X, Y = _planes(0.4, 0.9, g)
+    want = np.sin(0.9)
+    wrong = {
+        "norm_XtY_minus_1": abs(np.linalg.norm(X.T @ Y, 2) - 1.0),
+        "smallest_angle": float(np.linalg.svd(Y - X @ (X.T @ Y), compute_uv=False)[-1]),
+        "cosine": float(np.linalg.svd(X.T @ Y, compute_uv=False)[-1]),
+        "frobenius": float(np.linalg.norm(Y - X @ (X.T @ Y))),
+    }
+    for name, v in wrong.items():
+        assert abs(v - want) > 1e-3, name
+    assert abs(subspace_sin(X, Y) - want) < 1e-13
+
+
+def test_omega_ratio_closed_form():
+    """Omega~ = U^T Omega_1 = [D1; D2] with D1 = diag(d), D2 = [diag(c); 0]:
+    Omega~_2 Omega~_1^{-1} = [diag(c / d); 0], whose 2-norm is max |c_i / d_i|
+    (the quantity t of section 4.1, eq. 3, that Theorems 1-3 carry)."""
+    n, k = 12, 3
+    g = inputs.rng(313)
+    U = inputs.haar_columns(n, n, g)
+    d = np.array([2.0, -0.5, 4.0])
+    c = np.array([1.0, 0.75, -10.0])
+    Ot = np.zeros((n, k + 2))
+    Ot[:k, :k] = np.diag(d)
+    Ot[k:2 * k, :k] = np.diag(c)
+    Ot[:, k:] = g.standard_normal((n, 2))          # columns past k do not enter t
+    Om = U @ Ot
+    want = np.max(np.abs(c / d))
+    assert abs(omega_ratio(U, Om, k) - want) < 1e-12 * want
+    # planted slips: Omega~_1^{-1} Omega~_2 shape error, U in place of U^T, inverse dropped
+    assert abs(float(np.linalg.norm((U @ Om[:, :k])[k:] @ np.linalg.inv((U @ Om[:, :k])[:k]), 2)) - want) > 1e-3
+    assert abs(float(np.linalg.norm(Ot[k:, :k] @ Ot[:k, :k], 2)) - want) > 1e-3
+    assert abs(float(np.linalg.norm(Ot[k:, :k], 2)) - want) > 1e-3

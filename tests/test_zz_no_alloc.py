@@ -24,7 +24,7 @@ def _problem(m, n, k, p, seed):
     return A, Om
 
 
-def _noalloc(dA, dO, k, p, q):
+def _noalloc(dA, dO, k, p, q, precision=rqlp.PREC_FP32):
     import torch
     m, n = dA.shape
     d = k + p
@@ -37,23 +37,37 @@ def _noalloc(dA, dO, k, p, q):
     st = rqlp.rqlp_factor_noalloc(dA.data_ptr(), m, n, dA.stride(0), k, p, q, dO.data_ptr(),
                                   dO.stride(0), Q.data_ptr(), Q.stride(0), L.data_ptr(), L.stride(0),
                                   P.data_ptr(), P.stride(0), info.data_ptr(), diag.data_ptr(),
-                                  rqlp.rqlp_default_opts(), torch.cuda.current_stream().cuda_stream)
+                                  rqlp.Opts(precision=precision), torch.cuda.current_stream().cuda_stream)
     assert st == 0, rqlp.rqlp_status_string(st)
     return Q, L, P, info
 
 
+def _largest_square_within_bound(k, p, q, precision):
+    """The largest n (multiple of 64) whose n x n problem fits the library's
+    array: the bound is read from include/rqlp.h, not from a second copy."""
+    o = rqlp.Opts(precision=precision)
+    n = 64
+    while rqlp.rqlp_workspace_bytes(n + 64, n + 64, k, p, q, o) <= rqlp.header_define("RQLP_NOALLOC_SCRATCH_BYTES"):
+        n += 64
+    return n
+
+
 @pytest.mark.gpu
-def test_noalloc_matches_rqlp_factor_twice_in_a_row():
+@pytest.mark.parametrize("precision", [rqlp.PREC_FP32, rqlp.PREC_BF16X3])
+def test_noalloc_matches_rqlp_factor_twice_in_a_row(precision):
+    """Two calls in a row on different problems (the second one as large as
+    the array allows), each against rqlp_factor with a caller workspace."""
     import torch
-    cases = [(1000, 1000, 20, 5, 1, 11), (700, 500, 12, 4, 2, 23)]
+    nmax = _largest_square_within_bound(12, 4, 2, precision)
+    cases = [(1000, 1000, 20, 5, 1, 11), (nmax, nmax, 12, 4, 2, 23)]
     for (m, n, k, p, q, seed) in cases:
         A, Om = _problem(m, n, k, p, seed)
         dA = torch.from_numpy(A).cuda()
         dO = torch.from_numpy(Om).cuda()
-        Qn, Ln, Pn, info_n = _noalloc(dA, dO, k, p, q)
+        Qn, Ln, Pn, info_n = _noalloc(dA, dO, k, p, q, precision)
         torch.cuda.synchronize()
         Qn, Ln, Pn = (x.double().cpu().numpy() for x in (Qn, Ln, Pn))
-        Qr, Lr, Pr, info_r, _ = rqlp.factor(dA, k, p, q, dO)
+        Qr, Lr, Pr, info_r, _ = rqlp.factor(dA, k, p, q, dO, precision=precision)
         torch.cuda.synchronize()
         Qr, Lr, Pr = (x.double().cpu().numpy() for x in (Qr, Lr, Pr))
         assert int(info_n[0]) == 0 and int(info_r[0]) == 0
@@ -63,11 +77,22 @@ def test_noalloc_matches_rqlp_factor_twice_in_a_row():
         assert np.max(np.abs(np.diag(Ln) - np.diag(Lr)) / np.diag(Lr)) <= TOL_LII
 
 
+def test_noalloc_bound_comes_from_the_header():
+    """The binding's copy of the array size is the header's value, and the
+    sizes used above straddle it."""
+    bound = rqlp.header_define("RQLP_NOALLOC_SCRATCH_BYTES")
+    assert rqlp.NOALLOC_SCRATCH_BYTES == bound
+    for prec in (rqlp.PREC_FP32, rqlp.PREC_BF16X3):
+        n = _largest_square_within_bound(12, 4, 2, prec)
+        o = rqlp.Opts(precision=prec)
+        assert rqlp.rqlp_workspace_bytes(n, n, 12, 4, 2, o) <= bound < rqlp.rqlp_workspace_bytes(n + 64, n + 64, 12, 4, 2, o)
+
+
 def test_noalloc_rejects_oversize_before_any_work():
     """A problem whose workspace exceeds the library's array is refused with
     RQLP_ERR_WORKSPACE before anything touches the (fake) pointers."""
     m, n, k, p, q = 8192, 8192, 200, 10, 2
-    assert rqlp.rqlp_workspace_bytes(m, n, k, p, q) > rqlp.NOALLOC_SCRATCH_BYTES
+    assert rqlp.rqlp_workspace_bytes(m, n, k, p, q) > rqlp.header_define("RQLP_NOALLOC_SCRATCH_BYTES")
     fake = 0x1000
     st = rqlp.rqlp_factor_noalloc(fake, m, n, n, k, p, q, fake, k + p, fake, k + p, fake, k + p,
                                   fake, k + p, fake, None, rqlp.rqlp_default_opts(), None)
