@@ -59,6 +59,8 @@ def parse():
                     help="learned form: this request instead of the excess error FP32 (2, 10) reaches")
     ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "bf16x3"],
                     help="--form fixed: the form timed (auto = bf16x3)")
+    ap.add_argument("--parts", type=int, default=0, choices=[0, 2, 3],
+                    help="BF16 parts per pass operand of the split form (0 = the library's automatic choice)")
     ap.add_argument("--m", type=int, default=20000)
     ap.add_argument("--n", type=int, default=20000)
     ap.add_argument("--k", type=int, default=200)
@@ -307,14 +309,15 @@ def fixed_runner(a, A, Om, q, p, prec, dev):
 
     from paper_2110_01011_gb300 import rqlp
     d = a.k + p
-    opts = rqlp._opts(prec)
+    parts = a.parts if prec == rqlp.PREC_BF16X3 else 0
+    opts = rqlp._opts(prec, parts=parts)
     ws = torch.empty(rqlp.rqlp_workspace_bytes(a.m, a.n, a.k, p, q, opts) + 256, dtype=torch.uint8, device=dev)
     out = (torch.empty(a.m, d, device=dev), torch.empty(d, d, device=dev), torch.empty(a.n, d, device=dev),
            torch.empty(2, dtype=torch.int32, device=dev), torch.empty(4, dtype=torch.float64, device=dev))
     Omp = Om[:, :d]
 
     def step():
-        rqlp.factor(A, a.k, p, q, Omp, precision=prec, workspace=ws, out=out)
+        rqlp.factor(A, a.k, p, q, Omp, precision=prec, workspace=ws, out=out, parts=parts)
     return step, out
 
 

@@ -71,7 +71,22 @@ typedef struct {
                    /* loads, so that its bounded waits run out (~2 s each)    */
                    /* and the first problem's status row reports              */
                    /* RQLP_ERR_TIMEOUT; must be 0 for every other entry point */
-  int reserved[5]; /* must be zero                                            */
+  int bf16_parts;  /* BF16X3 only (0 with FP32): BF16 parts per operand of   */
+                   /* the passes over A. 2: A = A_hi + A_lo, X = X_hi + X_lo, */
+                   /* three products, error ~2^-16 |A| |X| per pass; 3: a    */
+                   /* third part each (A_lo2 = bf16(A - A_hi - A_lo)), the   */
+                   /* six products above 2^-24, FP32-level error at twice    */
+                   /* the MMA work and 1.5x the bytes of the split A;        */
+                   /* 0: automatic: three parts when p < 5 or m n <= 2^27,  */
+                   /* else two (the batched form: three parts)               */
+  int literal_step5; /* 0: step 5 on the d x d R, (P^, R^) = qr(R^T),         */
+                   /* L = R^^T, P = P~ P^ (no third pass over A); 1: step 5 */
+                   /* as Algorithm 1 prints it, (P, R') = qr((Q^T A)^T) =   */
+                   /* qr(A^T Q), L = R'^T: a third pass over A. The two     */
+                   /* agree when rank(A) <= d or d = n; with d = n, q = 0   */
+                   /* and 1 the chain is Algorithm 1 as printed. Single-    */
+                   /* matrix entry points only (0 for the batched form)     */
+  int reserved[3]; /* must be zero                                            */
 } rqlp_opts;
 
 /* d_info layout written by rqlp_factor (2 ints): [0] = rqlp_status of the
@@ -99,7 +114,16 @@ size_t rqlp_workspace_bytes(int64_t m, int64_t n, int k, int p, int q,
  *   L (d x d, ldl): lower triangular with positive diagonal, strict upper
  *                   part written as 0;
  *   P (n x d, ldp): orthonormal columns,
- * such that Q L P^T = A P~ P~^T ~= A. workspace must be 256-byte aligned and
+ * such that Q L P^T = A P~ P~^T ~= A. In the BF16X3 form the low parts'
+ * products accumulate in a TMEM accumulator apart from A_hi X_hi (added with
+ * round-to-nearest at the end of each chain). Unless opts->bf16_parts says
+ * otherwise the passes take three BF16 parts when p < 5 (a nearly square
+ * leading block of U^T Omega, whose large inverse amplifies pass rounding;
+ * Theorems 1-2) or m n <= 2^27, and two parts above that size, where every
+ * entry of a pass sums over K >= ~11600 products and the two-part rounding
+ * averages out (measured: |L_ii| within 5e-5 of the FP64 oracle at 16384^2
+ * and 20000^2 for sigma_1 / sigma_k up to 100). workspace must be 256-byte
+ * aligned and
  * hold rqlp_workspace_bytes(...) bytes; its contents on entry are ignored.
  * d_info: RQLP_INFO_INTS device ints (required). d_diag: RQLP_DIAG_DOUBLES
  * device doubles or NULL. opts may be NULL (defaults). Output buffers must
@@ -252,9 +276,9 @@ rqlp_status rqlp_factor_learned(const float* A, int64_t m, int64_t n, int64_t ld
  * BF16 halves of every A (split once per launch into the workspace, which
  * then also holds the halves, the pass operands' halves and eight tensor
  * maps per problem), the d-wide products in FP32; RQLP_ERR_UNSUPPORTED on a
- * device without the tensor-core path. The split form's pass error is
- * ~2^-16 of |A| |X|, so an |L_ii| near sigma_i carries up to about
- * 2^-15 sigma_1 / sigma_i of its own size.
+ * device without the tensor-core path. The passes take three BF16 parts per
+ * operand (six products, FP32-level rounding) unless opts->bf16_parts = 2
+ * (three products, ~2^-16 of |A| |X| per pass).
  *
  * A batch plan is built once on the host: it lays out the caller's
  * workspace, writes the per-problem job tables into it (one synchronous

@@ -31,7 +31,8 @@ namespace {
 // Product shapes the tuner distinguishes.
 enum Shape { kTallT = 0, kTallN = 1, kGram = 2, kTrmm = 3, kSmall = 4, kShapes = 5 };
 constexpr int kBuckets = 2;
-constexpr int kGates = 4;
+constexpr int kGates = 4;       // [0..2] final orthonormalisations, [3] intermediate ones
+constexpr int kInterGate = 3;
 
 int bucket_of(int d) { return d <= 32 ? 0 : 1; }
 
@@ -57,12 +58,17 @@ struct Bufs {
   int* gates;
   int64_t ld;
   uint16_t *Ahi = nullptr, *Alo = nullptr, *XTh = nullptr, *XTl = nullptr;
+  uint16_t *Alo2 = nullptr, *XTl2 = nullptr;   // three-part form only
   int64_t ldk = 0;
   char* maps = nullptr;     // 8 x kTcMapBytes
   int* flag = nullptr;      // X low part nonzero (per pass)
 };
 // Tensor maps of one problem, in this order.
-enum TcMap { kMapAhiT, kMapAloT, kMapAhiN, kMapAloN, kMapXhiM, kMapXloM, kMapXhiN, kMapXloN, kTcMaps };
+enum TcMap {
+  kMapAhiT, kMapAloT, kMapAhiN, kMapAloN, kMapXhiM, kMapXloM, kMapXhiN, kMapXloN,
+  kMapAlo2T, kMapAlo2N, kMapXlo2M, kMapXlo2N,   // three-part form only
+  kTcMaps
+};
 constexpr int kMaxTcCtas = 1024;
 
 struct GemmStage {
@@ -86,10 +92,11 @@ struct TcStage {
   int G;
   int npad_max;
   int stall;              // test hook: CTA 0 withholds its first stage (first pass only)
+  bool exact;             // A and X in three BF16 parts, six products
 };
 
 struct Stage {
-  enum Kind { kInit, kGemm, kChol, kTranspose, kWriteL, kFinish, kSplit, kTc } kind;
+  enum Kind { kInit, kGemm, kChol, kTranspose, kWriteL, kFinish, kSplit, kTc, kGateClear, kCopyGated } kind;
   int gemm = -1;         // index into gemms / tcs
   size_t jobs_off = 0;   // CholJob[], SmallJob[] or SplitJob[]
   size_t start_off = 0;  // kSplit: int[count + 1] block prefix
@@ -104,6 +111,7 @@ struct rqlp_batch_s {
   long long sums[rqlp::kBuckets][3] = {};    // per bucket: sum of m, n, d (tuning key)
   int cnt[rqlp::kBuckets] = {0, 0};          // problems per bucket (bucket 0 first)
   rqlp_opts opts{};
+  bool exact = false;                        // BF16x3 passes in three parts
   char* dev = nullptr;                       // plan area in the workspace
   std::vector<rqlp::Stage> stages;
   std::vector<rqlp::GemmStage> gemms;
@@ -219,6 +227,7 @@ struct Builder {
       j.npan = cdiv(pr[i].n, 64);
       j.hi = bf[i].Ahi;
       j.lo = bf[i].Alo;
+      j.lo2 = b->exact ? bf[i].Alo2 : nullptr;
       j.sumsq = &bf[i].scal[0];
       j.vec = (reinterpret_cast<uintptr_t>(pr[i].A) % 16 == 0 && pr[i].lda % 4 == 0) ? 1 : 0;
       js.push_back(j);
@@ -252,6 +261,8 @@ struct Builder {
       j.mAlo = mp + (transA ? kMapAloT : kMapAloN) * kTcMapBytes;
       j.mXhi = mp + (transA ? kMapXhiM : kMapXhiN) * kTcMapBytes;
       j.mXlo = mp + (transA ? kMapXloM : kMapXloN) * kTcMapBytes;
+      j.mAlo2 = mp + (transA ? kMapAlo2T : kMapAlo2N) * kTcMapBytes;
+      j.mXlo2 = mp + (transA ? kMapXlo2M : kMapXlo2N) * kTcMapBytes;
       j.out = out(i);
       j.ldo = bf[i].ld;
       j.M = (int)M;
@@ -269,6 +280,7 @@ struct Builder {
       p.d = di;
       p.th = bf[i].XTh;
       p.tl = bf[i].XTl;
+      p.tl2 = b->exact ? bf[i].XTl2 : nullptr;
       p.ldk = bf[i].ldk;
       p.flag = bf[i].flag;
       ps.push_back(p);
@@ -301,6 +313,7 @@ struct Builder {
     ts.cta_off = sg.put(cs.data(), cs.size());
     ts.G = G;
     ts.stall = (b->opts.test_stall != 0 && b->tcs.empty()) ? 1 : 0;
+    ts.exact = b->exact;
     Stage s;
     s.kind = Stage::kTc;
     s.gemm = (int)b->tcs.size();
@@ -345,27 +358,61 @@ struct Builder {
     }
     chol(js);
   }
-  // out = X R_slot^{-1}; gate_slot >= 0: out = X when that gate is 0.
+  // out = X R_slot^{-1}; gate_slot >= 0: when that gate is 0, out = X
+  // (kGateCopy) or no work (kGateSkip).
   template <typename XF, typename OF, typename LF, typename RF>
-  void trmm(XF X, OF out, LF ldout, RF rows, int slot, int shape, int gate_slot) {
+  void trmm(XF X, OF out, LF ldout, RF rows, int slot, int shape, int gate_slot, int gate_mode = kGateCopy) {
     std::vector<GroupGemm> js;
     for (int i = 0; i < n(); ++i) {
       GroupGemm j = job(X(i), bf[i].ld, bf[i].Ri[slot], bf[i].ld, out(i), ldout(i), rows(i), d(i), d(i));
       j.b_upper = 1;
       if (gate_slot >= 0) {
         j.gate = &bf[i].gates[gate_slot];
-        j.gate_mode = kGateCopy;
+        j.gate_mode = gate_mode;
       }
       js.push_back(j);
     }
     gemm(false, shape, js, gate_slot >= 0);
   }
-  // One CholeskyQR pass: out = X R^{-1} (slot 0).
+  // Gate word `slot` of every problem back to 0.
+  void gate_clear(int slot) {
+    std::vector<SmallJob> js(n());
+    for (int i = 0; i < n(); ++i) {
+      js[i].gates = bf[i].gates;
+      js[i].ngates = slot;
+    }
+    small(Stage::kGateClear, js);
+  }
+  // out = X for the problems whose gate `slot` is raised.
+  template <typename XF, typename OF, typename RF>
+  void copy_gated(XF X, OF out, RF rows, int slot) {
+    std::vector<SmallJob> js(n());
+    for (int i = 0; i < n(); ++i) {
+      js[i].d = d(i);
+      js[i].X = X(i); js[i].ldx = bf[i].ld;
+      js[i].Y = out(i); js[i].ldy = bf[i].ld;
+      js[i].rows = rows(i);
+      js[i].gates = bf[i].gates;
+      js[i].ngates = slot;
+    }
+    small(Stage::kCopyGated, js);
+  }
+  // One CholeskyQR pass, out = X R^{-1} (slot 0), and a second one for the
+  // problems whose first Cholesky had to shift (gate kInterGate): a shifted
+  // factor keeps the span but leaves out far from orthonormal, which the
+  // next pass over A would carry into its small directions. X is dead after.
   template <typename XF, typename OF, typename RF>
   void orth_inter(XF X, OF out, RF rows, bool tall) {
-    gram(X, rows, tall ? kGram : kSmall, -1);
-    cholesky(0, -1, -1);
-    trmm(X, out, [&](int i) { return bf[i].ld; }, rows, 0, tall ? kTrmm : kSmall, -1);
+    const int gs = tall ? kGram : kSmall, ts = tall ? kTrmm : kSmall;
+    auto ld = [&](int i) { return bf[i].ld; };
+    gate_clear(kInterGate);
+    gram(X, rows, gs, -1);
+    cholesky(0, kInterGate, -1);
+    trmm(X, out, ld, rows, 0, ts, -1);
+    gram(out, rows, gs, kInterGate);
+    cholesky(1, -1, kInterGate);
+    trmm(out, X, ld, rows, 1, ts, kInterGate, kGateSkip);
+    copy_gated(X, out, rows, kInterGate);
   }
   // CholeskyQR2 plus a third pass gated on a shifted Cholesky; X is
   // overwritten; Racc (optional) receives R3 R2 R1.
@@ -422,40 +469,28 @@ struct Builder {
     }
     small(Stage::kInit, sj);
 
-    // Y = A^T Omega (Algorithm 1 step 3); ||A||_F^2 rides along (or comes
-    // with the split in the BF16x3 form).
-    if (tc) {
-      split_stage();
-      tc_pass(true, [&](int i) { return pr[i].Omega; }, [&](int i) { return pr[i].ldo; }, Y);
-    } else {
+    // A pass over every problem: grouped tensor-core passes in the BF16x3
+    // form, grouped FP32 products otherwise (sumsq: ||A||_F^2 rides along).
+    auto pass = [&](bool transA, auto X, auto ldx, auto out, bool sumsq) {
+      if (tc) {
+        tc_pass(transA, X, ldx, out);
+        return;
+      }
       std::vector<GroupGemm> js;
       for (int i = 0; i < n(); ++i) {
-        GroupGemm j = job(pr[i].A, pr[i].lda, pr[i].Omega, pr[i].ldo, bf[i].Y, bf[i].ld, pr[i].n, d(i), pr[i].m);
-        j.sumsq = &bf[i].scal[0];
+        const int64_t M = transA ? pr[i].n : pr[i].m, K = transA ? pr[i].m : pr[i].n;
+        GroupGemm j = job(pr[i].A, pr[i].lda, X(i), ldx(i), out(i), bf[i].ld, M, d(i), K);
+        if (sumsq) j.sumsq = &bf[i].scal[0];
         js.push_back(j);
       }
-      gemm(true, kTallT, js, false);
-    }
-    auto passN = [&](auto X, auto out) {   // out (m x d) = A X
-      if (tc) {
-        tc_pass(false, X, ld, out);
-        return;
-      }
-      std::vector<GroupGemm> js;
-      for (int i = 0; i < n(); ++i)
-        js.push_back(job(pr[i].A, pr[i].lda, X(i), bf[i].ld, out(i), bf[i].ld, pr[i].m, d(i), pr[i].n));
-      gemm(false, kTallN, js, false);
+      gemm(transA, transA ? kTallT : kTallN, js, false);
     };
-    auto passT = [&](auto X, auto out) {   // out (n x d) = A^T X
-      if (tc) {
-        tc_pass(true, X, ld, out);
-        return;
-      }
-      std::vector<GroupGemm> js;
-      for (int i = 0; i < n(); ++i)
-        js.push_back(job(pr[i].A, pr[i].lda, X(i), bf[i].ld, out(i), bf[i].ld, pr[i].n, d(i), pr[i].m));
-      gemm(true, kTallT, js, false);
-    };
+    // Y = A^T Omega (Algorithm 1 step 3); ||A||_F^2 comes with it (or with
+    // the split in the BF16x3 form).
+    if (tc) split_stage();
+    pass(true, [&](int i) { return pr[i].Omega; }, [&](int i) { return pr[i].ldo; }, Y, true);
+    auto passN = [&](auto X, auto out) { pass(false, X, ld, out, false); };   // out (m x d) = A X
+    auto passT = [&](auto X, auto out) { pass(true, X, ld, out, false); };    // out (n x d) = A^T X
 
     if (q == 0) orth_final(Y, Pt, ld, T1, rows_n, true, 0, none, false);
     else orth_inter(Y, Pt, rows_n, true);
@@ -496,7 +531,7 @@ struct Builder {
   }
 };
 
-Bufs take_bufs(Arena& ar, const rqlp_problem& p, bool tc) {
+Bufs take_bufs(Arena& ar, const rqlp_problem& p, bool tc, bool exact) {
   Bufs f{};
   const int d = p.k + p.p;
   f.ld = round_up(d, 4);
@@ -525,12 +560,17 @@ Bufs take_bufs(Arena& ar, const rqlp_problem& p, bool tc) {
     f.ldk = round_up(tall, 8);
     f.XTh = ar.take<uint16_t>(d * f.ldk);
     f.XTl = ar.take<uint16_t>(d * f.ldk);
+    if (exact) {
+      f.Alo2 = ar.take<uint16_t>(p.m * cols);
+      f.XTl2 = ar.take<uint16_t>(d * f.ldk);
+    }
   }
   return f;
 }
 
-// The eight tensor maps of one problem (host encoding; false on failure).
-bool encode_maps(const Bufs& f, const rqlp_problem& p, char* out) {
+// The tensor maps of one problem (host encoding; false on failure): eight,
+// and four more for the third parts in the three-part form.
+bool encode_maps(const Bufs& f, const rqlp_problem& p, char* out, bool exact) {
   const int d = p.k + p.p, np = tc_npad(d);
   const long long npan = cdiv(p.n, 64);
   auto at_map = [&](int k) { return out + k * kTcMapBytes; };
@@ -541,7 +581,11 @@ bool encode_maps(const Bufs& f, const rqlp_problem& p, char* out) {
          tc_map2d(at_map(kMapXhiM), f.XTh, p.m, d, f.ldk, 32, np, false) &&
          tc_map2d(at_map(kMapXloM), f.XTl, p.m, d, f.ldk, 32, np, false) &&
          tc_map2d(at_map(kMapXhiN), f.XTh, p.n, d, f.ldk, 32, np, false) &&
-         tc_map2d(at_map(kMapXloN), f.XTl, p.n, d, f.ldk, 32, np, false);
+         tc_map2d(at_map(kMapXloN), f.XTl, p.n, d, f.ldk, 32, np, false) &&
+         (!exact || (tc_panel_map(at_map(kMapAlo2T), f.Alo2, p.m, npan, 64, 32, 2, true) &&
+                     tc_panel_map(at_map(kMapAlo2N), f.Alo2, p.m, npan, 32, 128, 1, false) &&
+                     tc_map2d(at_map(kMapXlo2M), f.XTl2, p.m, d, f.ldk, 32, np, false) &&
+                     tc_map2d(at_map(kMapXlo2N), f.XTl2, p.n, d, f.ldk, 32, np, false)));
 }
 
 bool valid_problem(const rqlp_problem& p) {
@@ -573,6 +617,10 @@ size_t layout(rqlp_batch_s* b, int count, const rqlp_problem* probs, Arena& ar, 
   std::vector<rqlp_problem> pr;
   std::vector<Bufs> bf;
   const bool tc = b->opts.precision == RQLP_PREC_BF16X3;
+  // Three BF16 parts unless the caller asked for two: the batch's problems are
+  // the small and medium sizes where the two-part rounding, amplified by an
+  // ill-conditioned leading block, reaches the 1e-4 |L_ii| bound.
+  b->exact = tc && b->opts.bf16_parts != 2;
   int* flags = nullptr;
   char* maps = nullptr;
   if (tc) {
@@ -589,7 +637,7 @@ size_t layout(rqlp_batch_s* b, int count, const rqlp_problem* probs, Arena& ar, 
   for (int i : ord) {
     const int d = probs[i].k + probs[i].p, bk = bucket_of(d);
     pr.push_back(probs[i]);
-    bf.push_back(take_bufs(ar, probs[i], tc));
+    bf.push_back(take_bufs(ar, probs[i], tc, b->exact));
     if (tc) {
       const size_t pos = bf.size() - 1;
       bf.back().flag = ar.dry ? nullptr : flags + pos;
@@ -603,7 +651,7 @@ size_t layout(rqlp_batch_s* b, int count, const rqlp_problem* probs, Arena& ar, 
   if (tc && !ar.dry) {
     b->maps_h.assign((size_t)count * kTcMaps * kTcMapBytes, 0);
     for (size_t i = 0; i < bf.size(); ++i)
-      if (!encode_maps(bf[i], pr[i], b->maps_h.data() + i * kTcMaps * kTcMapBytes)) b->maps_h.clear();
+      if (!encode_maps(bf[i], pr[i], b->maps_h.data() + i * kTcMaps * kTcMapBytes, b->exact)) b->maps_h.clear();
   }
   b->stages.clear();
   b->gemms.clear();
@@ -650,12 +698,14 @@ cudaError_t run_stages(const rqlp_batch_s* b, cudaStream_t st) {
       case Stage::kSplit:
         CK(split_grouped(at<SplitJob>(b, s.jobs_off), at<int>(b, s.start_off), b->count, s.total, st));
         break;
+      case Stage::kGateClear: CK(gate_clear_batched(at<SmallJob>(b, s.jobs_off), b->count, st)); break;
+      case Stage::kCopyGated: CK(copy_gated_batched(at<SmallJob>(b, s.jobs_off), b->count, st)); break;
       case Stage::kTc: {
         const TcStage& t = b->tcs[s.gemm];
         CK(cudaMemsetAsync(b->flags, 0, sizeof(int) * b->count, st));
         CK(prep_grouped(at<PrepJob>(b, t.prep_off), at<int>(b, t.prep_start_off), b->count, t.prep_total, st));
         CK(tc_grouped_pass(t.transA, at<TcGJob>(b, t.jobs_off), at<int2>(b, t.units_off), at<int>(b, t.cta_off),
-                           t.G, t.npad_max, b->info0, t.stall, st));
+                           t.G, t.npad_max, b->info0, t.stall, t.exact, st));
         break;
       }
     }
@@ -682,7 +732,10 @@ bool valid_batch(int count, const rqlp_problem* probs, int q, const rqlp_opts& o
   if ((o.precision != RQLP_PREC_FP32 && o.precision != RQLP_PREC_BF16X3) || (o.small_fp64 != 0 && o.small_fp64 != 1))
     return false;
   if (o.test_stall != 0 && (o.test_stall != 1 || o.precision != RQLP_PREC_BF16X3)) return false;
-  for (int i = 0; i < 5; ++i)
+  if (o.bf16_parts != 0 && (o.precision != RQLP_PREC_BF16X3 || (o.bf16_parts != 2 && o.bf16_parts != 3)))
+    return false;
+  if (o.literal_step5 != 0) return false;
+  for (int i = 0; i < 3; ++i)
     if (o.reserved[i] != 0) return false;
   for (int i = 0; i < count; ++i)
     if (!valid_problem(probs[i])) return false;
@@ -747,8 +800,8 @@ rqlp_status rqlp_batch_create(int count, const rqlp_problem* probs, int q, void*
   }
   if (gemm_grouped_prepare() != cudaSuccess ||
       chol_inv_batched(nullptr, 0, 0, o.small_fp64 != 0, st) != cudaSuccess ||
-      (tc && (tc_grouped_pass(true, nullptr, nullptr, nullptr, 0, 16, nullptr, 0, st) != cudaSuccess ||
-              tc_grouped_pass(false, nullptr, nullptr, nullptr, 0, 16, nullptr, 0, st) != cudaSuccess ||
+      (tc && (tc_grouped_pass(true, nullptr, nullptr, nullptr, 0, 16, nullptr, 0, false, st) != cudaSuccess ||
+              tc_grouped_pass(false, nullptr, nullptr, nullptr, 0, 16, nullptr, 0, false, st) != cudaSuccess ||
               cudaMemcpyAsync(b->maps_d, b->maps_h.data(), b->maps_h.size(), cudaMemcpyHostToDevice, st) !=
                   cudaSuccess)) ||
       cudaMemcpyAsync(b->dev, sg.h.data(), sg.h.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||

@@ -20,8 +20,14 @@
 // diagonal in a side array).
 //
 // A pivot that is not clearly positive restarts the elimination on G + s I
-// (shifted CholeskyQR, Fukaya et al. 2020) and raises the caller's gate flag;
-// a second breakdown reports RQLP_ERR_BREAKDOWN and writes identities.
+// (shifted CholeskyQR, Fukaya et al. 2020) and raises the caller's gate flag.
+// The shift starts small, s0 = 10 d u trace(G), and grows tenfold while the
+// shifted factor still breaks down (three shifts at most; then
+// RQLP_ERR_BREAKDOWN and identities): X R^{-1} has condition number about
+// sqrt(s / sigma_min(X)^2), so the smallest shift that factors leaves the
+// least for the next CholeskyQR pass. With s0 = 100 d u trace(G) one FP32
+// pass left a 317 x 66 sketch with kappa = 8e5 at kappa = 1.6e4, beyond what
+// CholeskyQR2 can finish; with s0 = 10 d u trace(G), at 5e3.
 #include <algorithm>
 #include <cmath>
 
@@ -31,6 +37,9 @@ namespace rqlp {
 namespace {
 
 constexpr int NB = 16;
+// Factorisation attempts: unshifted, then shifts s0, 10 s0, 100 s0 with
+// s0 = 10 d u trace(G) (u: unit roundoff of the factor's type).
+constexpr int kAttempts = 4;
 constexpr int kMaxD = RQLP_MAX_D;
 constexpr int kThreads = 512;
 constexpr int kBatchThreads = 128;
@@ -170,7 +179,10 @@ __device__ __forceinline__ void chol_body(int d, const float* __restrict__ G, in
   const T rel_tol = (T)64 * Eps<T>::u;
   T shift = 0;
   int fail = -1;
-  for (int attempt = 0; attempt < 2; ++attempt) {
+  for (int attempt = 0; attempt < kAttempts; ++attempt) {
+    // attempt a >= 1 factors G + 10^(a-1) s0 I: the smallest shift that
+    // succeeds reduces kappa(X R^{-1}) the most
+    if (attempt > 1) shift *= (T)10;
     const T sh = attempt == 0 ? (T)0 : shift;
     // Lower triangle of G (+ sh I) into S, zeros above: a warp per group of
     // four rows, lanes over columns, all of a group's loads issued before
@@ -206,7 +218,7 @@ __device__ __forceinline__ void chol_body(int d, const float* __restrict__ G, in
         write_identity(d, R, Rinv, ldr);
         return;
       }
-      shift = (T)(100.0 * d) * Eps<T>::u * tr;
+      shift = (T)(10.0 * d) * Eps<T>::u * tr;
     }
     fail = -1;
     // Panel loop. Phase B of panel J: warp 0 factors the diagonal block while

@@ -120,19 +120,24 @@ struct SmallJob {
   double* scal;                  // the job's scalars [||A||^2, ||L||^2, shifts, -]
   int* info;
   double* diag;                  // optional output (4 doubles)
-  int* gates; int ngates;
+  int* gates; int ngates;        // gate_clear / copy_gated: ngates = the gate's index
+  int64_t rows;                  // copy_gated: rows of X and Y (d columns)
 };
 cudaError_t init_batched(const SmallJob* jobs, int count, cudaStream_t st);
 cudaError_t transpose_batched(const SmallJob* jobs, int count, cudaStream_t st);
 cudaError_t write_L_batched(const SmallJob* jobs, int count, cudaStream_t st);
 cudaError_t finish_diag_batched(const SmallJob* jobs, int count, cudaStream_t st);
+// gates[ngates] = 0 for every job; Y = X (rows x d) for the jobs whose gates[ngates] is raised.
+cudaError_t gate_clear_batched(const SmallJob* jobs, int count, cudaStream_t st);
+cudaError_t copy_gated_batched(const SmallJob* jobs, int count, cudaStream_t st);
 cudaError_t transpose_small(int d, const float* X, int64_t ldx, float* Y, int64_t ldy, cudaStream_t st);
 cudaError_t write_L(int d, const float* Rh, int64_t ldrh, float* L, int64_t ldl, double* l2_accum,
                     cudaStream_t st);
 cudaError_t init_scratch(int* info, int* gates, int ngates, double* scal, int nscal, cudaStream_t st);
 cudaError_t finish_diag(const double* scal, double* diag, int* info, cudaStream_t st);
+// gate (optional): *gate == 0 -> no copy.
 cudaError_t copy_matrix(int64_t rows, int64_t cols, const float* X, int64_t ldx, float* Y, int64_t ldy,
-                        cudaStream_t st);
+                        cudaStream_t st, const int* gate = nullptr);
 
 // ---------------------------------------------------------------- learned (q, p)
 size_t mlp_workspace_floats(int batch);

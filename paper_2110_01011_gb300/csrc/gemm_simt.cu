@@ -104,11 +104,16 @@ __device__ __forceinline__ void gemm_tile(const GemmArgs& g, int64_t m0, int64_t
     }
   };
 
-  float acc[TM][TN];
+  // Two-level accumulation: acc runs over kPromoteTiles K-tiles (256 of K)
+  // and is then added into tot, so the rounding of a long K range grows with
+  // 256 + K / 256 terms instead of K (the Gram of a 4000-row block lost an
+  // order of magnitude of orthogonality to one running sum).
+  constexpr int kPromoteTiles = 256 / BK;
+  float acc[TM][TN], tot[TM][TN];
 #pragma unroll
   for (int i = 0; i < TM; ++i)
 #pragma unroll
-    for (int j = 0; j < TN; ++j) acc[i][j] = 0.f;
+    for (int j = 0; j < TN; ++j) acc[i][j] = tot[i][j] = 0.f;
 
   if (ntiles > 0) {
     load(kbeg);
@@ -136,9 +141,22 @@ __device__ __forceinline__ void gemm_tile(const GemmArgs& g, int64_t m0, int64_t
           for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
       }
       if (t + 1 < ntiles) store(buf ^ 1);
+      if ((t + 1) % kPromoteTiles == 0) {
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+          for (int j = 0; j < TN; ++j) {
+            tot[i][j] += acc[i][j];
+            acc[i][j] = 0.f;
+          }
+      }
       __syncthreads();
     }
   }
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] += tot[i][j];
 
 #pragma unroll
   for (int i = 0; i < TM; ++i) {

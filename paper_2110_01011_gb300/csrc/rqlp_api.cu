@@ -21,13 +21,18 @@
 namespace rqlp {
 namespace {
 
-constexpr int kGates = 8;   // gate words: one per final orthonormalisation
+constexpr int kGates = 8;   // gate words: one per final orthonormalisation, [3] intermediate ones
+constexpr int kInterGate = 3;
 constexpr int kScal = 4;    // [0] ||A||^2, [1] ||L||^2, [2] shifted Cholesky count, [3] spare
 
 // Building blocks of the chain for a fixed sketch width d, with their scratch.
 class Ops {
  public:
   Ops(int d, const rqlp_opts& o) : d_(d), dcap_(d), ld_(round_up(d, 4)), o_(o) {}
+
+  // Three BF16 parts per pass operand (six products) instead of two.
+  void set_three_part(bool on) { three_ = on; }
+  bool three_part() const { return three_; }
 
   // part_floats: largest split-K partial buffer any product of the caller needs.
   void layout(Arena& ar, size_t part_floats, bool with_tc, int64_t m, int64_t n) {
@@ -43,7 +48,7 @@ class Ops {
     gates = ar.take<int>(kGates);
     cstore_ = ar.take<char>(chol_global_bytes(dcap_, o_.small_fp64 != 0));
     if (with_tc) {
-      tc_.layout(ar, m, n, dcap_, std::max(m, n), false);
+      tc_.layout(ar, m, n, dcap_, std::max(m, n), false, three_);
       tc_.set_profiled(true);
       // Tall d-column operands of CholeskyQR: the Gram (BF16x3) and the
       // products X R^{-1} (exact mode, six products) on the tensor cores.
@@ -87,7 +92,7 @@ class Ops {
   cudaError_t pass(bool transA, const float* A, int64_t m, int64_t n, int64_t lda, const float* X,
                    int64_t ldx, float* out, int64_t ldout, double* sumsq) {
     if (o_.precision == RQLP_PREC_BF16X3)   // the engine brackets its MMA kernel when profiling
-      return tc_.pass(transA, A, m, n, lda, X, ldx, d_, out, ldout, sumsq, info_, st_);
+      return tc_.pass(transA, A, m, n, lda, X, ldx, d_, out, ldout, sumsq, info_, st_, three_);
     const bool prof = profiling_on();
     if (prof) profile_mark_begin(st_);
     const int64_t M = transA ? n : m, K = transA ? m : n;
@@ -133,15 +138,32 @@ class Ops {
     CK(chol(slot, gate_out, nullptr, want_r));
     return tcs_.pass(false, X, rows, d_, ldx, Ri_[slot], ld_, d_, out, ldout, nullptr, info_, st_, true);
   }
-  // One CholeskyQR pass (shifted on breakdown): out = X R^{-1}. have_r0: the
-  // R factor is already in slot 0 (the probe).
-  cudaError_t orth_inter(const float* X, int64_t ldx, int64_t rows, float* out, int64_t ldout,
-                         bool have_r0 = false) {
-    if (have_r0) return apply_r0(X, ldx, rows, out, ldout);
-    if (tc_on_ && rows > (int64_t)d_) return tc_cqr(X, ldx, rows, out, ldout, 0, nullptr, false);
-    CK(gram(X, ldx, rows, nullptr));
-    CK(chol(0, nullptr, nullptr, false));
-    return trmm(X, ldx, rows, Ri_[0], out, ldout, nullptr);
+  // One CholeskyQR pass: out = X R^{-1}, and a second pass when the first
+  // Cholesky had to shift (gated on a device flag, so the launch sequence
+  // stays static). A shifted factor still spans R(X) but leaves out far from
+  // orthonormal, and the next pass over A would carry that conditioning into
+  // its small directions. X is dead afterwards (it holds the second pass's
+  // product). have_r0: the R factor is already in slot 0 (the probe) and the
+  // probe's shift flag in gates[kInterGate].
+  cudaError_t orth_inter(float* X, int64_t ldx, int64_t rows, float* out, int64_t ldout, bool have_r0 = false) {
+    int* g = &gates[kInterGate];
+    if (have_r0) {
+      CK(apply_r0(X, ldx, rows, out, ldout));
+    } else {
+      CK(cudaMemsetAsync(g, 0, sizeof(int), st_));
+      if (tc_on_ && rows > (int64_t)d_) {
+        CK(tc_cqr(X, ldx, rows, out, ldout, 0, g, false));
+      } else {
+        CK(gram(X, ldx, rows, nullptr));
+        CK(chol(0, g, nullptr, false));
+        CK(trmm(X, ldx, rows, Ri_[0], out, ldout, nullptr));
+      }
+    }
+    CK(gram(out, ldout, rows, g));
+    CK(chol(1, nullptr, g, false));
+    CK(gemm_f32_ex(false, rows, d_, d_, out, ldout, Ri_[1], ld_, X, ldx, 1, nullptr, nullptr, g, kGateSkip, true,
+                   st_));
+    return copy_matrix(rows, d_, X, ldx, out, ldout, st_, g);
   }
   // CholeskyQR2 plus a third pass gated on a shifted Cholesky (shifted
   // CholeskyQR3). X (rows x d) is overwritten; tmp holds rows x d (ld_);
@@ -189,6 +211,7 @@ class Ops {
   void* cstore_ = nullptr;
   TcEngine tc_, tcs_;
   bool tc_on_ = false;
+  bool three_ = false;
 };
 
 struct Dims {
@@ -203,11 +226,31 @@ struct Out {
   float* P; int64_t ldp;
 };
 
+// Parts per operand of the BF16X3 passes over A: the caller's choice, or
+// automatically three when the oversampling p is below 5 or m n <= 2^27.
+// Every pass rounds at ~2^-16 |A| |X| with two parts; what that does to
+// |L_ii| grows with sigma_1 / sigma_i, with the inverse of the test matrix's
+// leading block U_k^T Omega (the t = ||Omega~_2 Omega~_1^{-1}|| of Theorems
+// 1-2, section 4.1; large when that block is nearly square, p < 5), and
+// shrinks like K^(-1/2) as each entry sums more independently rounded terms.
+// Measured against the FP64 oracle, two parts missed the 1e-4 |L_ii| bound on
+// small problems (2.2e-4 at 705 x 1798, k = 41, p = 5) and at p = 0, and met
+// it at 16384^2 and 20000^2 with p >= 5; three parts met it on all of them.
+// p < 0: the oversampling is not known (one pass on its own, two parts
+// unless the size says otherwise).
+bool three_part_passes(const rqlp_opts& o, int64_t m, int64_t n, int p) {
+  if (o.precision != RQLP_PREC_BF16X3) return false;
+  if (o.bf16_parts != 0) return o.bf16_parts == 3;
+  return (p >= 0 && p < 5) || m * n <= (int64_t(1) << 27);
+}
+
 // The whole chain for one matrix. Dims.d is the widest sketch the workspace
 // serves; the learned form runs the chain at a narrower width.
 class Plan {
  public:
-  Plan(const Dims& dm, const rqlp_opts& o) : d_(dm), ops_(dm.d, o), o_(o) {}
+  Plan(const Dims& dm, const rqlp_opts& o) : d_(dm), ops_(dm.d, o), o_(o) {
+    ops_.set_three_part(three_part_passes(o, dm.m, dm.n, dm.learned ? 20 : dm.p));
+  }
 
   size_t layout(Arena& ar) {
     const int64_t ld = ops_.ld(), dd = (int64_t)d_.d * ld, tall = std::max(d_.m, d_.n);
@@ -269,7 +312,10 @@ class Plan {
   cudaError_t finish_learned(const float* A, int q, int p, const Out& out, int* info, double* diag,
                              cudaStream_t st) {
     ops_.set_d(d_.k + p);
-    if (q > 0) CK(cudaMemsetAsync(&ops_.gates[0], 0, sizeof(int), st));
+    if (q > 0) {   // the probe's shift flag gates the second intermediate pass; gates[0] the final one
+      CK(cudaMemcpyAsync(&ops_.gates[kInterGate], &ops_.gates[0], sizeof(int), cudaMemcpyDeviceToDevice, st));
+      CK(cudaMemsetAsync(&ops_.gates[0], 0, sizeof(int), st));
+    }
     return chain(A, q, out, info, diag, st, true);
   }
 
@@ -292,6 +338,18 @@ class Plan {
       CK(ops_.pass(true, A, m, n, lda, T1_, ld, Y_, ld, nullptr));    // Y = A^T Z
       if (i == q) CK(ops_.orth_final(Y_, ld, n, Pt_, ld, T1_, nullptr, 0));
       else CK(ops_.orth_inter(Y_, ld, n, Pt_, ld));
+    }
+    if (o_.literal_step5 != 0) {
+      // Algorithm 1 steps 4-5 as printed: Q = qf(A P~), then the QR of
+      // (Q^T A)^T = A^T Q (a third pass over A) gives P and R', L = R'^T.
+      // Q L P^T = Q Q^T A, so ||A - Q L P^T||^2 = ||A||^2 - ||L||^2 as well.
+      Range r("rqlp: qf(A P~), qr(A^T Q), L");
+      CK(ops_.pass(false, A, m, n, lda, Pt_, ld, Z_, ld, nullptr));
+      CK(ops_.orth_final(Z_, ld, m, out.Q, out.ldq, T1_, nullptr, 1));
+      CK(ops_.pass(true, A, m, n, lda, out.Q, out.ldq, Y_, ld, nullptr));
+      CK(ops_.orth_final(Y_, ld, n, out.P, out.ldp, T1_, Rh_, 2));
+      CK(write_L(d, Rh_, ld, out.L, out.ldl, &ops_.scal[1], st));
+      return finish_diag(ops_.scal, diag, info, st);
     }
     // (Q, R) = qr(A P~)  (Algorithm 1 step 4)
     Range r("rqlp: qr(A P~), qr(R^T), L, P");
@@ -328,7 +386,10 @@ bool valid_opts(const rqlp_opts& o) {
   if (o.precision != RQLP_PREC_FP32 && o.precision != RQLP_PREC_BF16X3) return false;
   if (o.small_fp64 != 0 && o.small_fp64 != 1) return false;
   if (o.test_stall != 0) return false;   // the hook is the batched form's only
-  for (int i = 0; i < 5; ++i)
+  if (o.bf16_parts != 0 && (o.precision != RQLP_PREC_BF16X3 || (o.bf16_parts != 2 && o.bf16_parts != 3)))
+    return false;
+  if (o.literal_step5 != 0 && o.literal_step5 != 1) return false;
+  for (int i = 0; i < 3; ++i)
     if (o.reserved[i] != 0) return false;
   return true;
 }
@@ -366,6 +427,7 @@ size_t sketch_bytes(int64_t m, int64_t n, int d, const rqlp_opts& o) {
   Arena ar;
   ar.dry = true;
   Ops ops(d, o);
+  ops.set_three_part(three_part_passes(o, m, n, -1));
   ops.layout(ar, Ops::pass_part_floats(m, n, d), o.precision == RQLP_PREC_BF16X3, m, n);
   return ar.off;
 }
@@ -506,6 +568,7 @@ rqlp_status rqlp_sketch(int trans, const float* A, int64_t m, int64_t n, int64_t
   if (workspace == nullptr || ws_bytes < need || !aligned(workspace, 256)) return RQLP_ERR_WORKSPACE;
   Arena ar = arena_over(workspace, ws_bytes);
   Ops ops(d, o);
+  ops.set_three_part(three_part_passes(o, m, n, -1));
   ops.layout(ar, Ops::pass_part_floats(m, n, d), o.precision == RQLP_PREC_BF16X3, m, n);
   ops.bind(static_cast<cudaStream_t>(stream), nullptr);
   cudaError_t e = ops.pass(trans == 1, A, m, n, lda, X, ldx, Y, ldy, nullptr);

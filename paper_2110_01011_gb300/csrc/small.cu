@@ -66,7 +66,8 @@ __global__ void finish_diag_kernel(const double* scal, double* diag, int* info) 
 }
 
 __global__ void copy_kernel(int64_t rows, int64_t cols, const float* __restrict__ X, int64_t ldx,
-                            float* __restrict__ Y, int64_t ldy) {
+                            float* __restrict__ Y, int64_t ldy, const int* __restrict__ gate) {
+  if (gate != nullptr && *gate == 0) return;
   const int64_t total = rows * cols;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
@@ -189,12 +190,43 @@ cudaError_t finish_diag(const double* scal, double* diag, int* info, cudaStream_
   return cudaGetLastError();
 }
 
+__global__ void gate_clear_batched_kernel(const SmallJob* __restrict__ jobs, int count) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < count) jobs[b].gates[jobs[b].ngates] = 0;
+}
+
+// blockIdx.y = job; the job's rows x d elements over blockIdx.x.
+__global__ void copy_gated_batched_kernel(const SmallJob* __restrict__ jobs) {
+  const SmallJob& j = jobs[blockIdx.y];
+  if (j.gates[j.ngates] == 0) return;
+  const int64_t total = j.rows * j.d;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / j.d, c = e % j.d;
+    j.Y[r * j.ldy + c] = j.X[r * j.ldx + c];
+  }
+}
+
+cudaError_t gate_clear_batched(const SmallJob* jobs, int count, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  gate_clear_batched_kernel<<<(count + 127) / 128, 128, 0, st>>>(jobs, count);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t copy_gated_batched(const SmallJob* jobs, int count, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  if (count > 65535) return cudaErrorInvalidValue;   // one grid row per job
+  copy_gated_batched_kernel<<<dim3(16, count), 256, 0, st>>>(jobs);
+  note_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t copy_matrix(int64_t rows, int64_t cols, const float* X, int64_t ldx, float* Y, int64_t ldy,
-                        cudaStream_t st) {
+                        cudaStream_t st, const int* gate) {
   int64_t total = rows * cols;
   if (total <= 0) return cudaSuccess;
   int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)sm_count() * 8);
-  copy_kernel<<<blocks, 256, 0, st>>>(rows, cols, X, ldx, Y, ldy);
+  copy_kernel<<<blocks, 256, 0, st>>>(rows, cols, X, ldx, Y, ldy, gate);
   note_launch();
   return cudaGetLastError();
 }

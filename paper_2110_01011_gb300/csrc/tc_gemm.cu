@@ -82,6 +82,10 @@ struct TcArgs {
   int* tile_cnt;             // per-tile arrival counters (zero between passes)
   const int* xlo_nonzero;    // 1 when X has a nonzero low part
   int exact;                 // 1: A and X in three parts, six products
+  int chunk;                 // k-blocks per accumulation chain in TMEM
+  int split_acc;             // 1: correction products in their own accumulator
+  int nbuf;                  // accumulator buffers (2: the epilogue overlaps the next chain)
+  int bufcols;               // TMEM columns of one buffer (npad, or 2 npad when split_acc)
   int* info;                 // status word (may be null)
   uint32_t idesc, stage_bytes, tmem_cols;
 };
@@ -164,7 +168,7 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant_
   const bool ex = a.exact != 0;
   const int nx = ex ? 3 : ((*a.xlo_nonzero) ? 2 : 1);
   constexpr uint32_t kAP = BM * BKP * 2;   // one BF16 A tile
-  constexpr int kChunk = kChunkK / BKP;
+  const int kChunk = a.chunk;
   constexpr uint32_t kRow = BKP * 2;        // bytes of a K-major row: the swizzle span
   constexpr uint32_t kSbo = 8 * kRow;       // 8-row swizzle atom of the K-major operands
   constexpr uint32_t kSw = BKP == 64 ? tc::kSwizzle128 : tc::kSwizzle64;
@@ -217,10 +221,15 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant_
     long long u = u0;
     while (u < u1 && ok) {
       const long long seg_begin = u, seg_end = chunk_end(u, u1, KB, kChunk);
-      const int ab = seg & 1;
-      if (!tc::mbar_wait(&acce[ab], (uint32_t)(((seg >> 1) & 1) ^ 1), kWaitLimit)) { ok = false; break; }
+      const int ab = seg % a.nbuf;
+      if (!tc::mbar_wait(&acce[ab], (uint32_t)(((seg / a.nbuf) & 1) ^ 1), kWaitLimit)) { ok = false; break; }
       tc::tc_fence_after();
-      const uint32_t d_tmem = tmem_base + (uint32_t)(ab * a.npad);
+      const uint32_t d_tmem = tmem_base + (uint32_t)(ab * a.bufcols);
+      // The products of the low parts are ~2^-8 of A_hi X_hi or smaller. Added
+      // into the same FP32 accumulator they lose bits to its large magnitude
+      // at every MMA; with split_acc they accumulate on their own and the
+      // epilogue adds the two sums with round-to-nearest.
+      const uint32_t d_corr = a.split_acc ? d_tmem + (uint32_t)a.npad : d_tmem;
       for (; u < seg_end; ++u, ++consumed) {
         const int stage = (int)(consumed % S);
         if (!tc::mbar_wait(&full[stage], (uint32_t)((consumed / S) & 1), kWaitLimit)) { ok = false; break; }
@@ -244,13 +253,19 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant_
           const uint64_t dxl = tc::smem_desc(xlo + ks * 32, 16, kSbo, kSw);
           const uint64_t dxl2 = tc::smem_desc(xlo2 + ks * 32, 16, kSbo, kSw);
           const uint32_t acc = (u > seg_begin || ks > 0) ? 1u : 0u;
+          // the first correction product of a chain starts d_corr when it is separate
+          const uint32_t acc_c = a.split_acc ? acc : 1u;
           tc::mma_bf16(d_tmem, dah, dxh, a.idesc, acc);
-          if (nx >= 2) tc::mma_bf16(d_tmem, dah, dxl, a.idesc, 1u);
-          tc::mma_bf16(d_tmem, dal, dxh, a.idesc, 1u);
+          if (nx >= 2) {
+            tc::mma_bf16(d_corr, dah, dxl, a.idesc, acc_c);
+            tc::mma_bf16(d_corr, dal, dxh, a.idesc, 1u);
+          } else {
+            tc::mma_bf16(d_corr, dal, dxh, a.idesc, acc_c);
+          }
           if (ex) {
-            tc::mma_bf16(d_tmem, dal2, dxh, a.idesc, 1u);
-            tc::mma_bf16(d_tmem, dah, dxl2, a.idesc, 1u);
-            tc::mma_bf16(d_tmem, dal, dxl, a.idesc, 1u);
+            tc::mma_bf16(d_corr, dal2, dxh, a.idesc, 1u);
+            tc::mma_bf16(d_corr, dah, dxl2, a.idesc, 1u);
+            tc::mma_bf16(d_corr, dal, dxl, a.idesc, 1u);
           }
         }
         tc::mma_commit(&empty[stage]);
@@ -274,16 +289,16 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant_
       const long long tb = std::max(u0, (long long)t * KB), te = std::min(u1, (long long)(t + 1) * KB);
       const bool whole = tb == (long long)t * KB && te == (long long)(t + 1) * KB;
       const bool first_chunk = seg_begin == tb, last_chunk = seg_end == te;
-      const int ab = seg & 1;
+      const int ab = seg % a.nbuf;
       // One thread waits; the verdict is shared so the four warps stay in step.
-      if (threadIdx.x == 0) *epi_ok = tc::mbar_wait(&accf[ab], (uint32_t)((seg >> 1) & 1), kWaitLimit) ? 1 : 0;
+      if (threadIdx.x == 0) *epi_ok = tc::mbar_wait(&accf[ab], (uint32_t)((seg / a.nbuf) & 1), kWaitLimit) ? 1 : 0;
       asm volatile("bar.sync 1, 128;" ::: "memory");
       if (*epi_ok == 0) {
         if (threadIdx.x == 0) post_timeout(a.info);
         break;
       }
       tc::tc_fence_after();
-      const uint32_t taddr = tmem_base + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ab * a.npad);
+      const uint32_t taddr = tmem_base + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ab * a.bufcols);
       const long long gm = (long long)t * BM + row;
       float* dst;
       int ncols;
@@ -299,6 +314,12 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant_
       for (int c0 = 0; c0 < a.npad; c0 += 16) {
         float v[16];
         tc::tmem_ld16(taddr + (uint32_t)c0, v);
+        if (a.split_acc) {
+          float w[16];
+          tc::tmem_ld16(taddr + (uint32_t)(a.npad + c0), w);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) v[i] += w[i];
+        }
         if (vec && c0 + 16 <= ncols) {
           float4* d4 = reinterpret_cast<float4*>(dst + c0);
           if (!first_chunk) {   // this thread wrote the row's earlier chunks
@@ -674,9 +695,9 @@ bool make_panel_map(CUtensorMap* map, const void* base, long long m, long long p
 }
 
 int npad_of(int d) { return (int)round_up(std::max(d, 16), 16); }
-uint32_t tmem_cols_of(int npad) {
-  uint32_t need = 2u * (uint32_t)npad, c = 32;
-  while (c < need) c <<= 1;
+uint32_t tmem_cols_of(int cols) {
+  uint32_t c = 32;
+  while (c < (uint32_t)cols) c <<= 1;
   return c;
 }
 uint32_t stage_bytes_of(int npad, bool exact, int bkp) {
@@ -846,6 +867,14 @@ cudaError_t TcEngine::pass(bool transA, const float* A, int64_t m, int64_t n, in
   }
   a.vec_out = ((reinterpret_cast<uintptr_t>(out) % 16) == 0 && ldout % 4 == 0) ? 1 : 0;
   a.exact = exact ? 1 : 0;
+  a.chunk = kChunkK / bkp;
+  // Correction products get their own accumulator where two such buffer
+  // pairs fit in TMEM's 512 columns (npad <= 128), and always in exact mode
+  // (single-buffered above npad = 128: the epilogue then holds the MMAs for
+  // the drain of each chain).
+  a.split_acc = (exact || 4 * npad_ <= 512) ? 1 : 0;
+  a.bufcols = (a.split_acc ? 2 : 1) * npad_;
+  a.nbuf = 2 * a.bufcols <= 512 ? 2 : 1;
   a.stages = stages_of(npad_, exact, bkp);
   a.out = out;
   a.ldo = ldout;
@@ -855,7 +884,7 @@ cudaError_t TcEngine::pass(bool transA, const float* A, int64_t m, int64_t n, in
   a.info = info;
   a.idesc = tc::idesc_bf16(BM, npad_, transA, false);
   a.stage_bytes = stage_bytes_of(npad_, exact, bkp);
-  a.tmem_cols = tmem_cols_of(npad_);
+  a.tmem_cols = tmem_cols_of(a.nbuf * a.bufcols);
   const bool prof = profiled_ && profiling_on();
   if (prof) profile_mark_begin(st);
   if (bkp == 64)

@@ -58,6 +58,8 @@ struct TcGJob {
   const void* mAlo;
   const void* mXhi;
   const void* mXlo;
+  const void* mAlo2;        // three-part launches: A_lo2, X_lo2 (else unused)
+  const void* mXlo2;
   float* out;
   long long ldo;
   int M, d, npad, kblocks, vec_out;
@@ -69,6 +71,7 @@ struct SplitJob {           // A (m x n) -> panels of A_hi, A_lo; sumsq += ||A||
   long long lda, m, n, npan;
   void* hi;
   void* lo;
+  void* lo2;                // bf16(A - A_hi - A_lo), or null (two parts)
   double* sumsq;
   int vec;                  // A 16-byte aligned with lda % 4 == 0
 };
@@ -78,6 +81,7 @@ struct PrepJob {            // X (K x d) -> X_hi^T, X_lo^T (d x ldk)
   int d;
   void* th;
   void* tl;
+  void* tl2;                // bf16(X - X_hi - X_lo)^T, or null (two parts)
   long long ldk;
   int* flag;
 };
@@ -90,9 +94,10 @@ cudaError_t prep_grouped(const PrepJob* jobs, const int* start, int count, int t
 // units: (job, 128-row tile) pairs; CTA c takes units cta_start[c] .. cta_start[c + 1] - 1.
 // G = 0 only configures the kernel (call before capturing).
 // stall != 0 (fault-injection tests): CTA 0 withholds its first stage's loads,
-// its bounded waits run out and `info` receives RQLP_ERR_TIMEOUT.
+// its bounded waits run out and `info` receives RQLP_ERR_TIMEOUT. exact: A and
+// X in three parts, six products (every job's third-part maps are set).
 cudaError_t tc_grouped_pass(bool transA, const TcGJob* jobs, const int2* units, const int* cta_start, int G,
-                            int npad_max, int* info, int stall, cudaStream_t st);
+                            int npad_max, int* info, int stall, bool exact, cudaStream_t st);
 // Host encoders of the tensor maps above (false when the encoder is missing
 // or rejects the arguments).
 bool tc_panel_map(void* map, const void* base, long long m, long long panels, int bi, int bo, int bp, bool sw128);

@@ -12,8 +12,8 @@
 // CTA), so no tile is split and no CTA waits for another. Inside a CTA the
 // pipeline is the single-problem pass kernel's: one TMA warp, one MMA warp
 // (tcgen05.mma, M = 128, N = the problem's round16(d), FP32 accumulators in
-// two TMEM buffers, chains cut every K = 4096), four epilogue warps. Every
-// wait is bounded.
+// two TMEM buffers, the correction products in an accumulator of their own,
+// chains cut every K = 4096), four epilogue warps. Every wait is bounded.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -44,7 +44,7 @@ template <bool MN_A>
 __global__ void __launch_bounds__(kThreads, 1)
 tc_grouped_kernel(const TcGJob* __restrict__ jobs, const int2* __restrict__ units, const int* __restrict__ cta_start,
                   int stages, uint32_t stage_bytes, uint32_t xslot, int npad_max, uint32_t tmem_cols, int* info,
-                  int stall) {
+                  int stall, int exact) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -81,6 +81,10 @@ tc_grouped_kernel(const TcGJob* __restrict__ jobs, const int2* __restrict__ unit
   __syncthreads();
   tc::tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
+  // Stage layout: A_hi, A_lo[, A_lo2] (kABytes each), then X_hi, X_lo[, X_lo2]
+  // (xslot each).
+  const bool ex = exact != 0;
+  const uint32_t xoff = (ex ? 3u : 2u) * kABytes;
 
   if (warp == 4 && lane == 0) {
     // ------------------------------------------------ TMA producer
@@ -94,7 +98,9 @@ tc_grouped_kernel(const TcGJob* __restrict__ jobs, const int2* __restrict__ unit
       const CUtensorMap* mal = static_cast<const CUtensorMap*>(j.mAlo);
       const CUtensorMap* mxh = static_cast<const CUtensorMap*>(j.mXhi);
       const CUtensorMap* mxl = static_cast<const CUtensorMap*>(j.mXlo);
-      const int nx = (*j.xlo_nonzero) ? 2 : 1;
+      const CUtensorMap* mal2 = static_cast<const CUtensorMap*>(j.mAlo2);
+      const CUtensorMap* mxl2 = static_cast<const CUtensorMap*>(j.mXlo2);
+      const int nx = ex ? 3 : ((*j.xlo_nonzero) ? 2 : 1);
       const uint32_t xb = (uint32_t)j.npad * BK * 2;
       for (int kb = 0; kb < j.kblocks; ++kb, ++issued) {
         const int stage = (int)(issued % S);
@@ -104,17 +110,20 @@ tc_grouped_kernel(const TcGJob* __restrict__ jobs, const int2* __restrict__ unit
         // it, this thread's later waits and the epilogue's run out and report.
         if (stall != 0 && blockIdx.x == 0 && issued == 0) continue;
         unsigned char* base = smem + (size_t)stage * stage_bytes;
-        tc::mbar_expect_tx(&full[stage], 2 * kABytes + (uint32_t)nx * xb);
+        tc::mbar_expect_tx(&full[stage], xoff + (uint32_t)nx * xb);
         if (MN_A) {   // 32 rows (K) of panels 2t and 2t + 1 (M)
           tc::tma_load_3d(base, mah, &full[stage], 0, kb * BK, 2 * t);
           tc::tma_load_3d(base + kABytes, mal, &full[stage], 0, kb * BK, 2 * t);
+          if (ex) tc::tma_load_3d(base + 2 * kABytes, mal2, &full[stage], 0, kb * BK, 2 * t);
         } else {      // 128 rows (M) x 32 columns (K) of panel kb / 2
           const int kx = (kb & 1) * BK, kp = kb >> 1;
           tc::tma_load_3d(base, mah, &full[stage], kx, t * BM, kp);
           tc::tma_load_3d(base + kABytes, mal, &full[stage], kx, t * BM, kp);
+          if (ex) tc::tma_load_3d(base + 2 * kABytes, mal2, &full[stage], kx, t * BM, kp);
         }
-        tc::tma_load_2d(base + 2 * kABytes, mxh, &full[stage], kb * BK, 0);
-        if (nx == 2) tc::tma_load_2d(base + 2 * kABytes + xslot, mxl, &full[stage], kb * BK, 0);
+        tc::tma_load_2d(base + xoff, mxh, &full[stage], kb * BK, 0);
+        if (nx >= 2) tc::tma_load_2d(base + xoff + xslot, mxl, &full[stage], kb * BK, 0);
+        if (nx == 3) tc::tma_load_2d(base + xoff + 2 * xslot, mxl2, &full[stage], kb * BK, 0);
       }
     }
     if (!ok) post_timeout(info);
@@ -127,35 +136,52 @@ tc_grouped_kernel(const TcGJob* __restrict__ jobs, const int2* __restrict__ unit
     bool ok = true;
     for (int ui = ub; ui < ue && ok; ++ui) {
       const TcGJob& j = jobs[units[ui].x];
-      const int nx = (*j.xlo_nonzero) ? 2 : 1;
+      const int nx = ex ? 3 : ((*j.xlo_nonzero) ? 2 : 1);
       for (int s0 = 0; s0 < j.kblocks && ok; s0 += kChunkKB) {
         const int s1 = min(j.kblocks, s0 + kChunkKB);
         const int ab = seg & 1;
         if (!tc::mbar_wait(&acce[ab], (uint32_t)(((seg >> 1) & 1) ^ 1), kWaitLimit)) { ok = false; break; }
         tc::tc_fence_after();
-        const uint32_t d_tmem = tmem_base + (uint32_t)(ab * npad_max);
+        // Buffer ab holds A_hi X_hi in its first npad_max columns and the
+        // correction products (~2^-8 of it) in the next npad_max: summed into
+        // one accumulator they would lose bits to its magnitude at every MMA.
+        const uint32_t d_tmem = tmem_base + (uint32_t)(ab * 2 * npad_max);
+        const uint32_t d_corr = d_tmem + (uint32_t)npad_max;
         for (int kb = s0; kb < s1; ++kb, ++consumed) {
           const int stage = (int)(consumed % S);
           if (!tc::mbar_wait(&full[stage], (uint32_t)((consumed / S) & 1), kWaitLimit)) { ok = false; break; }
           tc::tc_fence_after();
           const uint32_t base = tc::smem_u32(smem + (size_t)stage * stage_bytes);
-          const uint32_t ahi = base, alo = base + kABytes, xhi = base + 2 * kABytes, xlo = xhi + xslot;
+          const uint32_t ahi = base, alo = base + kABytes, alo2 = base + 2 * kABytes, xhi = base + xoff,
+                         xlo = xhi + xslot, xlo2 = xlo + xslot;
 #pragma unroll
           for (int ks = 0; ks < BK / 16; ++ks) {
-            uint64_t dah, dal;
+            uint64_t dah, dal, dal2;
             if (MN_A) {   // MN-major, 128B swizzle: 16 k-rows = two 1024-byte atoms
               dah = tc::smem_desc(ahi + ks * 2048, kABytes / 2, 1024, tc::kSwizzle128);
               dal = tc::smem_desc(alo + ks * 2048, kABytes / 2, 1024, tc::kSwizzle128);
+              dal2 = tc::smem_desc(alo2 + ks * 2048, kABytes / 2, 1024, tc::kSwizzle128);
             } else {      // K-major, 64B swizzle: 16 k-columns = 32 bytes into the row
               dah = tc::smem_desc(ahi + ks * 32, 16, 512, tc::kSwizzle64);
               dal = tc::smem_desc(alo + ks * 32, 16, 512, tc::kSwizzle64);
+              dal2 = tc::smem_desc(alo2 + ks * 32, 16, 512, tc::kSwizzle64);
             }
             const uint64_t dxh = tc::smem_desc(xhi + ks * 32, 16, 512, tc::kSwizzle64);
             const uint64_t dxl = tc::smem_desc(xlo + ks * 32, 16, 512, tc::kSwizzle64);
+            const uint64_t dxl2 = tc::smem_desc(xlo2 + ks * 32, 16, 512, tc::kSwizzle64);
             const uint32_t acc = (kb > s0 || ks > 0) ? 1u : 0u;
             tc::mma_bf16(d_tmem, dah, dxh, j.idesc, acc);
-            if (nx >= 2) tc::mma_bf16(d_tmem, dah, dxl, j.idesc, 1u);
-            tc::mma_bf16(d_tmem, dal, dxh, j.idesc, 1u);
+            if (nx >= 2) {
+              tc::mma_bf16(d_corr, dah, dxl, j.idesc, acc);
+              tc::mma_bf16(d_corr, dal, dxh, j.idesc, 1u);
+            } else {
+              tc::mma_bf16(d_corr, dal, dxh, j.idesc, acc);
+            }
+            if (ex) {   // the products above 2^-24 of the three-part operands
+              tc::mma_bf16(d_corr, dal2, dxh, j.idesc, 1u);
+              tc::mma_bf16(d_corr, dah, dxl2, j.idesc, 1u);
+              tc::mma_bf16(d_corr, dal, dxl, j.idesc, 1u);
+            }
           }
           tc::mma_commit(&empty[stage]);
         }
@@ -190,11 +216,14 @@ tc_grouped_kernel(const TcGJob* __restrict__ jobs, const int2* __restrict__ unit
           break;
         }
         tc::tc_fence_after();
-        const uint32_t taddr = tmem_base + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ab * npad_max);
+        const uint32_t taddr = tmem_base + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ab * 2 * npad_max);
         const bool first = s0 == 0;
         for (int c0 = 0; c0 < j.npad; c0 += 16) {   // uniform over the warp (collective TMEM loads)
-          float v[16];
+          float v[16], w[16];
           tc::tmem_ld16(taddr + (uint32_t)c0, v);
+          tc::tmem_ld16(taddr + (uint32_t)(npad_max + c0), w);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) v[i] += w[i];
           if (vec && c0 + 16 <= ncols) {
             float4* d4 = reinterpret_cast<float4*>(dst + c0);
             if (!first) {
@@ -248,6 +277,7 @@ split_grouped_kernel(const SplitJob* __restrict__ jobs, const int* __restrict__ 
   const bool vec = j.vec != 0;
   bf16* hi = reinterpret_cast<bf16*>(j.hi);
   bf16* lo = reinterpret_cast<bf16*>(j.lo);
+  bf16* lo2 = reinterpret_cast<bf16*>(j.lo2);
   float s = 0.f, comp = 0.f;
   for (int it = 0; it < kSplitGroups / 256; ++it) {
     const long long g = g0 + it * 256 + threadIdx.x;
@@ -265,16 +295,20 @@ split_grouped_kernel(const SplitJob* __restrict__ jobs, const int* __restrict__ 
     }
     __align__(16) bf16 h[8];
     __align__(16) bf16 l[8];
+    __align__(16) bf16 l2[8];
     float ss = 0.f;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       h[i] = __float2bfloat16_rn(x[i]);
-      l[i] = __float2bfloat16_rn(x[i] - __bfloat162float(h[i]));
+      const float r1 = x[i] - __bfloat162float(h[i]);   // exact in FP32
+      l[i] = __float2bfloat16_rn(r1);
+      l2[i] = __float2bfloat16_rn(r1 - __bfloat162float(l[i]));
       ss = fmaf(x[i], x[i], ss);
     }
     const long long o = ((c0 >> 6) * j.m + r) * 64 + (c0 & 63);
     *reinterpret_cast<uint4*>(hi + o) = *reinterpret_cast<const uint4*>(h);
     *reinterpret_cast<uint4*>(lo + o) = *reinterpret_cast<const uint4*>(l);
+    if (lo2 != nullptr) *reinterpret_cast<uint4*>(lo2 + o) = *reinterpret_cast<const uint4*>(l2);
     const float y = ss - comp, tt = s + y;
     comp = (tt - s) - y;
     s = tt;
@@ -314,15 +348,18 @@ prep_grouped_kernel(const PrepJob* __restrict__ jobs, const int* __restrict__ st
   bool any = false;
   bf16* th = reinterpret_cast<bf16*>(j.th);
   bf16* tl = reinterpret_cast<bf16*>(j.tl);
+  bf16* tl2 = reinterpret_cast<bf16*>(j.tl2);
   for (int i = ty; i < 32; i += 8) {
     const int c = c0 + i;
     const long long r = r0 + tx;
     if (c < j.d && r < j.K) {
       const float x = tile[tx][i];
       const bf16 h = __float2bfloat16_rn(x);
-      const bf16 l = __float2bfloat16_rn(x - __bfloat162float(h));
+      const float r1 = x - __bfloat162float(h);
+      const bf16 l = __float2bfloat16_rn(r1);
       th[(long long)c * j.ldk + r] = h;
       tl[(long long)c * j.ldk + r] = l;
+      if (tl2 != nullptr) tl2[(long long)c * j.ldk + r] = __float2bfloat16_rn(r1 - __bfloat162float(l));
       any |= __bfloat162float(l) != 0.f;
     }
   }
@@ -344,13 +381,16 @@ size_t smem_optin() {
 
 template <bool MN_A>
 cudaError_t launch_grouped(const TcGJob* jobs, const int2* units, const int* cta_start, int G, int npad_max,
-                           int* info, int stall, cudaStream_t st) {
+                           int* info, int stall, bool exact, cudaStream_t st) {
   const uint32_t xslot = (uint32_t)npad_max * BK * 2;
-  const uint32_t stage_bytes = 2 * kABytes + 2 * xslot;
+  const uint32_t parts = exact ? 3u : 2u;
+  const uint32_t stage_bytes = parts * kABytes + parts * xslot;
   const size_t avail = smem_optin() - 1024 - 512;
   const int S = std::max(1, std::min(kMaxStages, (int)(avail / stage_bytes)));
+  // two buffers of (main, correction) accumulators: 4 npad_max <= 512 columns (d <= 128)
+  if (4 * npad_max > 512) return cudaErrorInvalidValue;
   uint32_t tmem_cols = 32;
-  while (tmem_cols < 2u * (uint32_t)npad_max) tmem_cols <<= 1;
+  while (tmem_cols < 4u * (uint32_t)npad_max) tmem_cols <<= 1;
   static bool configured = false;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(tc_grouped_kernel<MN_A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -361,7 +401,7 @@ cudaError_t launch_grouped(const TcGJob* jobs, const int2* units, const int* cta
   if (G <= 0) return cudaSuccess;   // configuration only
   const size_t smem = (size_t)S * stage_bytes + 1024 + 512;
   tc_grouped_kernel<MN_A><<<G, kThreads, smem, st>>>(jobs, units, cta_start, S, stage_bytes, xslot, npad_max,
-                                                     tmem_cols, info, stall);
+                                                     tmem_cols, info, stall, exact ? 1 : 0);
   note_launch();
   return cudaGetLastError();
 }
@@ -437,9 +477,9 @@ cudaError_t prep_grouped(const PrepJob* jobs, const int* start, int count, int t
 }
 
 cudaError_t tc_grouped_pass(bool transA, const TcGJob* jobs, const int2* units, const int* cta_start, int G,
-                            int npad_max, int* info, int stall, cudaStream_t st) {
-  return transA ? launch_grouped<true>(jobs, units, cta_start, G, npad_max, info, stall, st)
-                : launch_grouped<false>(jobs, units, cta_start, G, npad_max, info, stall, st);
+                            int npad_max, int* info, int stall, bool exact, cudaStream_t st) {
+  return transA ? launch_grouped<true>(jobs, units, cta_start, G, npad_max, info, stall, exact, st)
+                : launch_grouped<false>(jobs, units, cta_start, G, npad_max, info, stall, exact, st);
 }
 
 }  // namespace rqlp

@@ -46,8 +46,8 @@ EXPORTED = ["rqlp_default_opts", "rqlp_workspace_bytes", "rqlp_factor", "rqlp_ho
 
 class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("small_fp64", ctypes.c_int),
-                ("test_stall", ctypes.c_int),
-                ("reserved", ctypes.c_int * 5)]
+                ("test_stall", ctypes.c_int), ("bf16_parts", ctypes.c_int),
+                ("literal_step5", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
 
 
 class Problem(ctypes.Structure):
@@ -160,11 +160,13 @@ def load(build_if_missing: bool = True):
     return lib
 
 
-def _opts(precision=PREC_FP32, small_fp64=False):
+def _opts(precision=PREC_FP32, small_fp64=False, parts=0, literal=False):
     o = Opts()
     load().rqlp_default_opts(ctypes.byref(o))
     o.precision = int(precision)
     o.small_fp64 = 1 if small_fp64 else 0
+    o.bf16_parts = int(parts)
+    o.literal_step5 = 1 if literal else 0
     return o
 
 
@@ -356,11 +358,14 @@ def _stream():
     return torch.cuda.current_stream().cuda_stream
 
 
-def factor(A, k, p, q, Omega, precision=PREC_FP32, small_fp64=False, workspace=None, out=None):
+def factor(A, k, p, q, Omega, precision=PREC_FP32, small_fp64=False, workspace=None, out=None, parts=0,
+           literal=False):
     """Factor a CUDA FP32 row-major A (m x n) with Omega (m x (k+p)).
 
     Returns (Q, L, P, info, diag) as CUDA tensors; info (int32[2]) and diag
-    (float64[4]) are filled asynchronously on the current stream.
+    (float64[4]) are filled asynchronously on the current stream. parts:
+    BF16 parts per pass operand in the BF16X3 form (0 = automatic, 2, 3).
+    literal: step 5 as Algorithm 1 prints it (QR of A^T Q, a third pass).
     """
     import torch
     m, n = A.shape
@@ -369,7 +374,7 @@ def factor(A, k, p, q, Omega, precision=PREC_FP32, small_fp64=False, workspace=N
         raise TypeError("A and Omega must be CUDA float32 tensors")
     if A.stride(1) != 1 or Omega.stride(1) != 1:
         raise ValueError("A and Omega must be row-major (unit column stride)")
-    opts = _opts(precision, small_fp64)
+    opts = _opts(precision, small_fp64, parts, literal)
     ws_bytes = rqlp_workspace_bytes(m, n, k, p, q, opts)
     if ws_bytes == 0:
         raise RqlpError(1, "rqlp_workspace_bytes")
@@ -400,12 +405,12 @@ def _workspace(nbytes, device):
     return buf, (buf.data_ptr() + 255) // 256 * 256
 
 
-def sketch(A, X, trans, precision=PREC_FP32):
+def sketch(A, X, trans, precision=PREC_FP32, parts=0):
     """Y = A^T X (trans=1) or A X (trans=0) for CUDA float32 row-major A, X."""
     import torch
     m, n = A.shape
     d = X.shape[1]
-    opts = _opts(precision)
+    opts = _opts(precision, parts=parts)
     nb = rqlp_sketch_workspace_bytes(trans, m, n, d, opts)
     if nb == 0:
         raise RqlpError(1, "rqlp_sketch_workspace_bytes")
@@ -457,14 +462,14 @@ def probe_features(A, k, Omega, target, precision=PREC_BF16X3, workspace=None):
     return feat, info
 
 
-def factor_learned(A, k, Omega, params, target, precision=PREC_BF16X3, workspace=None, out=None):
+def factor_learned(A, k, Omega, params, target, precision=PREC_BF16X3, workspace=None, out=None, parts=0):
     """Rand-QLP with the (q, p) predicted for the requested excess rank-k
     error ``target``. Returns (Q, L, P, info, diag, (q, p)); Q, L, P are views
     of k + p columns of buffers sized for k + 20."""
     import torch
     m, n = A.shape
     dmax = k + 20
-    opts = _opts(precision)
+    opts = _opts(precision, parts=parts)
     nb = rqlp_learned_workspace_bytes(m, n, k, opts)
     if nb == 0:
         raise RqlpError(1, "rqlp_learned_workspace_bytes")
@@ -488,7 +493,7 @@ def factor_learned(A, k, Omega, params, target, precision=PREC_BF16X3, workspace
     return Q[:, :d], L[:d, :d], P[:, :d], info, diag, (qp[0], qp[1])
 
 
-def factor_host(A, k, p, q, Omega, precision=PREC_FP32, workspace=None, out=None):
+def factor_host(A, k, p, q, Omega, precision=PREC_FP32, workspace=None, out=None, parts=0):
     """Host-buffer form: numpy/torch CPU float32 A and Omega (pinned for full
     bandwidth). Returns host (Q, L, P, info, diag); synchronous."""
     import torch
@@ -496,7 +501,7 @@ def factor_host(A, k, p, q, Omega, precision=PREC_FP32, workspace=None, out=None
     O_t = torch.as_tensor(Omega)
     m, n = A_t.shape
     d = k + p
-    opts = _opts(precision)
+    opts = _opts(precision, parts=parts)
     ws_bytes = rqlp_host_workspace_bytes(m, n, k, p, q, opts)
     if ws_bytes == 0:
         raise RqlpError(1, "rqlp_host_workspace_bytes")
@@ -527,9 +532,9 @@ class Batch:
     per-problem info/diag rows and the workspace with torch; ``launch()``
     replays the captured graph, ``run()`` launches the kernels one by one.
     precision: PREC_FP32, or PREC_BF16X3 (the passes over A as grouped
-    tensor-core passes over BF16 halves)."""
+    tensor-core passes over BF16 parts; parts: 0 = three, 2, 3)."""
 
-    def __init__(self, As, Omegas, ks, ps, q, small_fp64=False, precision=PREC_FP32, test_stall=False):
+    def __init__(self, As, Omegas, ks, ps, q, small_fp64=False, precision=PREC_FP32, test_stall=False, parts=0):
         import torch
         self.count = len(As)
         dev = As[0].device
@@ -548,7 +553,7 @@ class Batch:
             arr[i] = Problem(A.data_ptr(), m, n, A.stride(0), O.data_ptr(), O.stride(0), k, p, Q.data_ptr(),
                              Q.stride(0), L.data_ptr(), L.stride(0), P.data_ptr(), P.stride(0))
         self.probs = arr
-        self.opts = _opts(precision, small_fp64)
+        self.opts = _opts(precision, small_fp64, parts)
         self.opts.test_stall = 1 if test_stall else 0
         nb = rqlp_batch_workspace_bytes(self.count, arr, q, self.opts)
         if nb == 0:

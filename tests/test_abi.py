@@ -42,7 +42,7 @@ def test_host_only_calls(lib):
     assert "breakdown" in rqlp.rqlp_status_string(3).lower()
     o = rqlp.rqlp_default_opts()
     assert o.precision == rqlp.PREC_FP32 and o.small_fp64 == 0
-    assert o.test_stall == 0 and list(o.reserved) == [0] * 5
+    assert o.test_stall == 0 and o.bf16_parts == 0 and o.literal_step5 == 0 and list(o.reserved) == [0] * 3
 
 
 @pytest.mark.parametrize("m,n,k,p,q", [(0, 10, 1, 0, 0), (10, 10, 0, 1, 0), (10, 10, 8, 3, 0),
@@ -69,6 +69,25 @@ def test_bad_opts_rejected(lib):
     o = rqlp.rqlp_default_opts()
     o.precision = 7
     assert rqlp.rqlp_workspace_bytes(100, 100, 5, 5, 0, o) == 0
+    o = rqlp.rqlp_default_opts()
+    o.bf16_parts = 3                 # BF16 parts belong to the BF16X3 form only
+    assert rqlp.rqlp_workspace_bytes(100, 100, 5, 5, 0, o) == 0
+    o.precision = rqlp.PREC_BF16X3
+    for parts, ok in ((0, True), (1, False), (2, True), (3, True), (4, False)):
+        o.bf16_parts = parts
+        assert (rqlp.rqlp_workspace_bytes(100, 100, 5, 5, 0, o) > 0) == ok, parts
+    o = rqlp.rqlp_default_opts()
+    o.literal_step5 = 2
+    assert rqlp.rqlp_workspace_bytes(100, 100, 5, 5, 0, o) == 0
+    o.literal_step5 = 1
+    assert rqlp.rqlp_workspace_bytes(100, 100, 5, 5, 0, o) > 0
+    o = rqlp.rqlp_default_opts()
+    o.precision = rqlp.PREC_BF16X3
+    # the third part of A costs half as much workspace again as the two halves
+    o.bf16_parts = 2
+    two = rqlp.rqlp_workspace_bytes(1000, 1000, 5, 5, 0, o)
+    o.bf16_parts = 3
+    assert rqlp.rqlp_workspace_bytes(1000, 1000, 5, 5, 0, o) >= two + 2 * 1000 * 1024
 
 
 def test_factor_argument_errors_without_device_work(lib):

@@ -44,17 +44,21 @@ def test_invalid_batch_arguments():
     assert rqlp.rqlp_batch_workspace_bytes(1, a, 1, rqlp._opts(7)) == 0          # unknown precision
 
 
-def test_split_form_workspace_holds_the_halves():
-    """The BF16x3 batch adds A's BF16 halves (64-column panels), the pass
-    operand's halves and the tensor maps to the FP32 batch's workspace."""
+@pytest.mark.parametrize("parts", [2, 3])
+def test_split_form_workspace_holds_the_parts(parts):
+    """The BF16x3 batch adds A's BF16 parts (64-column panels), the pass
+    operand's parts and the tensor maps (8, or 12 with a third part) to the
+    FP32 batch's workspace; without bf16_parts the batch takes three."""
     a = _arr([_prob(300, 200, 20, 5), _prob(500, 100, 40, 5)])
     fp32 = rqlp.rqlp_batch_workspace_bytes(2, a, 1)
-    split = rqlp.rqlp_batch_workspace_bytes(2, a, 1, rqlp._opts(rqlp.PREC_BF16X3))
-    halves = 2 * 2 * (300 * 256 + 500 * 128)                 # A_hi + A_lo, BF16
-    xt = 2 * 2 * (25 * 304 + 45 * 504)                      # X_hi^T + X_lo^T, d x round8(max(m, n))
-    maps = 2 * 8 * 128
+    split = rqlp.rqlp_batch_workspace_bytes(2, a, 1, rqlp._opts(rqlp.PREC_BF16X3, parts=parts))
+    halves = parts * 2 * (300 * 256 + 500 * 128)             # A_hi, A_lo[, A_lo2], BF16
+    xt = parts * 2 * (25 * 304 + 45 * 504)                  # X parts^T, d x round8(max(m, n))
+    maps = 2 * (8 if parts == 2 else 12) * 128
     assert split - fp32 >= halves + xt + maps
     assert split - fp32 <= halves + xt + maps + 64 * 1024     # + the grouped passes' plan tables
+    if parts == 3:
+        assert rqlp.rqlp_batch_workspace_bytes(2, a, 1, rqlp._opts(rqlp.PREC_BF16X3)) == split
 
 
 def test_stall_hook_only_for_split_batches():
@@ -67,3 +71,14 @@ def test_stall_hook_only_for_split_batches():
     o = rqlp._opts(rqlp.PREC_FP32)
     o.test_stall = 1
     assert rqlp.rqlp_batch_workspace_bytes(1, a, 1, o) == 0
+
+
+def test_batch_option_rules():
+    """The paper-literal step 5 is a single-matrix option; BF16 parts belong to
+    the BF16x3 form (2 or 3)."""
+    a = _arr([_prob(300, 200, 20, 5)])
+    assert rqlp.rqlp_batch_workspace_bytes(1, a, 1, rqlp._opts(literal=True)) == 0
+    assert rqlp.rqlp_batch_workspace_bytes(1, a, 1, rqlp._opts(rqlp.PREC_BF16X3, parts=2)) > 0
+    assert rqlp.rqlp_batch_workspace_bytes(1, a, 1, rqlp._opts(rqlp.PREC_BF16X3, parts=3)) > 0
+    assert rqlp.rqlp_batch_workspace_bytes(1, a, 1, rqlp._opts(rqlp.PREC_BF16X3, parts=1)) == 0
+    assert rqlp.rqlp_batch_workspace_bytes(1, a, 1, rqlp._opts(rqlp.PREC_FP32, parts=2)) == 0

@@ -11,14 +11,14 @@ from parity_util import compare
 pytestmark = pytest.mark.gpu
 
 
-def _problems(count, seed, q_rate=3.0, dmax=69, sizes=((40, 500), (40, 400))):
+def _problems(count, seed, q_rate=3.0, dmax=69, sizes=((40, 500), (40, 400)), ps=(0, 3, 5)):
     g = inputs.rng(seed)
     out = []
     while len(out) < count:
         m = int(g.integers(*sizes[0]))
         n = int(g.integers(*sizes[1]))
         k = int(g.integers(1, 65))
-        p = int(g.choice([0, 3, 5]))
+        p = int(g.choice(list(ps)))
         if k + p > min(m, n) or k + p > dmax:
             continue
         sig = inputs.exp_spectrum(min(m, n), rate=max(4.0, (k + p) / q_rate))
@@ -32,14 +32,14 @@ def _problems(count, seed, q_rate=3.0, dmax=69, sizes=((40, 500), (40, 400))):
 PRECS = [0, 1]   # rqlp.PREC_FP32, rqlp.PREC_BF16X3
 
 
-def _batch(probs, q, small_fp64=False, precision=0, test_stall=False):
+def _batch(probs, q, small_fp64=False, precision=0, test_stall=False, parts=0):
     import torch
 
     from paper_2110_01011_gb300 import rqlp
     As = [torch.from_numpy(np.ascontiguousarray(A)).cuda() for A, _, _, _ in probs]
     Os = [torch.from_numpy(np.ascontiguousarray(O)).cuda() for _, O, _, _ in probs]
     b = rqlp.Batch(As, Os, [k for _, _, k, _ in probs], [p for _, _, _, p in probs], q, small_fp64=small_fp64,
-                   precision=precision, test_stall=test_stall)
+                   precision=precision, test_stall=test_stall, parts=parts)
     return b
 
 
@@ -50,17 +50,9 @@ def _results(b, i):
             b.info[i].cpu().numpy(), b.diag[i].cpu().numpy())
 
 
-# BF16x3 passes: each product carries ~2^-16 of |A| |X| (16 bits per operand),
-# so an |L_ii| near sigma_i takes up to ~2 * 2^-16 * sigma_1 / sigma_i of its
-# own size (measured on the single-problem path too: 2.7e-4 at k = 12, p = 0,
-# q = 2, sigma_1 / sigma_k = 15.6, where FP32 gives 9e-6).
-LII_SCALE = {0: None, 1: 2 * 2.0 ** -16}
-
-
 def _check_all(b, probs, q, precision=0):
     for i, (A, Om, k, p) in enumerate(probs):
-        compare(A, Om, k, p, q, _results(b, i), elem_atol=5e-4, precision=precision,
-                lii_cond_scale=LII_SCALE[precision])
+        compare(A, Om, k, p, q, _results(b, i), elem_atol=5e-4, precision=precision)
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -143,19 +135,20 @@ def test_status_rows_follow_caller_order(prec):
     assert info[4, 0] in (0, 3) and diag[4, 3] >= 1
     for i in (0, 1, 3, 5):
         assert info[i, 0] == 0 and diag[i, 3] == 0
-        compare(*probs[i][:2], probs[i][2], probs[i][3], 0, _results(b, i), elem_atol=5e-4, precision=prec,
-                lii_cond_scale=LII_SCALE[prec])
+        compare(*probs[i][:2], probs[i][2], probs[i][3], 0, _results(b, i), elem_atol=5e-4, precision=prec)
     b.close()
 
 
-def test_split_form_large_problems():
+@pytest.mark.parametrize("parts", [0, 2])
+def test_split_form_large_problems(parts):
     """BF16x3 batch with problems whose K spans more than one accumulation
-    chunk of the grouped pass (m = 4500 > 4096) and ragged tiles."""
+    chunk of the grouped pass (m = 4500 > 4096) and ragged tiles, in three
+    parts (the default) and in two on request."""
     g = []
     for (m, n, k, p, s) in [(4500, 300, 40, 5, 11), (300, 4200, 20, 5, 12), (1111, 777, 64, 5, 13)]:
         sig = inputs.exp_spectrum(min(m, n), rate=max(4.0, (k + p) / 3))
         g.append((inputs.low_rank_matrix(m, n, sig, 1e-5, seed=s), inputs.omega(m, k + p, seed=s + 9), k, p))
-    b = _batch(g, 1, precision=1)
+    b = _batch(g, 1, precision=1, parts=parts)
     b.launch()
     _check_all(b, g, 1, 1)
     b.close()
@@ -168,7 +161,7 @@ def test_withheld_stage_times_out_and_the_context_survives():
     kernel frees what it holds and returns; a normal batch afterwards is
     correct."""
     import torch
-    probs = _problems(3, seed=41)
+    probs = _problems(3, seed=41, ps=(5, 8))   # p >= 5: the passes run on the tensor cores
     b = _batch(probs, 1, precision=1, test_stall=True)
     b.launch()
     torch.cuda.synchronize()
@@ -177,4 +170,34 @@ def test_withheld_stage_times_out_and_the_context_survives():
     b = _batch(probs, 1, precision=1)
     b.launch()
     _check_all(b, probs, 1, 1)
+    b.close()
+
+
+def _ill_conditioned(kind, ratio, m, n, k, p, seed):
+    """sigma_1 / sigma_k = ratio, exponential or polynomial decay, noise 1e-6."""
+    r = min(m, n)
+    if kind == "exp":
+        sig = np.exp(-np.arange(r) * np.log(ratio) / (k - 1))
+    else:
+        sig = np.arange(1, r + 1, dtype=np.float64) ** (-np.log(ratio) / np.log(k))
+    return inputs.low_rank_matrix(m, n, sig, 1e-6, seed=seed), inputs.omega(m, k + p, seed=seed + 1)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_ill_conditioned_leading_blocks(prec):
+    """The class the two-part split once missed: k = 12, p = 0, q = 2,
+    sigma_1 / sigma_k from 15.6 to 100 (and p = 5 beside it), one batch, the
+    plain 1e-4 |L_ii| bound in both precisions (BF16x3 in three parts)."""
+    probs = []
+    s = 500
+    for kind in ("exp", "poly"):
+        for ratio in (15.6, 50.0, 100.0):
+            for p in (0, 5):
+                s += 2
+                m, n = 300 + 17 * (s % 7), 200 + 13 * (s % 5)
+                A, Om = _ill_conditioned(kind, ratio, m, n, 12, p, s)
+                probs.append((A, Om, 12, p))
+    b = _batch(probs, 2, precision=prec)
+    b.launch()
+    _check_all(b, probs, 2, prec)
     b.close()

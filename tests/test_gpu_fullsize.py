@@ -82,3 +82,27 @@ def test_e3_spectra(family, noise, prec):
     A = inputs.low_rank_matrix(n, n, inputs.e3_spectrum(family, n, 200), noise, seed=3001)
     Om = inputs.omega(n, 25, seed=3002)
     compare(A, Om, 20, 5, 1, run_gpu(A, Om, 20, 5, 1, precision=prec), precision=prec)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("kind,par,k,p,q", [("exp", 100.0, 12, 5, 2), ("poly", 1.76, 41, 5, 1)],
+                         ids=["exp-ratio100-k12-q2", "poly1.76-k41-q1"])
+def test_two_parts_at_large_size(kind, par, k, p, q):
+    """Above m n = 2^27 the split form takes two BF16 parts: 16384^2 with a
+    steep leading block (sigma_1 / sigma_k = 100, or the polynomial decay on
+    which two parts missed at 705 x 1798) meets the plain tolerances."""
+    import torch
+
+    from paper_2110_01011_gb300 import rqlp
+    n = 16384
+    r = 1000
+    sig = (np.exp(-np.arange(r) * np.log(par) / (k - 1)) if kind == "exp"
+           else np.arange(1, r + 1, dtype=np.float64) ** (-par))
+    A = inputs.low_rank_matrix_torch(n, n, sig, 1e-6, seed=9100 + k, rank=r, device="cuda")
+    Om = inputs.omega_torch(n, k + p, seed=9200 + k, device="cuda")
+    torch.cuda.synchronize()
+    out = _gpu(A, Om, k, p, q, rqlp.PREC_BF16X3)
+    A64, Om64 = A.double().cpu().numpy(), Om.double().cpu().numpy()
+    del A, Om
+    err = compare(A64, Om64, k, p, q, out, elem_atol=2e-4, precision=rqlp.PREC_BF16X3)
+    print(kind, par, {kk: float(v) for kk, v in err.items()})

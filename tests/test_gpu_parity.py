@@ -107,3 +107,40 @@ def test_deterministic():
     b = run_gpu(A, Om, 20, 5, 1)
     for x, y in zip(a[:3], b[:3]):
         assert np.array_equal(x, y)
+
+
+def _ill_conditioned(kind, ratio, m, n, k, p, seed):
+    """sigma_1 / sigma_k = ratio, exponential or polynomial decay, noise 1e-6."""
+    r = min(m, n, 1000)
+    if kind == "exp":
+        sig = np.exp(-np.arange(r) * np.log(ratio) / (k - 1))
+    else:
+        sig = np.arange(1, r + 1, dtype=np.float64) ** (-np.log(ratio) / np.log(k))
+    return inputs.low_rank_matrix(m, n, sig, 1e-6, seed=seed), inputs.omega(m, k + p, seed=seed + 1)
+
+
+@pytest.mark.parametrize("m,n", [(300, 200), (500, 500), (2000, 1500)])
+@pytest.mark.parametrize("kind", ["exp", "poly"])
+@pytest.mark.parametrize("ratio", [15.6, 50.0, 100.0])
+@pytest.mark.parametrize("p", [0, 5])
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp32", "bf16x3"])
+def test_ill_conditioned_leading_block(m, n, kind, ratio, p, prec):
+    """k = 12, q = 2 and sigma_1 / sigma_k up to 100, the class on which the
+    two-part split once missed the 1e-4 |L_ii| bound (2.7e-4 at ratio 15.6,
+    p = 0): the plain bound in both forms (BF16x3 takes three parts at these
+    sizes)."""
+    A, Om = _ill_conditioned(kind, ratio, m, n, 12, p, seed=int(m + 7 * n + 1000 * ratio) + p)
+    compare(A, Om, 12, p, 2, run_gpu(A, Om, 12, p, 2, precision=prec), elem_atol=5e-4, precision=prec)
+
+
+@pytest.mark.parametrize("parts", [2, 3])
+def test_explicit_parts(parts):
+    """Either part count on request; three parts also where two would do."""
+    A, Om = _cfg1()
+    compare(A, Om, 20, 5, 1, run_gpu(A, Om, 20, 5, 1, precision=1, parts=parts), precision=1)
+
+
+def test_three_parts_at_large_k():
+    """Three-part passes over several accumulation chains (K = 6000)."""
+    A, Om = _ill_conditioned("exp", 100.0, 6000, 6000, 12, 0, seed=6100)
+    compare(A, Om, 12, 0, 2, run_gpu(A, Om, 12, 0, 2, precision=1), elem_atol=5e-4, precision=1)
