@@ -304,20 +304,20 @@ def time_steps(ctx, fn, steps):
     return ctx.max_over_ranks(e0.elapsed_time(e1) / steps)
 
 
-def fixed_runner(a, A, Om, q, p, prec, dev):
+def fixed_runner(a, A, Om, q, p, prec, dev, small_fp64=False):
     import torch
 
     from paper_2110_01011_gb300 import rqlp
     d = a.k + p
     parts = a.parts if prec == rqlp.PREC_BF16X3 else 0
-    opts = rqlp._opts(prec, parts=parts)
+    opts = rqlp._opts(prec, small_fp64, parts=parts)
     ws = torch.empty(rqlp.rqlp_workspace_bytes(a.m, a.n, a.k, p, q, opts) + 256, dtype=torch.uint8, device=dev)
     out = (torch.empty(a.m, d, device=dev), torch.empty(d, d, device=dev), torch.empty(a.n, d, device=dev),
            torch.empty(2, dtype=torch.int32, device=dev), torch.empty(4, dtype=torch.float64, device=dev))
     Omp = Om[:, :d]
 
     def step():
-        rqlp.factor(A, a.k, p, q, Omp, precision=prec, workspace=ws, out=out, parts=parts)
+        rqlp.factor(A, a.k, p, q, Omp, precision=prec, small_fp64=small_fp64, workspace=ws, out=out, parts=parts)
     return step, out
 
 
@@ -340,36 +340,83 @@ def learned_runner(a, A, Om, params, target, prec, dev):
     return step, res
 
 
-def roofline(a, recs, d, prec, peaks, dev):
+def pass_products(prec, three_part, x_has_low=True):
+    """BF16 MMA products per element pair of a split-form pass: six with three
+    parts; with two, three (two when X is BF16-exact, e.g. a rounded Omega)."""
+    if prec == 0:
+        return 1
+    if three_part:
+        return 6
+    return 3 if x_has_low else 2
+
+
+def three_part_auto(a, p):
+    """The library's automatic part count (three when p < 5 or m n <= 2^27)."""
+    if a.parts:
+        return a.parts == 3
+    return p < 5 or a.m * a.n <= (1 << 27)
+
+
+def roofline(a, recs, d, prec, peaks, dev, three_part, q, ms_step):
+    """Roofline of the dominant kernel (the pass over A that takes the most
+    time, per launch, against the burst peak: each launch runs alone inside
+    the step) and of the whole chain (the slower of A's bytes over HBM and the
+    passes' MMA flops at the tensor peak, against the step time)."""
     import torch
 
     from paper_2110_01011_gb300 import rqlp
     by_tag = {0: [r[0] for r in recs if r[1] == 0], 1: [r[0] for r in recs if r[1] == 1]}
     dom = max(by_tag, key=lambda t: sum(by_tag[t]))
     pass_ms = statistics.mean(by_tag[dom]) if by_tag[dom] else float("nan")
+    npad = max(16, -(-d // 16) * 16)
     flops = 2.0 * a.m * a.n * d
     sm_max = peaks.get("sm_max_mhz", 2070.0)
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
     kname = {0: "pass_AX", 1: "pass_AtX"}[dom]
     sha = kernel_sha(prec)
+    hbm = peaks.get("hbm_gbs", 6761.6)
+    burst = peaks.get("bf16_tflops", 1889.1)
+    sust = peaks.get("bf16_tflops_sustained", 1683.0)
     if prec == rqlp.PREC_FP32:
         peak = nsm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
         roof = {"bound": "alu", "achieved": flops / (pass_ms * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
                 "peak_source": f"derived: {nsm} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz",
                 "flops_per_launch": flops}
     else:
-        # Three BF16 products per pass (A_hi X_hi + A_hi X_lo + A_lo X_hi).
-        peak = peaks.get("bf16_tflops_sustained", 1683.0)
-        roof = {"bound": "tensor", "achieved": 3 * flops / (pass_ms * 1e-3) / 1e12, "peak": peak,
-                "unit": "TFLOP/s", "flops_per_launch": 3 * flops,
-                "peak_source": "MEASURED_PEAKS bf16_tflops_sustained (of measured)"}
+        # MMA flops as issued: N = round16(d) columns, products per element pair
+        mma = pass_products(prec, three_part) * 2.0 * a.m * a.n * npad
+        roof = {"bound": "tensor", "achieved": mma / (pass_ms * 1e-3) / 1e12, "peak": burst,
+                "unit": "TFLOP/s", "flops_per_launch": mma,
+                "peak_source": "MEASURED_PEAKS bf16_tflops (burst, of measured)",
+                "frac_of_sustained": mma / (pass_ms * 1e-3) / 1e12 / sust}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = traffic_for(f"{kname}_{'fp32' if prec == 0 else 'bf16x3'}", sha)
     roof["kernel"] = kname
     roof["launch_ms"] = pass_ms
     roof["launches_timed"] = len(by_tag[dom])
-    roof["hbm_gbs"] = a.m * a.n * 4 / (pass_ms * 1e-3) / 1e9
-    roof["hbm_frac_of_measured"] = roof["hbm_gbs"] / peaks.get("hbm_gbs", 6761.6)
+    part_bytes = 4 if prec == 0 else (6 if three_part else 4)
+    roof["hbm_gbs"] = a.m * a.n * part_bytes / (pass_ms * 1e-3) / 1e9
+    roof["hbm_frac_of_measured"] = roof["hbm_gbs"] / hbm
+    # the chain: 2q + 2 passes over A
+    npass = 2 * q + 2
+    chain_bytes = npass * a.m * a.n * part_bytes
+    if prec == rqlp.PREC_FP32:
+        chain_flops = npass * flops
+        t_flops = chain_flops / (roof["peak"] * 1e12)
+        peak_name = "derived FP32"
+        t_flops_s = t_flops
+    else:
+        # the sketch multiplies a BF16-exact Omega (two products with two parts)
+        chain_flops = (pass_products(prec, three_part, False) + (npass - 1) * pass_products(prec, three_part)) \
+            * 2.0 * a.m * a.n * npad
+        t_flops = chain_flops / (burst * 1e12)
+        t_flops_s = chain_flops / (sust * 1e12)
+        peak_name = "measured bf16 burst (sustained beside it)"
+    t_bytes = chain_bytes / (hbm * 1e9)
+    roof_ms, roof_ms_s = 1e3 * max(t_bytes, t_flops), 1e3 * max(t_bytes, t_flops_s)
+    roof["chain"] = {"passes": npass, "A_bytes": chain_bytes, "mma_flops": chain_flops,
+                     "roofline_ms": roof_ms, "bound": "hbm" if t_bytes >= t_flops else "tensor",
+                     "frac": roof_ms / ms_step, "frac_sustained": roof_ms_s / ms_step, "peak": peak_name}
     return roof, sha
 
 
@@ -402,16 +449,29 @@ def batched_leg(a, ctx):
         res = {"ms_per_batch": ms, "value": ctx.world * abytes / (ms * 1e-3) / 1e9, "unit": "GB/s",
                "problems_per_s": ctx.world * len(probs) / (ms * 1e-3), "graph_kernels": launches, "tuning": tune,
                "nonzero_status": bad}
+        # leading-k diagonals of L for the agreement check between the forms
+        diags[prec] = [torch.diagonal(b.L[i])[:probs[i].k].double().cpu() for i in range(len(probs))]
+        orth = [float(torch.linalg.norm(b.Q[i].double().T @ b.Q[i].double()
+                                        - torch.eye(probs[i].d, dtype=torch.float64, device=ctx.dev)))
+                for i in range(min(32, len(probs)))]
+        res["max_orth_Q_first32"] = max(orth)
         b.close()
         return res
 
     runs = {}
+    diags = {}
     if a.batched_precision in ("both", "bf16x3"):
         runs["bf16x3"] = one(rqlp.PREC_BF16X3)
     if a.batched_precision in ("both", "fp32"):
         runs["fp32"] = one(rqlp.PREC_FP32)
     head = "bf16x3" if "bf16x3" in runs else "fp32"
     out = dict(runs[head])
+    if len(diags) == 2:
+        # Parity with the FP64 oracle is a GPU test (the bench's first 32
+        # problems); here the two forms are checked against each other.
+        rel = [float(((diags[1][i] - diags[0][i]).abs() / diags[0][i].abs()).max()) for i in range(len(probs))]
+        out["agreement"] = {"max_rel_Lii_diff_bf16x3_vs_fp32": max(rel),
+                            "median_rel_Lii_diff": statistics.median(rel), "problems": len(rel)}
     out.update({"problems": len(probs), "A_bytes_per_batch": abytes, "generate_s": gen_s, "precision": head,
                 "workload": f"{len(probs)} problems, m in [256,4096], n in [256,2048], k in [8,64], p=5, q={q}, "
                             "half exp / half poly spectra"})
@@ -424,46 +484,34 @@ def batched_leg(a, ctx):
 
 
 def e2e_learned(a, ctx, A, Om, params, target, prec, steps, warmup):
-    """End to end through the public API: pinned host A and Omega copied in,
-    rqlp_factor_learned, Q, L, P copied back, every step."""
+    """End to end through the public C ABI with host buffers:
+    rqlp_factor_learned_host takes pinned host A and Omega, copies A by row
+    blocks while the probe sketch runs on the blocks that have landed, factors,
+    and copies Q, L, P back, every step."""
     import torch
 
     from paper_2110_01011_gb300 import rqlp
-    dev = ctx.dev
     w = a.k + 20
     hA, hO = A.cpu().pin_memory(), Om.cpu().pin_memory()
-    dA, dO = torch.empty_like(A), torch.empty_like(Om)
-    hQ, hL, hP = (torch.empty(a.m, w).pin_memory(), torch.empty(w, w).pin_memory(), torch.empty(a.n, w).pin_memory())
-    nb = rqlp.rqlp_learned_workspace_bytes(a.m, a.n, a.k, rqlp._opts(prec))
-    ws = torch.empty(nb + 256, dtype=torch.uint8, device=dev)
-    out = (torch.empty(a.m, w, device=dev), torch.empty(w, w, device=dev), torch.empty(a.n, w, device=dev),
-           torch.empty(2, dtype=torch.int32, device=dev), torch.empty(4, dtype=torch.float64, device=dev))
-
-    def step():
-        dA.copy_(hA, non_blocking=True)
-        dO.copy_(hO, non_blocking=True)
-        Q, L, P, info, diag, qp = rqlp.factor_learned(dA, a.k, dO, params, target, precision=prec, workspace=ws,
-                                                      out=out)
-        # The factors are the leading d columns of the k + 20 wide output
-        # buffers: one contiguous copy per buffer (the caller reads [:, :d]).
-        hQ.copy_(out[0], non_blocking=True)
-        hL.copy_(out[1], non_blocking=True)
-        hP.copy_(out[2], non_blocking=True)
-        torch.cuda.current_stream().synchronize()
-        return qp
-
+    out = (torch.empty(a.m, w).pin_memory(), torch.empty(w, w).pin_memory(), torch.empty(a.n, w).pin_memory(),
+           torch.zeros(2, dtype=torch.int32), torch.zeros(4, dtype=torch.float64))
+    nb = rqlp.rqlp_learned_host_workspace_bytes(a.m, a.n, a.k, rqlp._opts(prec))
+    ws = torch.empty(nb + 256, dtype=torch.uint8, device=ctx.dev)
+    qp = None
     for _ in range(max(1, warmup)):
-        qp = step()
+        qp = rqlp.factor_learned_host(hA, a.k, hO, params, target, precision=prec, workspace=ws, out=out)[5]
     ctx.barrier()
     t0 = time.perf_counter()
     for _ in range(steps):
-        qp = step()
+        qp = rqlp.factor_learned_host(hA, a.k, hO, params, target, precision=prec, workspace=ws, out=out)[5]
     ctx.barrier()
     dt = ctx.max_over_ranks((time.perf_counter() - t0) / steps)
+    d = a.k + qp[1]
     h2d = 4 * (a.m * a.n + a.m * w)
-    d2h = 4 * (a.m * w + w * w + a.n * w)
+    d2h = 4 * (a.m * d + d * d + a.n * d) + 8 + 32 + 8
     return {"value": ctx.world * (2 * qp[0] + 2) * a.m * a.n * 4 / dt / 1e9, "unit": "GB/s", "ms_per_step": dt * 1e3,
-            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "api": "rqlp_factor_learned + pinned copies"}
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "qp": list(qp),
+            "api": "rqlp_factor_learned_host"}
 
 
 def e2e_fixed(a, ctx, A, Om, q, p, prec, steps, warmup):
@@ -586,7 +634,8 @@ def main():
     d = a.k + p_used
     abytes = (2 * q_used + 2) * a.m * a.n * 4
     value = world * abytes / (ms_step * 1e-3) / 1e9
-    roof, sha = roofline(a, recs, d, prec, peaks, dev)
+    roof, sha = roofline(a, recs, d, prec, peaks, dev, prec == rqlp.PREC_BF16X3 and three_part_auto(a, p_used),
+                         q_used, ms_step)
 
     compare.update({"form": ("learned_" if form == "learned" else "fixed_") + ("fp32" if prec == 0 else "bf16x3"),
                     "qp": [q_used, p_used], **acc(out[2])})
@@ -604,6 +653,33 @@ def main():
         compare["bf16x3_fixed_excess_error"] = acc16["excess_error"]
         compare["bf16x3_fixed_rel_residual"] = acc16["rel_residual"]
         del s16, o16
+        torch.cuda.empty_cache()
+        # FP64 d x d factors (Cholesky and the QR of R^T) on the same split form
+        s64, o64 = fixed_runner(a, A, Om, 2, 10, rqlp.PREC_BF16X3, dev, small_fp64=True)
+        s64()
+        ctx.barrier()
+        compare["bf16x3_fixed_small_fp64_ms_per_step"] = time_steps(ctx, s64, 3)
+        del s64, o64
+        torch.cuda.empty_cache()
+        # the bench matrix's excess errors for every (q, p) (one width-(k + 20)
+        # FP32 chain, FP64 residuals) and the network's picks across requests
+        tab = learn.eps_table(A, Om, a.k, tail2(a))
+        compare["eps_table"] = {f"q{q_}_p{p_}": float(tab[qi][pi]) for qi, q_ in enumerate(learn.Q_CHOICES)
+                                for pi, p_ in enumerate(learn.P_CHOICES)}
+        sweep = []
+        for t in sorted({0.1, 0.05, 0.03, float(target), 0.015, 0.01}, reverse=True):
+            stp, rs = learned_runner(a, A, Om, params, t, prec, dev)
+            stp()
+            ctx.barrier()
+            ms_t = time_steps(ctx, stp, 3)
+            qt, pt = rs["qp"]
+            bq, bp = learn.label_from_table(tab, a.k, t)
+            sweep.append({"request": t, "qp": [qt, pt], "table_eps": float(tab[learn.Q_CHOICES.index(qt)]
+                                                                           [learn.P_CHOICES.index(pt)]),
+                          "ms_per_step": ms_t, "cheapest_feasible": [learn.Q_CHOICES[bq], learn.P_CHOICES[bp]]
+                          if tab[bq][bp] <= t else None})
+            del stp, rs
+        compare["request_sweep"] = sweep
         torch.cuda.empty_cache()
     if learned_note:
         compare["learned"] = learned_note

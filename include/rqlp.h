@@ -214,47 +214,53 @@ rqlp_status rqlp_orth(float* X, int64_t rows, int d, int64_t ldx, float* R, int6
 /* ---- Learned (q, p) (no counterpart in the paper, which fixes neither q nor
  * p). A probe sketch Y_w = A^T Omega_w of width w = k + 20 (the widest sketch
  * any p in {5, 10, 20} needs) has its R factor computed (FP32 Gram and
- * Cholesky in both precisions); 12 statistics of its R-diagonal plus
- * log10(target) (13 floats) feed a 3-layer MLP (13 -> 64 -> 64 -> 8, ReLU)
- * whose two heads pick q in {0, 1, 2, 3, 4} and p in {5, 10, 20}: the pass
- * count and oversampling expected to reach the requested excess rank-k error
- *   target >= ||A - A P_k P_k^T||_F / (sum_{i>k} sigma_i^2)^(1/2) - 1
- * at least cost (2q + 2)(k + p). The probe is the first sketch of the chain
- * and its R factor the chain's first orthonormalisation, so prediction costs
- * no extra pass over A. A failed probe (non-zero d_info status or non-finite
- * logits) falls back to q = 2, p = 10.
+ * Cholesky in both precisions); 12 statistics of its R-diagonal feed a
+ * 3-layer MLP (12 -> 64 -> 64 -> 15, ReLU) whose 15 outputs estimate, for
+ * every (q, p) with q in {0, 1, 2, 3, 4} and p in {5, 10, 20} (output
+ * 3 qi + pi), log10 of the excess rank-k error
+ *   eps = ||A - A P_k P_k^T||_F / (sum_{i>k} sigma_i^2)^(1/2) - 1
+ * that the chain with that (q, p) reaches. The prediction for a request
+ * `target` is the cheapest pair, by cost (2q + 2)(k + p), whose estimate plus
+ * the network's calibrated margin delta is at most log10(target) (ties:
+ * smaller q, then smaller p); (4, 20) when no pair qualifies. The probe is the
+ * first sketch of the chain and its R factor the chain's first
+ * orthonormalisation, so prediction costs no extra pass over A. A failed
+ * probe (non-zero d_info status) or a non-finite estimate falls back to
+ * q = 2, p = 10.
  *
- * Parameters: RQLP_MLP_PARAMS floats, device, layout W1 (13 x 64 row-major),
- * b1 (64), W2 (64 x 64), b2 (64), W3 (64 x 8), b3 (8); logits 0..4 = q head,
- * 5..7 = p head. target: 0 < target < 1, else RQLP_ERR_ARG. */
-#define RQLP_MLP_FEATURES 13
+ * Parameters: RQLP_MLP_PARAMS floats, device, layout W1 (12 x 64 row-major),
+ * b1 (64), W2 (64 x 64), b2 (64), W3 (64 x 15), b3 (15), delta (1, log10
+ * units; set by calibration on held-out data, its gradient is 0). target:
+ * 0 < target < 1, else RQLP_ERR_ARG. */
+#define RQLP_MLP_FEATURES 12
 #define RQLP_MLP_HIDDEN 64
-#define RQLP_MLP_PARAMS 5576
+#define RQLP_MLP_OUTPUTS 15
+#define RQLP_MLP_PARAMS 5968
 
-/* Forward pass: logits (batch x 8) of features X (batch x 13), device. */
-rqlp_status rqlp_mlp_forward(const float* params, const float* X, int batch, float* logits,
+/* Forward pass: estimates (batch x 15) of features X (batch x 12), device. */
+rqlp_status rqlp_mlp_forward(const float* params, const float* X, int batch, float* est,
                              void* stream);
-/* Mean cross-entropy of both heads and its gradient (RQLP_MLP_PARAMS floats)
- * for labels yq in 0..4, yp in 0..2 (device int arrays). loss: 1 device float
- * (may be NULL). workspace: rqlp_mlp_workspace_bytes(batch) bytes, device.
- * Deterministic (fixed summation order). */
+/* Mean over the batch and the 15 outputs of (estimate - Y)^2 and its gradient
+ * (RQLP_MLP_PARAMS floats, 0 for delta) for targets Y (batch x 15, device;
+ * log10 of the measured errors). loss: 1 device float (may be NULL).
+ * workspace: rqlp_mlp_workspace_bytes(batch) bytes, device. Deterministic
+ * (fixed summation order). */
 size_t rqlp_mlp_workspace_bytes(int batch);
-rqlp_status rqlp_mlp_grad(const float* params, const float* X, const int* yq, const int* yp,
-                          int batch, float* grad, float* loss, void* workspace, size_t ws_bytes,
+rqlp_status rqlp_mlp_grad(const float* params, const float* X, const float* Y, int batch,
+                          float* grad, float* loss, void* workspace, size_t ws_bytes,
                           void* stream);
 /* One Adam step (step is 1-based) on n parameters with moments m1, m2. */
 rqlp_status rqlp_mlp_adam(float* params, const float* grad, float* m1, float* m2, int n,
                           float lr, float beta1, float beta2, float eps, int step, void* stream);
 
-/* Probe features (13 device floats, the last log10(target)) of A (m x n)
- * with Omega (m x (k+20)). Workspace: rqlp_learned_workspace_bytes(...).
- * d_info as for rqlp_factor. */
+/* Probe features (12 device floats) of A (m x n) with Omega (m x (k+20)).
+ * Workspace: rqlp_learned_workspace_bytes(...). d_info as for rqlp_factor. */
 size_t rqlp_learned_workspace_bytes(int64_t m, int64_t n, int k, const rqlp_opts* opts);
 rqlp_status rqlp_probe_features(const float* A, int64_t m, int64_t n, int64_t lda, int k,
-                                const float* Omega, int64_t ldo, double target, float* feat,
+                                const float* Omega, int64_t ldo, float* feat,
                                 void* workspace, size_t ws_bytes, int* d_info,
                                 const rqlp_opts* opts, void* stream);
-/* Probe + MLP + argmax: d_qp (2 device ints) receives (q, p). */
+/* Probe + MLP + selection: d_qp (2 device ints) receives (q, p). */
 rqlp_status rqlp_predict_qp(const float* A, int64_t m, int64_t n, int64_t lda, int k,
                             const float* Omega, int64_t ldo, double target, const float* params,
                             int* d_qp, void* workspace, size_t ws_bytes, int* d_info,
@@ -268,6 +274,31 @@ rqlp_status rqlp_factor_learned(const float* A, int64_t m, int64_t n, int64_t ld
                                 float* Q, int64_t ldq, float* L, int64_t ldl, float* P, int64_t ldp,
                                 void* workspace, size_t ws_bytes, int* d_info, double* d_diag,
                                 int* h_qp, const rqlp_opts* opts, void* stream);
+
+/* Host-buffer form of rqlp_factor_learned: A (m x n, lda), Omega
+ * (m x (k+20), ldo), Q, L, P are HOST pointers (pinned memory gives full copy
+ * bandwidth; params stays a device pointer). A and Omega are copied to the
+ * device by row blocks on two copy streams that the library owns (created on
+ * the first call on each device), and each block's share of the probe
+ * sketch, A_b^T Omega_b, starts as soon as the block has landed, so the copy
+ * of A overlaps its first pass over A; the shares are summed in FP32 in
+ * block order (the sketch can therefore differ from rqlp_factor_learned's in
+ * the last bits). Then features, (q, p) (read back: one synchronisation), the
+ * chain, and the factors' copy back; returns after the stream has been
+ * synchronised, error returns included. Calls on one device are serialised.
+ * workspace (device) must hold rqlp_learned_host_workspace_bytes(...) bytes;
+ * h_info (2 ints), h_diag (4 doubles, may be NULL) and h_qp (2 ints) are host
+ * arrays. Q, L, P receive k + p columns (their buffers need room for k + 20).
+ * The copy/compute overlap is this library's; the factorisation is
+ * Algorithm 1 as in rqlp_factor_learned. */
+size_t rqlp_learned_host_workspace_bytes(int64_t m, int64_t n, int k, const rqlp_opts* opts);
+rqlp_status rqlp_factor_learned_host(const float* hA, int64_t m, int64_t n, int64_t lda, int k,
+                                     const float* hOmega, int64_t ldo, double target,
+                                     const float* params, float* hQ, int64_t ldq,
+                                     float* hL, int64_t ldl, float* hP, int64_t ldp,
+                                     void* workspace, size_t ws_bytes, int* h_info,
+                                     double* h_diag, int* h_qp, const rqlp_opts* opts,
+                                     void* stream);
 
 /* ---- Batched form: many independent problems, each with its own sizes,
  * k, p and buffers (one q for the batch), factored by the chain of
@@ -331,6 +362,41 @@ rqlp_status rqlp_batch_destroy(rqlp_batch batch);
 rqlp_status rqlp_factor_batched(int count, const rqlp_problem* probs, int q, void* workspace,
                                 size_t ws_bytes, int* d_info, double* d_diag, const rqlp_opts* opts,
                                 void* stream);
+
+/* ---- Evaluation utilities on the device (section 5.2: rank-r
+ * approximations; section 4.1, Theorem 2: distances between subspaces).
+ *
+ * rqlp_rank_errors: errs[r - 1] = ||A - A_r||_F for r = 1..d, where
+ *   A_r = Q L(:, 1:r) P(:, 1:r)^T, from the factors of rqlp_factor: this
+ *   chain's A_r is A P_r P_r^T (Q L P^T = A P~ P~^T), so ||A - A_r||_F^2 =
+ *   ||A||_F^2 - ||L(:, 1:r)||_F^2 with ||A||_F^2 = d_diag[0] (device, from
+ *   rqlp_factor). L (d x d, device, ldl), errs: d device doubles.
+ * rqlp_rank_residual: *out = ||A - Q L(:, 1:r) P(:, 1:r)^T||_F computed
+ *   explicitly (one pass over A, FP32 products, FP64 sums; 1 device double),
+ *   for checking the identity or factors that did not come from this chain.
+ *   workspace: rqlp_rank_residual_workspace_bytes(m, r), 256-byte aligned.
+ * rqlp_subspace_angles: for orthonormal X (rows x a, ldx) and Y (rows x b,
+ *   ldy), device, out (b device doubles, largest first) receives the sines
+ *   of the canonical angles between R(Y) and R(X) -- the singular values of
+ *   (I - X X^T) Y; out[0] is the distance sin theta of Theorem 2 when a = b
+ *   -- or, with cosines = 1, the singular values of X^T Y (out[0] =
+ *   ||X^T Y||_2, the form of the sin phi bounds with Y the trailing columns
+ *   of Q or P). The b x b Gram of that matrix is formed in FP64 and its
+ *   eigenvalues found by cyclic Jacobi on one CTA (a check, not a fast path):
+ *   sines resolve down to ~1e-7 of FP32 input. workspace:
+ *   rqlp_subspace_workspace_bytes(rows, a, b), 256-byte aligned.
+ * All three are stream-ordered; sizes out of range return RQLP_ERR_ARG. */
+rqlp_status rqlp_rank_errors(const float* L, int64_t ldl, int d, const double* d_diag, double* errs,
+                             void* stream);
+size_t rqlp_rank_residual_workspace_bytes(int64_t m, int r);
+rqlp_status rqlp_rank_residual(const float* A, int64_t m, int64_t n, int64_t lda,
+                               const float* Q, int64_t ldq, const float* L, int64_t ldl, int d,
+                               const float* P, int64_t ldp, int r, double* out,
+                               void* workspace, size_t ws_bytes, void* stream);
+size_t rqlp_subspace_workspace_bytes(int64_t rows, int a, int b);
+rqlp_status rqlp_subspace_angles(const float* X, int64_t rows, int a, int64_t ldx,
+                                 const float* Y, int b, int64_t ldy, int cosines, double* out,
+                                 void* workspace, size_t ws_bytes, void* stream);
 
 /* ---- Runtime services (host only; no device memory).
  *

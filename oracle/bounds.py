@@ -23,7 +23,7 @@ from __future__ import annotations
 
 import numpy as np
 
-__all__ = ["omega_ratio", "theorem1", "theorem2", "theorem3", "subspace_sin"]
+__all__ = ["omega_ratio", "theorem1", "theorem2", "theorem3", "subspace_sin", "subspace_sines", "subspace_cosines"]
 
 
 def omega_ratio(U, Omega, k):
@@ -62,3 +62,22 @@ def subspace_sin(X, Y):
     """dist(R(X), R(Y)) for orthonormal X, Y of equal column count: the sine
     of the largest canonical angle, ||X_perp^T Y||_2 = ||(I - X X^T) Y||_2."""
     return float(np.linalg.norm(Y - X @ (X.T @ Y), 2))
+
+
+def subspace_sines(X, Y):
+    """Sines of the canonical angles between R(Y) and R(X) for orthonormal X
+    (rows x a) and Y (rows x b), largest first: the singular values of
+    (I - X X^T) Y (section 4.1, the distances of Theorem 2). The largest is
+    ``subspace_sin`` when a = b."""
+    X = np.asarray(X, dtype=np.float64)
+    Y = np.asarray(Y, dtype=np.float64)
+    return np.linalg.svd(Y - X @ (X.T @ Y), compute_uv=False)
+
+
+def subspace_cosines(X, Y):
+    """Singular values of X^T Y, largest first (the cosines of the canonical
+    angles; their largest is ||X^T Y||_2, the form of Theorem 2's sin phi
+    bounds with Y the trailing columns of Q or P)."""
+    X = np.asarray(X, dtype=np.float64)
+    Y = np.asarray(Y, dtype=np.float64)
+    return np.linalg.svd(X.T @ Y, compute_uv=False)

@@ -34,7 +34,7 @@ from __future__ import annotations
 import numpy as np
 
 __all__ = ["householder_qr", "qf", "rand_qlp", "rand_qlp_literal", "rand_qlp_full",
-           "residual_fro", "rank_r_error_fro", "RQLPResult"]
+           "residual_fro", "rank_r_error_fro", "rank_r_errors", "RQLPResult"]
 
 
 def householder_qr(X):
@@ -160,3 +160,14 @@ def rank_r_error_fro(A, Q, L, P, r):
     A = np.asarray(A, dtype=np.float64)
     Ar = (Q @ L[:, :r]) @ P[:, :r].T
     return float(np.linalg.norm(A - Ar))
+
+
+def rank_r_errors(A, L):
+    """||A - A_r||_F for r = 1..d from the identity of reading C9: for this
+    chain A_r = Q L(:, 1:r) P(:, 1:r)^T = A P_r P_r^T (section 5.2), so
+    ||A - A_r||_F^2 = ||A||_F^2 - ||L(:, 1:r)||_F^2."""
+    A = np.asarray(A, dtype=np.float64)
+    L = np.asarray(L, dtype=np.float64)
+    nA2 = float((A * A).sum())
+    col2 = (L * L).sum(axis=0)
+    return np.sqrt(np.maximum(nA2 - np.cumsum(col2), 0.0))

@@ -135,19 +135,22 @@ cudaError_t write_L(int d, const float* Rh, int64_t ldrh, float* L, int64_t ldl,
                     cudaStream_t st);
 cudaError_t init_scratch(int* info, int* gates, int ngates, double* scal, int nscal, cudaStream_t st);
 cudaError_t finish_diag(const double* scal, double* diag, int* info, cudaStream_t st);
+// Y += X (rows x cols).
+cudaError_t add_matrix(int64_t rows, int64_t cols, const float* X, int64_t ldx, float* Y, int64_t ldy,
+                       cudaStream_t st);
 // gate (optional): *gate == 0 -> no copy.
 cudaError_t copy_matrix(int64_t rows, int64_t cols, const float* X, int64_t ldx, float* Y, int64_t ldy,
                         cudaStream_t st, const int* gate = nullptr);
 
 // ---------------------------------------------------------------- learned (q, p)
 size_t mlp_workspace_floats(int batch);
-cudaError_t mlp_forward(const float* prm, const float* X, int batch, float* logits, cudaStream_t st);
-cudaError_t mlp_grad(const float* prm, const float* X, const int* yq, const int* yp, int batch, float* grad,
-                     float* loss, void* ws, cudaStream_t st);
+cudaError_t mlp_forward(const float* prm, const float* X, int batch, float* est, cudaStream_t st);
+cudaError_t mlp_grad(const float* prm, const float* X, const float* Y, int batch, float* grad, float* loss,
+                     void* ws, cudaStream_t st);
 cudaError_t mlp_adam(float* prm, const float* g, float* m1, float* m2, int n, float lr, float beta1, float beta2,
                      float eps, int step, cudaStream_t st);
-cudaError_t probe_features(const float* R, int64_t ldr, int w, int k, int64_t mn, double target, float* feat,
-                           cudaStream_t st);
-cudaError_t predict_qp(const float* logits, const int* info, int* qp, cudaStream_t st);
+cudaError_t probe_features(const float* R, int64_t ldr, int w, int k, int64_t mn, float* feat, cudaStream_t st);
+cudaError_t predict_qp(const float* est, const float* prm, const int* info, double target, int k, int* qp,
+                       cudaStream_t st);
 
 }  // namespace rqlp

@@ -1,14 +1,17 @@
-// Learned (q, p) predictor: a 3-layer MLP (F = 13 -> 64 -> 64 -> 8, ReLU)
-// with two softmax heads (5 logits for q in {0..4}, 3 for p in {5, 10, 20}),
-// trained with cross-entropy and Adam, plus the features of a probe sketch
-// and the argmax that turns logits into (q, p).
+// Learned (q, p) predictor: a 3-layer MLP (F = 12 -> 64 -> 64 -> 15, ReLU)
+// whose 15 outputs estimate log10 of the excess rank-k error that each
+// (q, p), q in {0..4}, p in {5, 10, 20}, would reach (pair j = 3 qi + pi),
+// trained by mean squared error with Adam; the features of a probe sketch;
+// and the selection that turns the estimates into (q, p): the cheapest pair,
+// by cost (2q + 2)(k + p), whose estimate plus a calibrated margin delta
+// stays within the request.
 //
 // Parameter layout (flat FP32): W1 (F x H, row-major), b1 (H), W2 (H x H),
-// b2 (H), W3 (H x 8), b3 (8).
+// b2 (H), W3 (H x 15), b3 (15), delta (1, log10 units; its gradient is 0).
 //
 // Training step = mlp_sample_kernel<true> (one CTA of H threads per sample:
-// forward, softmax, per-sample backward quantities) + mlp_grad_reduce_kernel
-// (one thread per parameter summing the per-sample terms in sample order, so
+// forward and per-sample backward quantities) + mlp_grad_reduce_kernel (one
+// thread per parameter summing the per-sample terms in sample order, so
 // gradients are deterministic) + adam_kernel.
 #include <cmath>
 
@@ -19,9 +22,10 @@ namespace {
 
 constexpr int F = RQLP_MLP_FEATURES;
 constexpr int H = RQLP_MLP_HIDDEN;
-constexpr int NQ = 5, NP = 3, NO = NQ + NP;
+constexpr int NQ = 5, NP = 3, NO = RQLP_MLP_OUTPUTS;
+static_assert(NO == NQ * NP, "one output per (q, p)");
 constexpr int OFF_W1 = 0, OFF_B1 = OFF_W1 + F * H, OFF_W2 = OFF_B1 + H, OFF_B2 = OFF_W2 + H * H;
-constexpr int OFF_W3 = OFF_B2 + H, OFF_B3 = OFF_W3 + H * NO, NPARAM = OFF_B3 + NO;
+constexpr int OFF_W3 = OFF_B2 + H, OFF_B3 = OFF_W3 + H * NO, OFF_DELTA = OFF_B3 + NO, NPARAM = OFF_DELTA + 1;
 static_assert(NPARAM == RQLP_MLP_PARAMS, "parameter count");
 
 __device__ const int kQChoices[NQ] = {0, 1, 2, 3, 4};
@@ -34,9 +38,9 @@ struct SampleBufs {
 
 template <bool BACKWARD>
 __global__ void __launch_bounds__(H)
-mlp_sample_kernel(const float* __restrict__ prm, const float* __restrict__ X, int B, const int* __restrict__ yq,
-                  const int* __restrict__ yp, float* __restrict__ logits, SampleBufs sb) {
-  __shared__ float x[F], h1[H], h2[H], lg[NO], d3[NO], dz2[H];
+mlp_sample_kernel(const float* __restrict__ prm, const float* __restrict__ X, int B, const float* __restrict__ Y,
+                  float* __restrict__ est, SampleBufs sb) {
+  __shared__ float x[F], h1[H], h2[H], d3[NO], dz2[H], sq[NO];
   const int t = threadIdx.x;
   for (int b = blockIdx.x; b < B; b += gridDim.x) {
     if (t < F) x[t] = X[(int64_t)b * F + t];
@@ -53,30 +57,21 @@ mlp_sample_kernel(const float* __restrict__ prm, const float* __restrict__ X, in
     if (t < NO) {
       float o = prm[OFF_B3 + t];
       for (int j = 0; j < H; ++j) o += h2[j] * prm[OFF_W3 + j * NO + t];
-      lg[t] = o;
-      if (!BACKWARD) logits[(int64_t)b * NO + t] = o;
+      if (!BACKWARD) est[(int64_t)b * NO + t] = o;
+      if (BACKWARD) {
+        // d(mean of squares)/d(estimate) for this sample's output t
+        const float r = o - Y[(int64_t)b * NO + t];
+        d3[t] = 2.f * r / (float)(B * NO);
+        sq[t] = r * r;
+      }
     }
     __syncthreads();
     if (BACKWARD) {
       if (t == 0) {
-        // softmax of each head, d3 = (softmax - onehot) / B, per-sample loss
-        float loss = 0.f;
-        for (int head = 0; head < 2; ++head) {
-          const int o0 = head == 0 ? 0 : NQ, no = head == 0 ? NQ : NP;
-          const int y = head == 0 ? yq[b] : yp[b];
-          float mx = lg[o0];
-          for (int o = 1; o < no; ++o) mx = fmaxf(mx, lg[o0 + o]);
-          float se = 0.f;
-          for (int o = 0; o < no; ++o) se += expf(lg[o0 + o] - mx);
-          for (int o = 0; o < no; ++o) {
-            const float s = expf(lg[o0 + o] - mx) / se;
-            d3[o0 + o] = (s - (o == y ? 1.f : 0.f)) / (float)B;
-          }
-          loss += logf(se) + mx - lg[o0 + y];
-        }
-        sb.loss[b] = loss;
+        float s = 0.f;
+        for (int o = 0; o < NO; ++o) s += sq[o];
+        sb.loss[b] = s / (float)NO;
       }
-      __syncthreads();
       if (t < NO) sb.d3[(int64_t)b * NO + t] = d3[t];
       float dh2 = 0.f;
 #pragma unroll
@@ -121,10 +116,10 @@ __global__ void mlp_grad_reduce_kernel(const float* __restrict__ X, int B, Sampl
   } else if (i < OFF_B3) {
     const int h = (i - OFF_W3) / NO, o = (i - OFF_W3) % NO;
     for (int b = 0; b < B; ++b) s += sb.h2[(int64_t)b * H + h] * sb.d3[(int64_t)b * NO + o];
-  } else {
+  } else if (i < OFF_DELTA) {
     const int o = i - OFF_B3;
     for (int b = 0; b < B; ++b) s += sb.d3[(int64_t)b * NO + o];
-  }
+  }   // delta: 0 (set by calibration)
   grad[i] = s;
 }
 
@@ -141,10 +136,10 @@ __global__ void adam_kernel(float* __restrict__ prm, const float* __restrict__ g
   prm[i] -= lr * (a / c1) / (sqrtf(v / c2) + eps);
 }
 
-// Features of the probe R-diagonal (R w x w upper, ldr) followed by
-// log10(target): see probe_features in the FP64 reference. One warp.
+// Features of the probe R-diagonal (R w x w upper, ldr): see probe_features
+// in the FP64 reference. One warp.
 __global__ void probe_features_kernel(const float* __restrict__ R, int64_t ldr, int w, int k, int64_t mn,
-                                      float log_target, float* __restrict__ feat) {
+                                      float* __restrict__ feat) {
   __shared__ float lr[RQLP_MAX_D];
   const int t = threadIdx.x;
   const float r0 = R[0];
@@ -182,26 +177,35 @@ __global__ void probe_features_kernel(const float* __restrict__ R, int64_t ldr, 
     feat[9] = log10f((float)k);
     feat[10] = log10f((float)mn);
     feat[11] = (float)k / (float)mn;
-    feat[12] = log_target;
   }
 }
 
-// (q, p) = (Q[argmax of the q head], P[argmax of the p head]) for one sample;
-// (2, 10) when the probe failed (status != 0) or a logit is not finite.
-__global__ void predict_kernel(const float* __restrict__ logits, const int* __restrict__ info,
-                               int* __restrict__ qp) {
-  bool ok = info == nullptr || info[0] == 0;
-  for (int o = 0; o < NO; ++o) ok = ok && isfinite(logits[o]);
+// (q, p) for one sample: the cheapest pair (cost (2q + 2)(k + p); ties
+// smaller q, then smaller p) with est + delta <= log10(target); (4, 20) when
+// none qualifies; (2, 10) when the probe failed (status != 0) or an estimate
+// or delta is not finite.
+__global__ void predict_kernel(const float* __restrict__ est, const float* __restrict__ prm, const int* __restrict__ info,
+                               float log_target, int k, int* __restrict__ qp) {
+  const float delta = prm[OFF_DELTA];
+  bool ok = (info == nullptr || info[0] == 0) && isfinite(delta);
+  for (int o = 0; o < NO; ++o) ok = ok && isfinite(est[o]);
   if (!ok) {
     qp[0] = 2;
     qp[1] = 10;
     return;
   }
-  int bq = 0, bp = 0;
-  for (int o = 1; o < NQ; ++o)
-    if (logits[o] > logits[bq]) bq = o;
-  for (int o = 1; o < NP; ++o)
-    if (logits[NQ + o] > logits[NQ + bp]) bp = o;
+  int bq = NQ - 1, bp = NP - 1;
+  long long best = -1;
+  for (int qi = 0; qi < NQ; ++qi)
+    for (int pi = 0; pi < NP; ++pi) {
+      if (est[qi * NP + pi] + delta > log_target) continue;
+      const long long c = (long long)(2 * kQChoices[qi] + 2) * (k + kPChoices[pi]);
+      if (best < 0 || c < best) {   // the loops run q, then p, upwards: the first minimum wins ties
+        best = c;
+        bq = qi;
+        bp = pi;
+      }
+    }
   qp[0] = kQChoices[bq];
   qp[1] = kPChoices[bp];
 }
@@ -222,18 +226,18 @@ SampleBufs carve(void* ws, int B) {
 
 size_t mlp_workspace_floats(int B) { return (size_t)B * (4 * H + NO + 1); }
 
-cudaError_t mlp_forward(const float* prm, const float* X, int B, float* logits, cudaStream_t st) {
+cudaError_t mlp_forward(const float* prm, const float* X, int B, float* est, cudaStream_t st) {
   const int blocks = std::min(B, sm_count() * 8);
-  mlp_sample_kernel<false><<<blocks, H, 0, st>>>(prm, X, B, nullptr, nullptr, logits, SampleBufs{});
+  mlp_sample_kernel<false><<<blocks, H, 0, st>>>(prm, X, B, nullptr, est, SampleBufs{});
   note_launch();
   return cudaGetLastError();
 }
 
-cudaError_t mlp_grad(const float* prm, const float* X, const int* yq, const int* yp, int B, float* grad,
-                     float* loss, void* ws, cudaStream_t st) {
+cudaError_t mlp_grad(const float* prm, const float* X, const float* Y, int B, float* grad, float* loss, void* ws,
+                     cudaStream_t st) {
   SampleBufs sb = carve(ws, B);
   const int blocks = std::min(B, sm_count() * 8);
-  mlp_sample_kernel<true><<<blocks, H, 0, st>>>(prm, X, B, yq, yp, nullptr, sb);
+  mlp_sample_kernel<true><<<blocks, H, 0, st>>>(prm, X, B, Y, nullptr, sb);
   note_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -250,15 +254,15 @@ cudaError_t mlp_adam(float* prm, const float* g, float* m1, float* m2, int n, fl
   return cudaGetLastError();
 }
 
-cudaError_t probe_features(const float* R, int64_t ldr, int w, int k, int64_t mn, double target, float* feat,
-                           cudaStream_t st) {
-  probe_features_kernel<<<1, 32, 0, st>>>(R, ldr, w, k, mn, (float)std::log10(target), feat);
+cudaError_t probe_features(const float* R, int64_t ldr, int w, int k, int64_t mn, float* feat, cudaStream_t st) {
+  probe_features_kernel<<<1, 32, 0, st>>>(R, ldr, w, k, mn, feat);
   note_launch();
   return cudaGetLastError();
 }
 
-cudaError_t predict_qp(const float* logits, const int* info, int* qp, cudaStream_t st) {
-  predict_kernel<<<1, 1, 0, st>>>(logits, info, qp);
+cudaError_t predict_qp(const float* est, const float* prm, const int* info, double target, int k, int* qp,
+                       cudaStream_t st) {
+  predict_kernel<<<1, 1, 0, st>>>(est, prm, info, (float)std::log10(target), k, qp);
   note_launch();
   return cudaGetLastError();
 }

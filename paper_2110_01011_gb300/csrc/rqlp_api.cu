@@ -14,6 +14,7 @@
 // launch sequence is static and capturable.
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 
 #include "common.cuh"
 #include "tc_gemm.cuh"
@@ -99,6 +100,23 @@ class Ops {
     cudaError_t e = gemm_f32_ex(transA, M, d_, K, A, lda, X, ldx, out, ldout, gemm_f32_splits(M, d_, K), part_,
                                 sumsq, nullptr, kGateNone, false, st_);
     if (prof) profile_mark_end(st_, transA ? 1 : 0);
+    return e;
+  }
+  // out (n x d) = A(r0 .. r0 + rows - 1, :)^T X (X: those rows), A m x n on
+  // the device; first: rows start at 0 (the split of A begins). ||A||_F^2 of
+  // the rows rides along into scal[0].
+  cudaError_t pass_rows(const float* A, int64_t m, int64_t n, int64_t lda, int64_t r0, int64_t rows,
+                        const float* X, int64_t ldx, float* out, int64_t ldout) {
+    if (o_.precision == RQLP_PREC_BF16X3) {
+      if (r0 == 0) CK(tc_.begin_split(A, m, n, st_));
+      CK(tc_.split_rows(A + r0 * lda, r0, rows, lda, &scal[0], st_));
+      return tc_.pass_k(true, r0, rows, X, ldx, d_, out, ldout, info_, st_, three_);
+    }
+    const bool prof = profiling_on();
+    if (prof) profile_mark_begin(st_);
+    cudaError_t e = gemm_f32_ex(true, n, d_, rows, A + r0 * lda, lda, X, ldx, out, ldout,
+                                gemm_f32_splits(n, d_, rows), part_, &scal[0], nullptr, kGateNone, false, st_);
+    if (prof) profile_mark_end(st_, 1);
     return e;
   }
   static size_t pass_part_floats(int64_t m, int64_t n, int d) {
@@ -226,6 +244,35 @@ struct Out {
   float* P; int64_t ldp;
 };
 
+// Copy streams and events of the host-ingest entry points: created on first
+// use per device and kept for the life of the process (host-side objects; no
+// device memory).
+constexpr int kIngestBlocks = 16;
+struct IngestStreams {
+  std::mutex busy;   // one host-ingest call per device at a time
+  cudaStream_t copy[2];
+  cudaEvent_t start;
+  cudaEvent_t landed[kIngestBlocks];
+};
+IngestStreams* ingest_streams() {
+  static std::mutex mu;
+  static IngestStreams* per_dev[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(mu);
+  if (per_dev[dev] == nullptr) {
+    IngestStreams* io = new IngestStreams();
+    bool ok = cudaStreamCreateWithFlags(&io->copy[0], cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&io->copy[1], cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&io->start, cudaEventDisableTiming) == cudaSuccess;
+    for (int i = 0; ok && i < kIngestBlocks; ++i)
+      ok = cudaEventCreateWithFlags(&io->landed[i], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) return nullptr;   // (the handles created so far are left to the process)
+    per_dev[dev] = io;
+  }
+  return per_dev[dev];
+}
+
 // Parts per operand of the BF16X3 passes over A: the caller's choice, or
 // automatically three when the oversampling p is below 5 or m n <= 2^27.
 // Every pass rounds at ~2^-16 |A| |X| with two parts; what that does to
@@ -264,7 +311,7 @@ class Plan {
     Ts2_ = ar.take<float>(dd);
     Ph_ = ar.take<float>(dd);
     feat_ = ar.take<float>(RQLP_MLP_FEATURES);
-    logits_ = ar.take<float>(8);
+    logits_ = ar.take<float>(RQLP_MLP_OUTPUTS);
     qp_ = ar.take<int>(2);
     // Split-K partial buffers for every width this plan may run at.
     size_t part = 0;
@@ -287,8 +334,9 @@ class Plan {
     return chain(A, d_.q, out, info, diag, st);
   }
 
-  // Probe sketch of the full width, its R factor, features, MLP and (q, p),
-  // all on the device. params == nullptr stops after the features.
+  // Probe sketch of the full width, its R factor, features, the network's
+  // error estimates and (q, p), all on the device. params == nullptr stops
+  // after the features.
   cudaError_t probe(const float* A, const float* Om, double target, const float* params, int* info,
                     cudaStream_t st) {
     Range r("rqlp: probe sketch, features, (q, p)");
@@ -297,13 +345,52 @@ class Plan {
     ops_.set_d(d_.d);
     CK(ops_.pass(true, A, d_.m, d_.n, d_.lda, Om, d_.ldo, Y_, ops_.ld(), &ops_.scal[0]));
     CK(ops_.gram_chol(Y_, ops_.ld(), d_.n));
-    CK(probe_features(ops_.R(0), ops_.ld(), d_.d, d_.k, std::min(d_.m, d_.n), target, feat_, st));
+    CK(probe_features(ops_.R(0), ops_.ld(), d_.d, d_.k, std::min(d_.m, d_.n), feat_, st));
     if (params == nullptr) return cudaSuccess;
     CK(mlp_forward(params, feat_, 1, logits_, st));
-    return predict_qp(logits_, info, qp_, st);
+    return predict_qp(logits_, params, info, target, d_.k, qp_, st);
   }
   const float* features() const { return feat_; }
   const int* qp() const { return qp_; }
+
+  // The probe with A and Omega arriving from host memory: row blocks are
+  // copied on the library's copy streams and each block's share of the
+  // sketch, A_b^T Omega_b, runs as soon as it has landed (the sum over blocks
+  // in FP32, in block order), so the copy of A overlaps its first pass.
+  // dA (m x n, ld n) and dOm (m x ldo) receive the copies.
+  cudaError_t probe_from_host(float* dA, float* dOm, int64_t ldo, const float* hA, int64_t hlda, const float* hOm,
+                              int64_t hldo, double target, const float* params, int* info, cudaStream_t st) {
+    Range r("rqlp: host ingest, probe sketch, features, (q, p)");
+    ops_.bind(st, info);
+    CK(ops_.init());
+    ops_.set_d(d_.d);
+    const int64_t m = d_.m, n = d_.n, ld = ops_.ld();
+    IngestStreams* io = ingest_streams();
+    if (io == nullptr) return cudaErrorInitializationError;
+    const int nb = (int)std::min<int64_t>(kIngestBlocks, std::max<int64_t>(1, cdiv(m, 2048)));
+    const int64_t brows = round_up(cdiv(m, nb), 64);
+    const size_t F = sizeof(float);
+    // the copy streams start after the work already on `st`
+    CK(cudaEventRecord(io->start, st));
+    for (int c = 0; c < 2; ++c) CK(cudaStreamWaitEvent(io->copy[c], io->start, 0));
+    int b = 0;
+    for (int64_t r0 = 0; r0 < m; r0 += brows, ++b) {
+      const int64_t rows = std::min(brows, m - r0);
+      cudaStream_t cs = io->copy[b & 1];
+      CK(cudaMemcpy2DAsync(dA + r0 * n, n * F, hA + r0 * hlda, hlda * F, n * F, rows, cudaMemcpyHostToDevice, cs));
+      CK(cudaMemcpy2DAsync(dOm + r0 * ldo, ldo * F, hOm + r0 * hldo, hldo * F, d_.d * F, rows,
+                           cudaMemcpyHostToDevice, cs));
+      CK(cudaEventRecord(io->landed[b], cs));
+      CK(cudaStreamWaitEvent(st, io->landed[b], 0));
+      float* dst = r0 == 0 ? Y_ : T1_;
+      CK(ops_.pass_rows(dA, m, n, n, r0, rows, dOm + r0 * ldo, ldo, dst, ld));
+      if (r0 > 0) CK(add_matrix(n, d_.d, T1_, ld, Y_, ld, st));
+    }
+    CK(ops_.gram_chol(Y_, ld, n));
+    CK(probe_features(ops_.R(0), ld, d_.d, d_.k, std::min(m, n), feat_, st));
+    CK(mlp_forward(params, feat_, 1, logits_, st));
+    return predict_qp(logits_, params, info, target, d_.k, qp_, st);
+  }
 
   // Continue from the probe with the predicted (q, p): the probe's first
   // k + p columns are the sketch A^T Omega_{k+p}.
@@ -615,14 +702,12 @@ rqlp_status rqlp_mlp_forward(const float* params, const float* X, int batch, flo
                                                                                                  : RQLP_ERR_CUDA;
 }
 
-rqlp_status rqlp_mlp_grad(const float* params, const float* X, const int* yq, const int* yp, int batch,
-                          float* grad, float* loss, void* workspace, size_t ws_bytes, void* stream) {
-  if (params == nullptr || X == nullptr || yq == nullptr || yp == nullptr || grad == nullptr || batch <= 0)
-    return RQLP_ERR_ARG;
+rqlp_status rqlp_mlp_grad(const float* params, const float* X, const float* Y, int batch, float* grad, float* loss,
+                          void* workspace, size_t ws_bytes, void* stream) {
+  if (params == nullptr || X == nullptr || Y == nullptr || grad == nullptr || batch <= 0) return RQLP_ERR_ARG;
   if (workspace == nullptr || ws_bytes < rqlp_mlp_workspace_bytes(batch) || !aligned(workspace, 16))
     return RQLP_ERR_WORKSPACE;
-  return mlp_grad(params, X, yq, yp, batch, grad, loss, workspace, static_cast<cudaStream_t>(stream)) ==
-                 cudaSuccess
+  return mlp_grad(params, X, Y, batch, grad, loss, workspace, static_cast<cudaStream_t>(stream)) == cudaSuccess
              ? RQLP_OK
              : RQLP_ERR_CUDA;
 }
@@ -679,10 +764,11 @@ static rqlp_status probe_common(const float* A, int64_t m, int64_t n, int64_t ld
 }
 
 rqlp_status rqlp_probe_features(const float* A, int64_t m, int64_t n, int64_t lda, int k, const float* Omega,
-                                int64_t ldo, double target, float* feat, void* workspace, size_t ws_bytes,
-                                int* d_info, const rqlp_opts* opts, void* stream) {
+                                int64_t ldo, float* feat, void* workspace, size_t ws_bytes, int* d_info,
+                                const rqlp_opts* opts, void* stream) {
   if (feat == nullptr) return RQLP_ERR_ARG;
-  return probe_common(A, m, n, lda, k, Omega, ldo, target, nullptr, feat, nullptr, workspace, ws_bytes, d_info,
+  // no request is involved in the features; any valid one passes the check
+  return probe_common(A, m, n, lda, k, Omega, ldo, 0.5, nullptr, feat, nullptr, workspace, ws_bytes, d_info,
                       opts, stream);
 }
 
@@ -721,6 +807,83 @@ rqlp_status rqlp_factor_learned(const float* A, int64_t m, int64_t n, int64_t ld
   h_qp[1] = qp[1];
   Out out{Q, ldq, L, ldl, P, ldp};
   return pl.finish_learned(A, qp[0], qp[1], out, d_info, d_diag, st) == cudaSuccess ? RQLP_OK : RQLP_ERR_CUDA;
+}
+
+size_t rqlp_learned_host_workspace_bytes(int64_t m, int64_t n, int k, const rqlp_opts* opts) {
+  const size_t core = rqlp_learned_workspace_bytes(m, n, k, opts);
+  if (core == 0) return 0;
+  const int64_t w = k + 20, ld = round_up(w, 4);
+  Arena ar;
+  ar.dry = true;
+  ar.take<float>((size_t)(m * n));       // A
+  ar.take<float>((size_t)(m * ld));      // Omega
+  ar.take<float>((size_t)(m * ld));      // Q
+  ar.take<float>((size_t)(w * ld));      // L
+  ar.take<float>((size_t)(n * ld));      // P
+  ar.take<int>(RQLP_INFO_INTS);
+  ar.take<double>(RQLP_DIAG_DOUBLES);
+  return round_up((int64_t)ar.off, 256) + core;
+}
+
+rqlp_status rqlp_factor_learned_host(const float* hA, int64_t m, int64_t n, int64_t lda, int k, const float* hOmega,
+                                     int64_t ldo, double target, const float* params, float* hQ, int64_t ldq,
+                                     float* hL, int64_t ldl, float* hP, int64_t ldp, void* workspace,
+                                     size_t ws_bytes, int* h_info, double* h_diag, int* h_qp,
+                                     const rqlp_opts* opts, void* stream) {
+  rqlp_opts o = resolve(opts);
+  if (!valid_opts(o) || !valid_learned(m, n, k) || !valid_target(target) || hA == nullptr || hOmega == nullptr ||
+      params == nullptr || hQ == nullptr || hL == nullptr || hP == nullptr || h_info == nullptr || h_qp == nullptr)
+    return RQLP_ERR_ARG;
+  const int64_t w = k + 20, ld = round_up(w, 4);
+  if (lda < n || ldo < w || ldq < w || ldl < w || ldp < w) return RQLP_ERR_ARG;
+  if (o.precision == RQLP_PREC_BF16X3 && !tc_supported(nullptr, 0, nullptr, 0)) return RQLP_ERR_UNSUPPORTED;
+  const size_t need = rqlp_learned_host_workspace_bytes(m, n, k, &o);
+  if (workspace == nullptr || ws_bytes < need || !aligned(workspace, 256)) return RQLP_ERR_WORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  IngestStreams* io = ingest_streams();
+  if (io == nullptr) return RQLP_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(io->busy);
+  Arena ar = arena_over(workspace, ws_bytes);
+  float* A = ar.take<float>((size_t)(m * n));
+  float* Om = ar.take<float>((size_t)(m * ld));
+  float* Q = ar.take<float>((size_t)(m * ld));
+  float* L = ar.take<float>((size_t)(w * ld));
+  float* P = ar.take<float>((size_t)(n * ld));
+  int* info = ar.take<int>(RQLP_INFO_INTS);
+  double* diag = ar.take<double>(RQLP_DIAG_DOUBLES);
+  const size_t off = (size_t)round_up((int64_t)ar.off, 256);
+  Arena core = arena_over(static_cast<char*>(workspace) + off, ws_bytes - off);
+  Dims dm = learned_dims(m, n, n, k, ld);
+  Plan pl(dm, o);
+  pl.layout(core);
+  // Once a copy from the caller's host buffers is enqueued, every return
+  // waits for the device first (the copies run on the library's streams).
+  auto fail = [](rqlp_status s) {
+    (void)cudaDeviceSynchronize();
+    return s;
+  };
+  if (pl.probe_from_host(A, Om, ld, hA, lda, hOmega, ldo, target, params, info, st) != cudaSuccess)
+    return fail(RQLP_ERR_CUDA);
+  int qp[2] = {-1, -1};
+  if (cudaMemcpyAsync(qp, pl.qp(), sizeof(qp), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return fail(RQLP_ERR_CUDA);
+  if (qp[0] < 0 || qp[0] > 4 || (qp[1] != 5 && qp[1] != 10 && qp[1] != 20)) return fail(RQLP_ERR_CUDA);
+  h_qp[0] = qp[0];
+  h_qp[1] = qp[1];
+  const int64_t d = k + qp[1];
+  Out out{Q, ld, L, ld, P, ld};
+  const size_t F = sizeof(float);
+  if (pl.finish_learned(A, qp[0], qp[1], out, info, diag, st) != cudaSuccess ||
+      cudaMemcpy2DAsync(hQ, ldq * F, Q, ld * F, d * F, m, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaMemcpy2DAsync(hL, ldl * F, L, ld * F, d * F, d, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaMemcpy2DAsync(hP, ldp * F, P, ld * F, d * F, n, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaMemcpyAsync(h_info, info, RQLP_INFO_INTS * sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      (h_diag != nullptr &&
+       cudaMemcpyAsync(h_diag, diag, RQLP_DIAG_DOUBLES * sizeof(double), cudaMemcpyDeviceToHost, st) !=
+           cudaSuccess))
+    return fail(RQLP_ERR_CUDA);
+  return cudaStreamSynchronize(st) == cudaSuccess ? RQLP_OK : fail(RQLP_ERR_CUDA);
 }
 
 const char* rqlp_status_string(int status) {

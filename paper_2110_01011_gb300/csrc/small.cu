@@ -221,6 +221,26 @@ cudaError_t copy_gated_batched(const SmallJob* jobs, int count, cudaStream_t st)
   return cudaGetLastError();
 }
 
+__global__ void add_kernel(int64_t rows, int64_t cols, const float* __restrict__ X, int64_t ldx,
+                           float* __restrict__ Y, int64_t ldy) {
+  const int64_t total = rows * cols;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / cols, c = e % cols;
+    Y[r * ldy + c] += X[r * ldx + c];
+  }
+}
+
+cudaError_t add_matrix(int64_t rows, int64_t cols, const float* X, int64_t ldx, float* Y, int64_t ldy,
+                       cudaStream_t st) {
+  const int64_t total = rows * cols;
+  if (total <= 0) return cudaSuccess;
+  const int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)sm_count() * 8);
+  add_kernel<<<blocks, 256, 0, st>>>(rows, cols, X, ldx, Y, ldy);
+  note_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t copy_matrix(int64_t rows, int64_t cols, const float* X, int64_t ldx, float* Y, int64_t ldy,
                         cudaStream_t st, const int* gate) {
   int64_t total = rows * cols;

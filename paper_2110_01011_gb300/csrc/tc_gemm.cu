@@ -73,6 +73,7 @@ constexpr int kChunkK = 4096;
 
 struct TcArgs {
   int M, K, d, npad, kblocks, tiles, G, stages;
+  int k0;                    // A^T X over A's rows k0 .. k0 + K - 1 (X holds those rows); 0 otherwise
   int tpc;                   // > 0: whole tiles per CTA (no split tiles); 0: stream-K
   int vec_out;               // out rows are 16-byte aligned (float4 stores)
   long long units;
@@ -196,9 +197,10 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant_
       tc::mbar_expect_tx(&full[stage], xoff + (uint32_t)nx * xbytes);
       // A maps are 3-D over the panel layout: {column in panel, row, panel}.
       if (MN_A) {   // 64 rows (K) of panels 2t and 2t + 1 (M), one box
-        tc::tma_load_3d(base, &tmAhi, &full[stage], 0, kb * BKP, 2 * t);
-        tc::tma_load_3d(base + kAP, &tmAlo, &full[stage], 0, kb * BKP, 2 * t);
-        if (ex) tc::tma_load_3d(base + 2 * kAP, &tmAlo2, &full[stage], 0, kb * BKP, 2 * t);
+        const int kr = a.k0 + kb * BKP;
+        tc::tma_load_3d(base, &tmAhi, &full[stage], 0, kr, 2 * t);
+        tc::tma_load_3d(base + kAP, &tmAlo, &full[stage], 0, kr, 2 * t);
+        if (ex) tc::tma_load_3d(base + 2 * kAP, &tmAlo2, &full[stage], 0, kr, 2 * t);
       } else {      // 128 rows (M) x BKP columns (K) of panel kb BKP / 64
         const int kx = (kb * BKP) & 63, kp = (kb * BKP) >> 6;
         tc::tma_load_3d(base, &tmAhi, &full[stage], kx, t * BM, kp);
@@ -561,9 +563,10 @@ __global__ void tc_gram_reduce_kernel(const float* __restrict__ part, int G, int
 // A (m x n FP32) -> A_hi, A_lo (BF16) and ||A||_F^2, in 64-column panels:
 // element (r, c) at ((c / 64) m + r) 64 + c % 64, columns n..npan*64-1 zero.
 // lo2 (optional) receives bf16(A - A_hi - A_lo); both differences are exact in FP32.
+// Rows row0 .. row0 + m - 1 of a matrix of mstride rows (the panel height).
 __global__ void split_a_kernel(const float* __restrict__ A, long long m, long long n, long long lda, bool vec,
                                bf16* __restrict__ hi, bf16* __restrict__ lo, bf16* __restrict__ lo2, long long npan,
-                               double* sumsq) {
+                               double* sumsq, long long mstride, long long row0) {
   const long long cpr = npan * 8, total = m * cpr;
   float s = 0.f, comp = 0.f;
   for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
@@ -591,7 +594,7 @@ __global__ void split_a_kernel(const float* __restrict__ A, long long m, long lo
       l2[i] = __float2bfloat16_rn(r1 - __bfloat162float(l[i]));
       ss = fmaf(x[i], x[i], ss);
     }
-    const long long o = ((c0 >> 6) * m + r) * 64 + (c0 & 63);
+    const long long o = ((c0 >> 6) * mstride + row0 + r) * 64 + (c0 & 63);
     *reinterpret_cast<uint4*>(hi + o) = *reinterpret_cast<const uint4*>(h);
     *reinterpret_cast<uint4*>(lo + o) = *reinterpret_cast<const uint4*>(l);
     if (lo2 != nullptr) *reinterpret_cast<uint4*>(lo2 + o) = *reinterpret_cast<const uint4*>(l2);
@@ -790,7 +793,7 @@ cudaError_t TcEngine::split(const float* A, int64_t rows, int64_t cols, int64_t 
   const int blocks = (int)std::min<long long>(cdiv(total, 256), (long long)G_ * 8);
   split_a_kernel<<<blocks, 256, 0, st>>>(A, rows, cols, lda, vec, reinterpret_cast<bf16*>(Ahi_),
                                          reinterpret_cast<bf16*>(Alo_), reinterpret_cast<bf16*>(Alo2_), npan,
-                                         sumsq);
+                                         sumsq, rows, 0);
   note_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -801,19 +804,49 @@ cudaError_t TcEngine::split(const float* A, int64_t rows, int64_t cols, int64_t 
   return cudaMemsetAsync(cnt_, 0, sizeof(int) * cdiv(std::max(rows_cap_, cols_cap_), BM), st);
 }
 
+cudaError_t TcEngine::begin_split(const float* A, int64_t rows, int64_t cols, cudaStream_t st) {
+  if (rows > rows_cap_ || cols > cols_cap_) return cudaErrorInvalidValue;
+  split_of_ = A;
+  m_ = rows;
+  n_ = cols;
+  return cudaMemsetAsync(cnt_, 0, sizeof(int) * cdiv(std::max(rows_cap_, cols_cap_), BM), st);
+}
+
+cudaError_t TcEngine::split_rows(const float* Ablock, int64_t row0, int64_t rows, int64_t lda, double* sumsq,
+                                 cudaStream_t st) {
+  if (split_of_ == nullptr || row0 < 0 || row0 + rows > m_) return cudaErrorInvalidValue;
+  const bool vec = (reinterpret_cast<uintptr_t>(Ablock) % 16 == 0) && (lda % 4 == 0);
+  const long long npan = cdiv(n_, 64);
+  const long long total = rows * npan * 8;
+  const int blocks = (int)std::max<long long>(1, std::min<long long>(cdiv(total, 256), (long long)G_ * 8));
+  split_a_kernel<<<blocks, 256, 0, st>>>(Ablock, rows, n_, lda, vec, reinterpret_cast<bf16*>(Ahi_),
+                                         reinterpret_cast<bf16*>(Alo_), reinterpret_cast<bf16*>(Alo2_), npan,
+                                         sumsq, m_, row0);
+  note_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t TcEngine::pass(bool transA, const float* A, int64_t m, int64_t n, int64_t lda, const float* X,
                            int64_t ldx, int d, float* out, int64_t ldout, double* sumsq, int* info,
                            cudaStream_t st, bool exact) {
-  if (d > d_cap_) return cudaErrorInvalidValue;
-  if (exact && (Alo2_ == nullptr || Xlo2_ == nullptr)) return cudaErrorInvalidValue;
-  cudaError_t e;
   if (split_of_ != A || m != m_ || n != n_) {
-    if ((e = split(A, m, n, lda, sumsq, st)) != cudaSuccess) return e;
+    cudaError_t e = split(A, m, n, lda, sumsq, st);
+    if (e != cudaSuccess) return e;
   } else if (sumsq != nullptr) {
     return cudaErrorInvalidValue;   // ||A||^2 comes with the split only
   }
+  return pass_k(transA, 0, transA ? m : n, X, ldx, d, out, ldout, info, st, exact);
+}
+
+cudaError_t TcEngine::pass_k(bool transA, int64_t k0, int64_t K, const float* X, int64_t ldx, int d, float* out,
+                             int64_t ldout, int* info, cudaStream_t st, bool exact) {
+  if (d > d_cap_ || split_of_ == nullptr) return cudaErrorInvalidValue;
+  if (exact && (Alo2_ == nullptr || Xlo2_ == nullptr)) return cudaErrorInvalidValue;
+  if (k0 < 0 || (!transA && k0 != 0) || k0 + K > (transA ? m_ : n_) || K <= 0) return cudaErrorInvalidValue;
+  cudaError_t e;
+  const int64_t m = m_, n = n_;
   const int npad_ = npad_of(d);
-  const long long K = transA ? m : n, M = transA ? n : m;
+  const long long M = transA ? n : m;
   if (K > k_cap_) return cudaErrorInvalidValue;
   if ((e = cudaMemsetAsync(flag_, 0, sizeof(int), st)) != cudaSuccess) return e;
   {
@@ -852,6 +885,7 @@ cudaError_t TcEngine::pass(bool transA, const float* A, int64_t m, int64_t n, in
   TcArgs a;
   a.M = (int)M;
   a.K = (int)K;
+  a.k0 = (int)k0;
   a.d = d;
   a.npad = npad_;
   a.kblocks = (int)cdiv(K, bkp);

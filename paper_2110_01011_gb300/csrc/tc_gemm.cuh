@@ -32,6 +32,17 @@ class TcEngine {
   cudaError_t pass(bool transA, const float* A, int64_t rows, int64_t cols, int64_t lda, const float* X,
                    int64_t ldx, int d, float* out, int64_t ldout, double* sumsq, int* info, cudaStream_t st,
                    bool exact = false);
+  // Split A by row blocks as they arrive: begin_split names A (rows x cols,
+  // device, whose rows the caller fills) as the current split and resets the
+  // tile counters; split_rows splits rows row0 .. row0 + rows - 1 (Ablock
+  // points at row row0, lda); sumsq += their squares.
+  cudaError_t begin_split(const float* A, int64_t rows, int64_t cols, cudaStream_t st);
+  cudaError_t split_rows(const float* Ablock, int64_t row0, int64_t rows, int64_t lda, double* sumsq,
+                         cudaStream_t st);
+  // out = op(A_cur) X over K rows k0 .. k0 + K - 1 of the current split
+  // (transA only for k0 > 0; X holds those K rows).
+  cudaError_t pass_k(bool transA, int64_t k0, int64_t K, const float* X, int64_t ldx, int d, float* out,
+                     int64_t ldout, int* info, cudaStream_t st, bool exact = false);
   // G (cols x cols, ldg) = A^T A of the current split (cols <= 256).
   cudaError_t gram(float* G, int64_t ldg, int* info, cudaStream_t st);
 

@@ -3,8 +3,8 @@
 Everything runs on the GPU through the library's C ABI. For each generated
 matrix A and Gaussian Omega of width w = k + 20:
 
-* features: ``rqlp_probe_features`` (statistics of the probe sketch's
-  R-diagonal; the 13th input is log10 of the requested error);
+* features: ``rqlp_probe_features`` (12 statistics of the probe sketch's
+  R-diagonal);
 * error table: the chain is run once at width w with ``rqlp_sketch`` and
   ``rqlp_orth`` (Y = A^T Omega, P~ = qf(Y); each power pass Z = qf(A P~),
   P~ = qf(A^T Z)), saving after q = 0..4 passes the R factor of B = A P~.
@@ -15,18 +15,19 @@ matrix A and Gaussian Omega of width w = k + 20:
   (14 passes over A instead of 90);
 * excess error eps = ||A - A P_k P_k^T||_F / (sum_{i>k} sigma_i^2)^(1/2) - 1,
   in FP64 from P_k re-orthonormalised in FP64 (||A||^2 - ||A P_k||^2 is then
-  exact to ~1e-11 of the tail for tails >= 0.3 % of ||A||_F);
-* rows: several requested errors per matrix, log-uniform in [1e-3, 1e-1];
-  label = the cheapest pair, by cost (2q + 2)(k + p) (ties: smaller q, then
-  smaller p), whose eps is at most the request / LABEL_MARGIN; (4, 20) when
-  none is. The margin keeps the prediction on the safe side of a boundary
-  that the features only approximate: without it about a third of the
-  predictions for 1-3 % requests missed the request.
+  exact to ~1e-11 of the tail for tails >= 0.3 % of ||A||_F).
 
-The MLP is trained with the library's kernels (``rqlp_mlp_grad``,
-``rqlp_mlp_adam``). Trained weights (standardisation folded into the first
-layer, so the network takes raw features) are stored as little-endian
-float32 in ``data/qp_mlp.f32`` with a JSON description beside them.
+The network maps the features to estimates of log10 eps for all 15 pairs
+(targets clipped to [1e-4, 10]) and is trained by mean squared error with the
+library's kernels (``rqlp_mlp_grad``, ``rqlp_mlp_adam``). A request t is then
+answered with the cheapest pair, by cost (2q + 2)(k + p), whose estimate plus
+a margin delta is at most log10 t. delta is calibrated on the validation
+matrices: the 90th percentile of (measured - estimated) log10 eps over the
+entries near the requests' range, so that a pair picked as feasible reaches
+the request about nine times in ten. Trained weights (standardisation folded
+into the first layer, so the network takes raw features; delta last) are
+stored as little-endian float32 in ``data/qp_mlp.f32`` with a JSON
+description beside them.
 
     python -m paper_2110_01011_gb300.learn --train 4000 --test 500 --out <dir> --save
 """
@@ -42,10 +43,10 @@ import numpy as np
 
 from . import inputs, rqlp
 
-TARGET = 1e-3                    # the headline request
-LABEL_MARGIN = 2.0               # labels aim at request / LABEL_MARGIN
-TARGET_RANGE = (1e-3, 1e-1)      # requests seen in training
+TARGET_RANGE = (1e-3, 1e-1)      # requests the predictor is calibrated for
 EVAL_TARGETS = (1e-3, 3e-3, 1e-2, 3e-2, 1e-1)
+CALIBRATION_QUANTILE = 0.9       # delta: this quantile of (measured - estimated) log10 eps
+LOG_FLOOR, LOG_CEIL = -4.0, 1.0  # training targets: log10 eps clipped to [1e-4, 10]
 Q_CHOICES = rqlp.Q_CHOICES
 P_CHOICES = rqlp.P_CHOICES
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -57,7 +58,9 @@ def cost(q, p, k):
     return (2 * q + 2) * (k + p)
 
 
-def label_from_table(eps, k, target=TARGET):
+def label_from_table(eps, k, target):
+    """The cheapest pair that truly reaches `target` (ties: smaller q, then p);
+    (4, 20) when none does."""
     best = None
     for qi, q in enumerate(Q_CHOICES):
         for pi, p in enumerate(P_CHOICES):
@@ -68,14 +71,37 @@ def label_from_table(eps, k, target=TARGET):
     return (len(Q_CHOICES) - 1, len(P_CHOICES) - 1) if best is None else (best[1], best[2])
 
 
-def draw_problem(g, n_range=(384, 2048), k_range=(16, 236)):
-    """Sizes (m / n in [1/2, 2]), spectrum (exponential, rate in [5, 100], or
-    polynomial, alpha in [0.5, 3]) and k (log-uniform in [16, 236], so that k + 20
-    fits the widest sketch of 256 columns, and k + 20 <= min(m, n) / 2)
-    with the optimal rank-k tail at 0.3-30 % of ||A||_F."""
+def error_target(tab):
+    """log10 eps of a (5 x 3) table as the 15 training targets, clipped to
+    [1e-4, 10] (failed runs, inf, count as 10)."""
+    e = np.asarray(tab, dtype=np.float64).reshape(-1, len(Q_CHOICES) * len(P_CHOICES))
+    e = np.where(np.isfinite(e), e, 10.0 ** LOG_CEIL)
+    return np.log10(np.clip(e, 10.0 ** LOG_FLOOR, 10.0 ** LOG_CEIL))
+
+
+def choose_from_estimates(est, k, target, delta):
+    """The device's selection on the host: (qi, pi) of the cheapest pair whose
+    estimate plus delta is at most log10(target); (4, 20) when none is."""
+    lt = np.log10(target)
+    best = None
+    for qi, q in enumerate(Q_CHOICES):
+        for pi, p in enumerate(P_CHOICES):
+            if est[qi * len(P_CHOICES) + pi] + delta <= lt:
+                key = (cost(q, p, k), q, p)
+                if best is None or key < best[0]:
+                    best = (key, qi, pi)
+    return (len(Q_CHOICES) - 1, len(P_CHOICES) - 1) if best is None else (best[1], best[2])
+
+
+def draw_problem(g, n_range=(384, 2048), k_range=(16, 236), square=False):
+    """Sizes (m / n in [1/2, 2], or m = n), spectrum (exponential, rate in
+    [5, 100], or polynomial, alpha in [0.5, 3]) and k (log-uniform in
+    [16, 236], so that k + 20 fits the widest sketch of 256 columns, and
+    k + 20 <= min(m, n) / 2) with the optimal rank-k tail at 0.3-30 % of
+    ||A||_F."""
     while True:
         n = int(math.exp(g.uniform(math.log(n_range[0]), math.log(n_range[1]))))
-        m = int(n * math.exp(g.uniform(math.log(0.5), math.log(2.0))))
+        m = n if square else int(n * math.exp(g.uniform(math.log(0.5), math.log(2.0))))
         mn = min(m, n)
         if g.random() < 0.5:
             sig = inputs.exp_spectrum(mn, float(g.uniform(5.0, 100.0)))
@@ -148,20 +174,20 @@ def eps_table(A, Om, k, tail2):
     return tab
 
 
-def build_dataset(count, seed, device, log_every=500, n_range=(384, 2048)):
-    """Probe features (12 statistics; the 13th input is added per request),
-    error tables, k and sizes for ``count`` generated matrices."""
+def build_dataset(count, seed, device, log_every=500, n_range=(384, 2048), square=False):
+    """Probe features (12 statistics), error tables, k and sizes for
+    ``count`` generated matrices."""
     import torch
     g = inputs.rng(seed)
     feats, ks, tabs, meta = [], [], [], []
     t0 = time.time()
     for i in range(count):
-        m, n, k, sig, kind = draw_problem(g, n_range=n_range)
+        m, n, k, sig, kind = draw_problem(g, n_range=n_range, square=square)
         A = make_matrix(m, n, sig, seed * 1000003 + i, device)
         Om = torch.from_numpy(inputs.omega(m, k + 20, seed=seed * 7919 + i)).to(device)
         tail2 = float((sig[k:] ** 2).sum())
         tabs.append(eps_table(A, Om, k, tail2))
-        f, _ = rqlp.probe_features(A, k, Om, TARGET, precision=rqlp.PREC_BF16X3)
+        f, _ = rqlp.probe_features(A, k, Om, precision=rqlp.PREC_BF16X3)
         feats.append(f.cpu().numpy().astype(np.float64)[:12])
         ks.append(k)
         meta.append((m, n, k, kind))
@@ -170,50 +196,37 @@ def build_dataset(count, seed, device, log_every=500, n_range=(384, 2048)):
     return np.array(feats), np.array(ks), np.array(tabs), np.array(meta, dtype=object)
 
 
-def rows(feats, ks, tabs, targets, margin=LABEL_MARGIN):
-    """Training rows: for matrix i and request t, features + log10 t and the
-    label for t / margin."""
-    X, yq, yp, idx, ts = [], [], [], [], []
-    for i in range(len(ks)):
-        for t in targets[i]:
-            X.append(np.concatenate([feats[i], [math.log10(t)]]))
-            a, b = label_from_table(tabs[i], ks[i], t / margin)
-            yq.append(a)
-            yp.append(b)
-            idx.append(i)
-            ts.append(t)
-    return np.array(X), np.array(yq, np.int32), np.array(yp, np.int32), np.array(idx), np.array(ts)
+def rows(feats, tabs):
+    """Training rows: the features of each matrix and the 15 targets of its
+    error table."""
+    X = np.asarray(feats, dtype=np.float64)
+    Y = np.concatenate([error_target(t) for t in tabs]) if len(tabs) else np.zeros((0, 15))
+    return X, Y
 
 
-def draw_targets(count, per, seed):
-    g = inputs.rng(seed)
-    lo, hi = (math.log(v) for v in TARGET_RANGE)
-    return [np.exp(g.uniform(lo, hi, per)) for _ in range(count)]
-
-
-def init_params(seed, F=rqlp.MLP_FEATURES, H=rqlp.MLP_HIDDEN):
+def init_params(seed, F=rqlp.MLP_FEATURES, H=rqlp.MLP_HIDDEN, O=rqlp.MLP_OUTPUTS):
     g = inputs.rng(seed)
     W1 = g.standard_normal((F, H)) * math.sqrt(2.0 / F)
     W2 = g.standard_normal((H, H)) * math.sqrt(2.0 / H)
-    W3 = g.standard_normal((H, 8)) * math.sqrt(1.0 / H)
-    return np.concatenate([W1.ravel(), np.zeros(H), W2.ravel(), np.zeros(H), W3.ravel(), np.zeros(8)])
+    W3 = g.standard_normal((H, O)) * math.sqrt(1.0 / H)
+    return np.concatenate([W1.ravel(), np.zeros(H), W2.ravel(), np.zeros(H), W3.ravel(), np.zeros(O), [0.0]])
 
 
-def train(X, yq, yp, steps=3000, lr=3e-3, seed=11, device="cuda", val=None, every=50, init=None):
-    """Full-batch Adam with the library's kernels. With val = (Xv, yqv, ypv),
-    the parameters of the lowest validation loss (checked every ``every``
-    steps) are returned. init: parameters to start from (on standardised
-    features, see unfold_standardisation); Adam's moments start at zero.
-    Returns (params, curve of (step, loss, val_loss))."""
+def train(X, Y, steps=3000, lr=3e-3, seed=11, device="cuda", val=None, every=50, init=None):
+    """Full-batch Adam with the library's kernels on the mean squared error of
+    the 15 log10-error estimates. With val = (Xv, Yv), the parameters of the
+    lowest validation loss (checked every ``every`` steps) are returned.
+    init: parameters to start from (on standardised features, see
+    unfold_standardisation); Adam's moments start at zero. Returns (params,
+    curve of (step, loss, val_loss))."""
     import torch
     dev = torch.device(device)
 
-    def upload(Xa, qa, pa):
+    def upload(Xa, Ya):
         B = Xa.shape[0]
         nb = rqlp.rqlp_mlp_workspace_bytes(B)
         return (B, torch.from_numpy(np.ascontiguousarray(Xa, dtype=np.float32)).to(dev),
-                torch.from_numpy(np.ascontiguousarray(qa, dtype=np.int32)).to(dev),
-                torch.from_numpy(np.ascontiguousarray(pa, dtype=np.int32)).to(dev),
+                torch.from_numpy(np.ascontiguousarray(Ya, dtype=np.float32)).to(dev),
                 torch.empty(nb // 4 + 64, dtype=torch.float32, device=dev), nb)
 
     start = init_params(seed) if init is None else np.asarray(init, dtype=np.float64)
@@ -226,14 +239,14 @@ def train(X, yq, yp, steps=3000, lr=3e-3, seed=11, device="cuda", val=None, ever
     vgrad = torch.empty_like(prm)
     loss = torch.empty(1, device=dev)
     vloss = torch.empty(1, device=dev)
-    tr = upload(X, yq, yp)
+    tr = upload(X, Y)
     va = upload(*val) if val is not None else None
     st = torch.cuda.current_stream().cuda_stream
 
     def grad_of(data, g, lo):
-        B, Xd, qd, pd, ws, nb = data
-        s = rqlp.rqlp_mlp_grad(prm.data_ptr(), Xd.data_ptr(), qd.data_ptr(), pd.data_ptr(), B, g.data_ptr(),
-                               lo.data_ptr(), ws.data_ptr(), nb, st)
+        B, Xd, Yd, ws, nb = data
+        s = rqlp.rqlp_mlp_grad(prm.data_ptr(), Xd.data_ptr(), Yd.data_ptr(), B, g.data_ptr(), lo.data_ptr(),
+                               ws.data_ptr(), nb, st)
         if s != 0:
             raise rqlp.RqlpError(s, "rqlp_mlp_grad")
 
@@ -281,22 +294,36 @@ def unfold_standardisation(params, mu, sd, F=rqlp.MLP_FEATURES, H=rqlp.MLP_HIDDE
     return p
 
 
-def predict_logits(params, X):
-    """Logits on the device with rqlp_mlp_forward."""
+def predict_estimates(params, X):
+    """The network's 15 log10-error estimates per row, on the device with
+    rqlp_mlp_forward."""
     import torch
     dev = torch.device("cuda")
-    prm = torch.from_numpy(params.astype(np.float32)).to(dev)
+    prm = torch.from_numpy(np.asarray(params, dtype=np.float32)).to(dev)
     Xd = torch.from_numpy(np.ascontiguousarray(X, dtype=np.float32)).to(dev)
-    out = torch.empty(X.shape[0], 8, device=dev)
+    out = torch.empty(X.shape[0], rqlp.MLP_OUTPUTS, device=dev)
     s = rqlp.rqlp_mlp_forward(prm.data_ptr(), Xd.data_ptr(), X.shape[0], out.data_ptr(),
                               torch.cuda.current_stream().cuda_stream)
     if s != 0:
         raise rqlp.RqlpError(s, "rqlp_mlp_forward")
-    return out.cpu().numpy()
+    return out.cpu().numpy().astype(np.float64)
 
 
-def choose(logits):
-    return logits[:, :5].argmax(axis=1), logits[:, 5:].argmax(axis=1)
+def calibrate(est, tabs, quantile=CALIBRATION_QUANTILE):
+    """delta: the `quantile` of (measured - estimated) log10 eps over the
+    entries whose measured error lies within a decade of the requests' range
+    (the entries that decide a pick)."""
+    Y = np.concatenate([error_target(t) for t in tabs])
+    r = Y - np.asarray(est)
+    lo, hi = math.log10(TARGET_RANGE[0]) - 1.0, math.log10(TARGET_RANGE[1]) + 1.0
+    sel = (Y >= lo) & (Y <= hi)
+    return float(np.quantile(r[sel], quantile)) if sel.any() else 0.0
+
+
+def choose(est, ks, target, delta):
+    """(qi, pi) arrays of the picks for every row."""
+    picks = [choose_from_estimates(est[i], int(ks[i]), target, delta) for i in range(len(ks))]
+    return np.array([a for a, _ in picks]), np.array([b for _, b in picks])
 
 
 def evaluate_at(qi, pi, tabs, ks, target):
@@ -331,12 +358,9 @@ def evaluate_at(qi, pi, tabs, ks, target):
 
 
 def evaluate(params, feats, tabs, ks, targets=EVAL_TARGETS):
-    out = []
-    for t in targets:
-        X = np.concatenate([feats, np.full((len(ks), 1), math.log10(t))], axis=1)
-        qi, pi = choose(predict_logits(params, X))
-        out.append(evaluate_at(qi, pi, tabs, ks, t))
-    return out
+    est = predict_estimates(params, feats)
+    delta = float(np.asarray(params)[-1])
+    return [evaluate_at(*choose(est, ks, t, delta), tabs, ks, t) for t in targets]
 
 
 def save_weights(params, meta, path=WEIGHTS):
@@ -357,13 +381,12 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--train", type=int, default=4000)
     ap.add_argument("--test", type=int, default=500)
-    ap.add_argument("--per", type=int, default=5, help="requests per training matrix")
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--lr", type=float, default=3e-3)
     ap.add_argument("--out", default="learn_out")
     ap.add_argument("--data", default=None, help="reuse a qp_dataset.npz instead of generating one")
     ap.add_argument("--large", type=int, default=0,
-                    help="add this many training matrices with n in [2048, 8192] (and a fifth as many to test)")
+                    help="add this many square training matrices with n in [1000, 8000] (and a fifth as many to test)")
     ap.add_argument("--save", action="store_true", help="write data/qp_mlp.f32")
     ap.add_argument("--resume", default=None,
                     help="start from saved weights (a qp_mlp.f32); Adam's moments restart from zero")
@@ -378,35 +401,36 @@ def main():
         ftr, ktr, tabtr, _ = build_dataset(a.train, seed=501, device="cuda")
         fte, kte, tabte, _ = build_dataset(a.test, seed=909, device="cuda")
     if a.large > 0:
-        big = (2048, 8192)
-        f2, k2, t2, _ = build_dataset(a.large, seed=601, device="cuda", log_every=50, n_range=big)
-        f3, k3, t3, _ = build_dataset(max(1, a.large // 5), seed=919, device="cuda", log_every=50, n_range=big)
+        big = (1000, 8000)   # square, as the 20000-matrix specification of the training set draws them
+        f2, k2, t2, _ = build_dataset(a.large, seed=601, device="cuda", log_every=100, n_range=big, square=True)
+        f3, k3, t3, _ = build_dataset(max(1, a.large // 5), seed=919, device="cuda", log_every=100, n_range=big,
+                                      square=True)
         # interleave so that the validation slice (the first tenth) holds both sizes
         order = np.random.default_rng(5).permutation(len(ktr) + len(k2))
         ftr, ktr, tabtr = (np.concatenate([x, y])[order] for x, y in ((ftr, f2), (ktr, k2), (tabtr, t2)))
         fte, kte, tabte = (np.concatenate([x, y]) for x, y in ((fte, f3), (kte, k3), (tabte, t3)))
     t_data = time.time() - t0
-    # 10 % of the training matrices (all their requests) validate the early stop
+    # 10 % of the training matrices validate the early stop and calibrate delta
     nv = max(1, len(ktr) // 10)
-    tg = draw_targets(len(ktr), a.per, seed=77)
-    Xtr, yqtr, yptr, _, _ = rows(ftr[nv:], ktr[nv:], tabtr[nv:], tg[nv:])
-    Xva, yqva, ypva, _, _ = rows(ftr[:nv], ktr[:nv], tabtr[:nv], tg[:nv])
+    Xtr, Ytr = rows(ftr[nv:], tabtr[nv:])
+    Xva, Yva = rows(ftr[:nv], tabtr[:nv])
     mu = Xtr.mean(axis=0)
     sd = Xtr.std(axis=0)
     sd[sd < 1e-6] = 1.0
     t1 = time.time()
     init = unfold_standardisation(load_weights(a.resume), mu, sd) if a.resume else None
-    params, curve = train((Xtr - mu) / sd, yqtr, yptr, steps=a.steps, lr=a.lr,
-                          val=((Xva - mu) / sd, yqva, ypva), init=init)
+    params, curve = train((Xtr - mu) / sd, Ytr, steps=a.steps, lr=a.lr, val=((Xva - mu) / sd, Yva), init=init)
     t_train = time.time() - t1
     params = fold_standardisation(params, mu, sd)
+    params[-1] = calibrate(predict_estimates(params, ftr[:nv]), tabtr[:nv])
     ev = evaluate(params, fte, tabte, kte)
-    report = {"train_matrices": int(len(ktr)), "train_rows": int(len(yqtr)), "val_rows": int(len(yqva)),
-              "label_margin": LABEL_MARGIN,
+    est_te = predict_estimates(params, fte)
+    Yte = np.concatenate([error_target(t) for t in tabte])
+    report = {"train_matrices": int(len(ktr)), "train_rows": int(len(Ytr)), "val_rows": int(len(Yva)),
+              "delta": float(params[-1]), "calibration_quantile": CALIBRATION_QUANTILE,
               "test_matrices": int(len(kte)), "steps": a.steps, "lr": a.lr, "target_range": TARGET_RANGE,
-              "seconds_data": t_data, "seconds_train": t_train, "curve": curve,
-              "label_hist_q": np.bincount(yqtr, minlength=5).tolist(),
-              "label_hist_p": np.bincount(yptr, minlength=3).tolist(), "test": ev}
+              "test_rmse_log10": float(np.sqrt(np.mean((est_te - Yte) ** 2))),
+              "seconds_data": t_data, "seconds_train": t_train, "curve": curve, "test": ev}
     os.makedirs(a.out, exist_ok=True)
     if not a.data or a.large > 0:
         np.savez(os.path.join(a.out, "qp_dataset.npz"), ftr=ftr, ktr=ktr, tabtr=tabtr, fte=fte, kte=kte,

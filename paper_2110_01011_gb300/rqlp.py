@@ -24,9 +24,10 @@ __all__ = ["load", "RqlpError", "rqlp_default_opts", "rqlp_workspace_bytes", "rq
 PREC_FP32 = 0
 PREC_BF16X3 = 1
 MAX_D = 256
-MLP_FEATURES = 13
+MLP_FEATURES = 12
 MLP_HIDDEN = 64
-MLP_PARAMS = 5576
+MLP_OUTPUTS = 15
+MLP_PARAMS = 5968
 Q_CHOICES = (0, 1, 2, 3, 4)
 P_CHOICES = (5, 10, 20)
 STATUS = {0: "RQLP_OK", 1: "RQLP_ERR_ARG", 2: "RQLP_ERR_CUDA", 3: "RQLP_ERR_BREAKDOWN",
@@ -38,7 +39,10 @@ EXPORTED = ["rqlp_default_opts", "rqlp_workspace_bytes", "rqlp_factor", "rqlp_ho
             "rqlp_factor_host", "rqlp_factor_noalloc", "rqlp_sketch_workspace_bytes", "rqlp_sketch",
             "rqlp_orth_workspace_bytes", "rqlp_orth", "rqlp_mlp_forward", "rqlp_mlp_workspace_bytes",
             "rqlp_mlp_grad", "rqlp_mlp_adam", "rqlp_learned_workspace_bytes", "rqlp_probe_features",
-            "rqlp_predict_qp", "rqlp_factor_learned", "rqlp_batch_workspace_bytes", "rqlp_batch_create",
+            "rqlp_predict_qp", "rqlp_factor_learned", "rqlp_learned_host_workspace_bytes",
+            "rqlp_factor_learned_host", "rqlp_rank_errors", "rqlp_rank_residual_workspace_bytes",
+            "rqlp_rank_residual", "rqlp_subspace_workspace_bytes", "rqlp_subspace_angles",
+            "rqlp_batch_workspace_bytes", "rqlp_batch_create",
             "rqlp_batch_autotune", "rqlp_batch_tuning", "rqlp_batch_run", "rqlp_batch_launch",
             "rqlp_batch_destroy", "rqlp_factor_batched", "rqlp_kernel_launches", "rqlp_profile_enable",
             "rqlp_profile_read", "rqlp_status_string", "rqlp_version"]
@@ -98,14 +102,14 @@ def _declare(lib):
     lib.rqlp_mlp_forward.restype = _int
     lib.rqlp_mlp_workspace_bytes.argtypes = [_int]
     lib.rqlp_mlp_workspace_bytes.restype = _sz
-    lib.rqlp_mlp_grad.argtypes = [_vp, _vp, _vp, _vp, _int, _vp, _vp, _vp, _sz, _vp]
+    lib.rqlp_mlp_grad.argtypes = [_vp, _vp, _vp, _int, _vp, _vp, _vp, _sz, _vp]
     lib.rqlp_mlp_grad.restype = _int
     lib.rqlp_mlp_adam.argtypes = [_vp, _vp, _vp, _vp, _int, _f, _f, _f, _f, _int, _vp]
     lib.rqlp_mlp_adam.restype = _int
     lib.rqlp_learned_workspace_bytes.argtypes = [_i64, _i64, _int, ctypes.POINTER(Opts)]
     lib.rqlp_learned_workspace_bytes.restype = _sz
     _d = ctypes.c_double
-    lib.rqlp_probe_features.argtypes = [_vp, _i64, _i64, _i64, _int, _vp, _i64, _d, _vp, _vp, _sz, _vp,
+    lib.rqlp_probe_features.argtypes = [_vp, _i64, _i64, _i64, _int, _vp, _i64, _vp, _vp, _sz, _vp,
                                         ctypes.POINTER(Opts), _vp]
     lib.rqlp_probe_features.restype = _int
     lib.rqlp_predict_qp.argtypes = [_vp, _i64, _i64, _i64, _int, _vp, _i64, _d, _vp, _vp, _vp, _sz, _vp,
@@ -114,6 +118,22 @@ def _declare(lib):
     lib.rqlp_factor_learned.argtypes = [_vp, _i64, _i64, _i64, _int, _vp, _i64, _d, _vp, _vp, _i64, _vp, _i64,
                                         _vp, _i64, _vp, _sz, _vp, _vp, _vp, ctypes.POINTER(Opts), _vp]
     lib.rqlp_factor_learned.restype = _int
+    lib.rqlp_learned_host_workspace_bytes.argtypes = [_i64, _i64, _int, ctypes.POINTER(Opts)]
+    lib.rqlp_learned_host_workspace_bytes.restype = _sz
+    lib.rqlp_factor_learned_host.argtypes = [_vp, _i64, _i64, _i64, _int, _vp, _i64, _d, _vp, _vp, _i64, _vp,
+                                             _i64, _vp, _i64, _vp, _sz, _vp, _vp, _vp, ctypes.POINTER(Opts), _vp]
+    lib.rqlp_factor_learned_host.restype = _int
+    lib.rqlp_rank_errors.argtypes = [_vp, _i64, _int, _vp, _vp, _vp]
+    lib.rqlp_rank_errors.restype = _int
+    lib.rqlp_rank_residual_workspace_bytes.argtypes = [_i64, _int]
+    lib.rqlp_rank_residual_workspace_bytes.restype = _sz
+    lib.rqlp_rank_residual.argtypes = [_vp, _i64, _i64, _i64, _vp, _i64, _vp, _i64, _int, _vp, _i64, _int, _vp,
+                                       _vp, _sz, _vp]
+    lib.rqlp_rank_residual.restype = _int
+    lib.rqlp_subspace_workspace_bytes.argtypes = [_i64, _int, _int]
+    lib.rqlp_subspace_workspace_bytes.restype = _sz
+    lib.rqlp_subspace_angles.argtypes = [_vp, _i64, _int, _i64, _vp, _int, _i64, _int, _vp, _vp, _sz, _vp]
+    lib.rqlp_subspace_angles.restype = _int
     _pp = ctypes.POINTER(Problem)
     lib.rqlp_batch_workspace_bytes.argtypes = [_int, _pp, _int, ctypes.POINTER(Opts)]
     lib.rqlp_batch_workspace_bytes.restype = _sz
@@ -246,16 +266,16 @@ def rqlp_orth(X, rows, d, ldx, R, ldr, workspace, ws_bytes, d_info, opts, stream
                                 ctypes.byref(opts) if opts is not None else None, stream))
 
 
-def rqlp_mlp_forward(params, X, batch, logits, stream):
-    return int(load().rqlp_mlp_forward(params, X, batch, logits, stream))
+def rqlp_mlp_forward(params, X, batch, est, stream):
+    return int(load().rqlp_mlp_forward(params, X, batch, est, stream))
 
 
 def rqlp_mlp_workspace_bytes(batch):
     return int(load().rqlp_mlp_workspace_bytes(batch))
 
 
-def rqlp_mlp_grad(params, X, yq, yp, batch, grad, loss, workspace, ws_bytes, stream):
-    return int(load().rqlp_mlp_grad(params, X, yq, yp, batch, grad, loss, workspace, ws_bytes, stream))
+def rqlp_mlp_grad(params, X, Y, batch, grad, loss, workspace, ws_bytes, stream):
+    return int(load().rqlp_mlp_grad(params, X, Y, batch, grad, loss, workspace, ws_bytes, stream))
 
 
 def rqlp_mlp_adam(params, grad, m1, m2, n, lr, beta1, beta2, eps, step, stream):
@@ -266,8 +286,8 @@ def rqlp_learned_workspace_bytes(m, n, k, opts=None):
     return int(load().rqlp_learned_workspace_bytes(m, n, k, ctypes.byref(opts or _opts())))
 
 
-def rqlp_probe_features(A, m, n, lda, k, Omega, ldo, target, feat, workspace, ws_bytes, d_info, opts, stream):
-    return int(load().rqlp_probe_features(A, m, n, lda, k, Omega, ldo, target, feat, workspace, ws_bytes, d_info,
+def rqlp_probe_features(A, m, n, lda, k, Omega, ldo, feat, workspace, ws_bytes, d_info, opts, stream):
+    return int(load().rqlp_probe_features(A, m, n, lda, k, Omega, ldo, feat, workspace, ws_bytes, d_info,
                                           ctypes.byref(opts) if opts is not None else None, stream))
 
 
@@ -441,9 +461,8 @@ def orth(X, small_fp64=False):
     return X, R, info, buf
 
 
-def probe_features(A, k, Omega, target, precision=PREC_BF16X3, workspace=None):
-    """Probe features (13 floats, CUDA tensor; the last is log10(target)) of A
-    with Omega (m x (k+20))."""
+def probe_features(A, k, Omega, precision=PREC_BF16X3, workspace=None):
+    """Probe features (12 floats, CUDA tensor) of A with Omega (m x (k+20))."""
     import torch
     m, n = A.shape
     opts = _opts(precision)
@@ -455,7 +474,7 @@ def probe_features(A, k, Omega, target, precision=PREC_BF16X3, workspace=None):
     ws = (workspace.data_ptr() + 255) // 256 * 256
     feat = torch.empty(MLP_FEATURES, dtype=torch.float32, device=A.device)
     info = torch.empty(2, dtype=torch.int32, device=A.device)
-    st = rqlp_probe_features(A.data_ptr(), m, n, A.stride(0), k, Omega.data_ptr(), Omega.stride(0), float(target),
+    st = rqlp_probe_features(A.data_ptr(), m, n, A.stride(0), k, Omega.data_ptr(), Omega.stride(0),
                              feat.data_ptr(), ws, nb, info.data_ptr(), opts, _stream())
     if st != 0:
         raise RqlpError(st, "rqlp_probe_features")
@@ -491,6 +510,90 @@ def factor_learned(A, k, Omega, params, target, precision=PREC_BF16X3, workspace
         raise RqlpError(st, "rqlp_factor_learned")
     d = k + qp[1]
     return Q[:, :d], L[:d, :d], P[:, :d], info, diag, (qp[0], qp[1])
+
+
+def rqlp_learned_host_workspace_bytes(m, n, k, opts=None):
+    return int(load().rqlp_learned_host_workspace_bytes(m, n, k, ctypes.byref(opts or _opts())))
+
+
+def factor_learned_host(A, k, Omega, params, target, precision=PREC_BF16X3, workspace=None, out=None, parts=0):
+    """Host-buffer learned form: CPU float32 A (m x n) and Omega (m x (k+20))
+    (pinned for full bandwidth), params on the device. Returns host
+    (Q, L, P, info, diag, (q, p)) with Q, L, P views of k + p columns;
+    synchronous."""
+    import torch
+    A_t, O_t = torch.as_tensor(A), torch.as_tensor(Omega)
+    m, n = A_t.shape
+    w = k + 20
+    opts = _opts(precision, parts=parts)
+    nb = rqlp_learned_host_workspace_bytes(m, n, k, opts)
+    if nb == 0:
+        raise RqlpError(1, "rqlp_learned_host_workspace_bytes")
+    if workspace is None or workspace.numel() < nb + 256:
+        workspace = torch.empty(nb + 256, dtype=torch.uint8, device="cuda")
+    if out is None:
+        pin = torch.cuda.is_available()
+        out = (torch.empty(m, w, pin_memory=pin), torch.empty(w, w, pin_memory=pin), torch.empty(n, w, pin_memory=pin),
+               torch.zeros(2, dtype=torch.int32), torch.zeros(4, dtype=torch.float64))
+    Q, L, P, info, diag = out
+    qp = (ctypes.c_int * 2)()
+    ws = (workspace.data_ptr() + 255) // 256 * 256
+    st = int(load().rqlp_factor_learned_host(A_t.data_ptr(), m, n, A_t.stride(0), k, O_t.data_ptr(), O_t.stride(0),
+                                             float(target), params.data_ptr(), Q.data_ptr(), Q.stride(0),
+                                             L.data_ptr(), L.stride(0), P.data_ptr(), P.stride(0), ws, nb,
+                                             info.data_ptr(), diag.data_ptr(), ctypes.addressof(qp),
+                                             ctypes.byref(opts), _stream()))
+    if st != 0:
+        raise RqlpError(st, "rqlp_factor_learned_host")
+    d = k + qp[1]
+    return Q[:, :d], L[:d, :d], P[:, :d], info, diag, (qp[0], qp[1])
+
+
+def rank_errors(L, diag):
+    """||A - A_r||_F for r = 1..d (CUDA float64 tensor) from L and d_diag."""
+    import torch
+    d = L.shape[0]
+    errs = torch.empty(d, dtype=torch.float64, device=L.device)
+    st = int(load().rqlp_rank_errors(L.data_ptr(), L.stride(0), d, diag.data_ptr(), errs.data_ptr(), _stream()))
+    if st != 0:
+        raise RqlpError(st, "rqlp_rank_errors")
+    return errs
+
+
+def rank_residual(A, Q, L, P, r):
+    """||A - Q L(:, 1:r) P(:, 1:r)^T||_F computed explicitly (CUDA float64 scalar tensor)."""
+    import torch
+    m, n = A.shape
+    d = L.shape[0]
+    nb = int(load().rqlp_rank_residual_workspace_bytes(m, r))
+    if nb == 0:
+        raise RqlpError(1, "rqlp_rank_residual_workspace_bytes")
+    buf, ws = _workspace(nb, A.device)
+    out = torch.empty(1, dtype=torch.float64, device=A.device)
+    st = int(load().rqlp_rank_residual(A.data_ptr(), m, n, A.stride(0), Q.data_ptr(), Q.stride(0), L.data_ptr(),
+                                       L.stride(0), d, P.data_ptr(), P.stride(0), r, out.data_ptr(), ws, nb,
+                                       _stream()))
+    if st != 0:
+        raise RqlpError(st, "rqlp_rank_residual")
+    return out
+
+
+def subspace_angles(X, Y, cosines=False):
+    """Sines (or cosines) of the canonical angles between R(Y) and R(X), for
+    orthonormal CUDA float32 X (rows x a) and Y (rows x b); largest first."""
+    import torch
+    rows, a = X.shape
+    b = Y.shape[1]
+    nb = int(load().rqlp_subspace_workspace_bytes(rows, a, b))
+    if nb == 0:
+        raise RqlpError(1, "rqlp_subspace_workspace_bytes")
+    buf, ws = _workspace(nb, X.device)
+    out = torch.empty(b, dtype=torch.float64, device=X.device)
+    st = int(load().rqlp_subspace_angles(X.data_ptr(), rows, a, X.stride(0), Y.data_ptr(), b, Y.stride(0),
+                                         1 if cosines else 0, out.data_ptr(), ws, nb, _stream()))
+    if st != 0:
+        raise RqlpError(st, "rqlp_subspace_angles")
+    return out
 
 
 def factor_host(A, k, p, q, Omega, precision=PREC_FP32, workspace=None, out=None, parts=0):

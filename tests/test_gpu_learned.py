@@ -1,15 +1,15 @@
 """GPU parity of the learned (q, p) predictor.
 
-* MLP kernels (forward, gradient, Adam) against the FP64 reference on the same
-  FP32 parameters and features. A ReLU mask is an FP decision: samples whose
+* MLP kernels (forward, mean-squared-error gradient, Adam) against the FP64
+  reference on the same FP32 parameters, features and targets. A ReLU mask is an FP decision: samples whose
   FP64 pre-activations come within 1e-4 of zero are dropped so that both sides
   take the same branch.
 * Probe features against the FP64 reference computed from the R-diagonal of a
   Householder QR of the same probe sketch A^T Omega_w (w = k + 20).
 * The learned factorisation against the oracle run with the same (q, p) and
   the first k + p columns of Omega, for every p width and q from 0 to 4
-  (forced through the output bias), and with a random network whose choice is
-  checked against the FP64 argmax.
+  (forced through the output bias), and with a random network whose pick is
+  checked against the FP64 selection rule.
 """
 import ctypes
 import os
@@ -55,7 +55,7 @@ def _st():
 def test_mlp_params_count():
     from paper_2110_01011_gb300 import rqlp
     assert rqlp.MLP_PARAMS == mo.n_params()
-    assert (rqlp.MLP_FEATURES, rqlp.MLP_HIDDEN) == (F, H)
+    assert (rqlp.MLP_FEATURES, rqlp.MLP_HIDDEN, rqlp.MLP_OUTPUTS) == (F, H, mo.N_OUT)
 
 
 @pytest.mark.parametrize("B", [1, 37, 1300])
@@ -66,7 +66,7 @@ def test_mlp_forward(B):
     theta = _theta(5 + B)
     X = _features(9 + B, B)
     ref, _ = mo.forward(theta, X)
-    out = torch.empty(B, 8, device="cuda")
+    out = torch.empty(B, mo.N_OUT, device="cuda")
     dt, dX = _dev(theta, torch.float32), _dev(X, torch.float32)   # kept alive across the launch
     st = rqlp.rqlp_mlp_forward(dt.data_ptr(), dX.data_ptr(), B, out.data_ptr(), _st())
     assert st == 0
@@ -83,17 +83,15 @@ def test_mlp_grad(B):
     theta = _theta(100 + B)
     X = _safe_rows(theta, _features(200 + B, B + 40))[:B]
     B = X.shape[0]
-    g = inputs.rng(300 + B)
-    yq = g.integers(0, 5, B).astype(np.int32)
-    yp = g.integers(0, 3, B).astype(np.int32)
-    loss_ref, grad_ref = mo.loss_and_grads(theta, X, yq, yp)
+    Y = inputs.rng(300 + B).uniform(-4, 1, (B, mo.N_OUT)).astype(np.float32).astype(np.float64)
+    loss_ref, grad_ref = mo.loss_and_grads(theta, X, Y)
     nb = rqlp.rqlp_mlp_workspace_bytes(B)
     ws = torch.empty(nb // 4 + 1, device="cuda")
     grad = torch.empty(mo.n_params(), device="cuda")
     loss = torch.empty(1, device="cuda")
-    dt, dX, dq, dp = _dev(theta, torch.float32), _dev(X, torch.float32), _dev(yq), _dev(yp)
-    st = rqlp.rqlp_mlp_grad(dt.data_ptr(), dX.data_ptr(), dq.data_ptr(), dp.data_ptr(), B, grad.data_ptr(),
-                            loss.data_ptr(), ws.data_ptr(), nb, _st())
+    dt, dX, dY = _dev(theta, torch.float32), _dev(X, torch.float32), _dev(Y, torch.float32)
+    st = rqlp.rqlp_mlp_grad(dt.data_ptr(), dX.data_ptr(), dY.data_ptr(), B, grad.data_ptr(), loss.data_ptr(),
+                            ws.data_ptr(), nb, _st())
     assert st == 0
     gg = grad.double().cpu().numpy()
     # sums over the batch of FP32 products: relative 1e-4 of the largest entry
@@ -110,9 +108,9 @@ def test_mlp_grad_workspace_too_small():
     ws = torch.empty(nb // 4, device="cuda")
     z = torch.zeros(mo.n_params(), device="cuda")
     X = torch.zeros(B, F, device="cuda")
-    y = torch.zeros(B, dtype=torch.int32, device="cuda")
-    st = rqlp.rqlp_mlp_grad(z.data_ptr(), X.data_ptr(), y.data_ptr(), y.data_ptr(), B, z.data_ptr(), None,
-                            ws.data_ptr(), nb - 4, _st())
+    Y = torch.zeros(B, mo.N_OUT, device="cuda")
+    st = rqlp.rqlp_mlp_grad(z.data_ptr(), X.data_ptr(), Y.data_ptr(), B, z.data_ptr(), None, ws.data_ptr(), nb - 4,
+                            _st())
     assert st == 6   # RQLP_ERR_WORKSPACE
 
 
@@ -152,10 +150,10 @@ def _probe_problem(m, n, k, rate, seed):
     return A, Om
 
 
-def _oracle_features(A, Om, k, target):
+def _oracle_features(A, Om, k):
     Y = np.asarray(A, np.float64).T @ np.asarray(Om, np.float64)
     _, R = orc.householder_qr(Y)
-    return mo.probe_features(np.diag(R), k, *A.shape, target), np.diag(R)
+    return mo.probe_features(np.diag(R), k, *A.shape), np.diag(R)
 
 
 @pytest.mark.parametrize("m,n,k,rate", [(700, 500, 20, 25.0), (333, 900, 7, 12.0), (1200, 1200, 60, 60.0),
@@ -169,12 +167,11 @@ def test_probe_features(m, n, k, rate, prec):
     for the two steep ones)."""
     from paper_2110_01011_gb300 import rqlp
     A, Om = _probe_problem(m, n, k, rate, seed=m + n + k)
-    target = 10.0 ** -(1 + (m % 3))
-    ref, r = _oracle_features(A, Om, k, target)
+    ref, r = _oracle_features(A, Om, k)
     kappa = r[0] / r[-1]
     tol = 1e-4 + 40 * 2.0 ** -24 * kappa ** 2
     dA, dO = _dev(A), _dev(Om)
-    feat, info = rqlp.probe_features(dA, k, dO, target, precision=prec)
+    feat, info = rqlp.probe_features(dA, k, dO, precision=prec)
     got = feat.double().cpu().numpy()
     assert int(info[0].item()) == 0
     np.testing.assert_allclose(got[:9], ref[:9], atol=tol, rtol=0)
@@ -182,10 +179,12 @@ def test_probe_features(m, n, k, rate, prec):
 
 
 def _forced_params(qi, pi):
+    """Zero weights, output biases +5 (error 1e5: never feasible) except pair
+    (qi, pi) at -5: the only pair within any request."""
     theta = np.zeros(mo.n_params())
-    b3 = mo.n_params() - 8
-    theta[b3 + qi] = 5.0
-    theta[b3 + 5 + pi] = 5.0
+    b3 = mo.n_params() - 1 - mo.N_OUT
+    theta[b3:b3 + mo.N_OUT] = 5.0
+    theta[b3 + 3 * qi + pi] = -5.0
     return theta.astype(np.float32)
 
 
@@ -213,23 +212,25 @@ def test_factor_learned_forced(qi, pi, prec):
 
 
 def test_factor_learned_random_net():
-    """The device argmax equals the FP64 argmax of the same network on the
-    device's features (margins checked), and the chain runs that (q, p)."""
-    import torch
-
-    from paper_2110_01011_gb300 import rqlp
+    """The device's pick equals the FP64 selection of the same network on the
+    device's features (estimates at least 1e-3 from the request's boundary),
+    and the chain runs that (q, p)."""
     m, n, k = 800, 800, 30
     A, Om = _probe_problem(m, n, k, 30.0, seed=777)
     dA, dO = _dev(A), _dev(Om)
-    feat, _ = rqlp.probe_features(dA, k, dO, 1e-2, precision=1)
+    from paper_2110_01011_gb300 import rqlp
+    feat, _ = rqlp.probe_features(dA, k, dO, precision=1)
     f = feat.double().cpu().numpy()[None, :]
-    for seed in range(40):
-        theta = _theta(9000 + seed, scale=0.5).astype(np.float32)
-        lg, _ = mo.forward(theta.astype(np.float64), f)
-        sq, sp = np.sort(lg[0, :5]), np.sort(lg[0, 5:])
-        if sq[-1] - sq[-2] > 1e-3 and sp[-1] - sp[-2] > 1e-3:
+    lt = np.log10(1e-2)
+    for seed in range(200):
+        theta = _theta(9000 + seed, scale=0.5)
+        theta[-1] = 0.1
+        theta = theta.astype(np.float32)
+        est, _ = mo.forward(theta.astype(np.float64), f)
+        qi, pi = mo.choose(est[0], k, 1e-2, float(theta[-1]))
+        if np.abs(est[0] + float(theta[-1]) - lt).min() > 1e-3 and (qi, pi) != (4, 2):
             break
-    want = (mo.Q_CHOICES[int(lg[0, :5].argmax())], mo.P_CHOICES[int(lg[0, 5:].argmax())])
+    want = (mo.Q_CHOICES[qi], mo.P_CHOICES[pi])
     gpu, qp = _learned(A, Om, k, theta, 1)
     assert qp == want
     compare(A, Om[:, :k + want[1]], k, want[1], want[0], gpu, elem_atol=5e-4, precision=1)
@@ -262,11 +263,12 @@ def test_learned_argument_errors():
     A = torch.zeros(100, 30, device="cuda")
     Om = torch.zeros(100, 40, device="cuda")
     with pytest.raises(rqlp.RqlpError):
-        rqlp.probe_features(A, 20, Om, 1e-2)
+        rqlp.probe_features(A, 20, Om)
     A = torch.zeros(100, 60, device="cuda")
+    prm = torch.zeros(mo.n_params(), device="cuda")
     for bad in (0.0, -1e-3, 1.0, float("nan")):
         with pytest.raises(rqlp.RqlpError):
-            rqlp.probe_features(A, 20, Om, bad)
+            rqlp.factor_learned(A, 20, Om, prm, bad)
 
 
 def test_shipped_weights_load():
@@ -279,23 +281,25 @@ def test_shipped_weights_load():
 
 
 def test_predict_fallback_on_nonfinite_logits():
-    """A network whose logits are not finite falls back to (q, p) = (2, 10)."""
+    """A network whose estimates or margin are not finite falls back to
+    (q, p) = (2, 10)."""
     import torch
 
     from paper_2110_01011_gb300 import rqlp
     m, n, k = 400, 300, 12
     A, Om = _probe_problem(m, n, k, 10.0, seed=5)
-    theta = _forced_params(4, 2)
-    theta[-1] = np.nan
-    dA, dO, dP = _dev(A), _dev(Om), _dev(theta)
-    nb = rqlp.rqlp_learned_workspace_bytes(m, n, k, rqlp._opts(0))
-    buf, ws = rqlp._workspace(nb, dA.device)
-    qp = torch.empty(2, dtype=torch.int32, device="cuda")
-    info = torch.empty(2, dtype=torch.int32, device="cuda")
-    st = rqlp.rqlp_predict_qp(dA.data_ptr(), m, n, n, k, dO.data_ptr(), k + 20, 1e-2, dP.data_ptr(), qp.data_ptr(),
-                              ws, nb, info.data_ptr(), rqlp._opts(0), _st())
-    assert st == 0
-    assert tuple(qp.cpu().tolist()) == (2, 10)
+    for where in (-2, -1):          # the last output bias, then delta
+        theta = _forced_params(4, 2)
+        theta[where] = np.nan
+        dA, dO, dP = _dev(A), _dev(Om), _dev(theta)
+        nb = rqlp.rqlp_learned_workspace_bytes(m, n, k, rqlp._opts(0))
+        buf, ws = rqlp._workspace(nb, dA.device)
+        qp = torch.empty(2, dtype=torch.int32, device="cuda")
+        info = torch.empty(2, dtype=torch.int32, device="cuda")
+        st = rqlp.rqlp_predict_qp(dA.data_ptr(), m, n, n, k, dO.data_ptr(), k + 20, 1e-2, dP.data_ptr(),
+                                  qp.data_ptr(), ws, nb, info.data_ptr(), rqlp._opts(0), _st())
+        assert st == 0
+        assert tuple(qp.cpu().tolist()) == (2, 10)
 
 
 def test_label_table_matches_oracle():
@@ -318,3 +322,26 @@ def test_label_table_matches_oracle():
             Q, L, P = orc.rand_qlp(A64, np.asarray(Om[:, :k + p], np.float64), q)
             ref = orc.rank_r_error_fro(A64, Q, L, P, k) / np.sqrt(tail2) - 1.0
             assert abs(tab[qi, pi] - ref) <= 1e-4 + 1e-3 * abs(ref), (q, p, tab[qi, pi], ref)
+
+
+@pytest.mark.parametrize("m,n,k", [(900, 640, 24), (5000, 3000, 40)])
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp32", "bf16x3"])
+def test_factor_learned_host_overlapped_ingest(m, n, k, prec):
+    """The host-buffer learned entry (row blocks of A copied on the library's
+    streams, the probe sketch started per landed block) picks the same
+    (q, p) as the device-buffer entry and matches the oracle at it."""
+    import torch
+
+    from paper_2110_01011_gb300 import rqlp
+    A, Om = _probe_problem(m, n, k, 20.0, seed=m + k)
+    theta = _forced_params(2, 1)
+    dt = _dev(theta, torch.float32)
+    hA = torch.from_numpy(A).pin_memory()
+    hO = torch.from_numpy(Om).pin_memory()
+    Q, L, P, info, diag, qp = rqlp.factor_learned_host(hA, k, hO, dt, 1e-2, precision=prec)
+    assert qp == (2, 10) and int(info[0]) == 0
+    gpu = (Q.double().numpy(), L.double().numpy(), P.double().numpy(), info.numpy(), diag.numpy())
+    compare(A, Om[:, :k + 10], k, 10, 2, gpu, elem_atol=5e-4, precision=prec)
+    dgpu, dqp = _learned(A, Om, k, theta, prec)
+    assert dqp == qp
+    assert np.max(np.abs(gpu[1] - dgpu[1])) <= 1e-5 * np.abs(dgpu[1]).max()

@@ -18,14 +18,14 @@ def test_label_matches_reference():
 
 def test_label_infeasible_and_ties():
     tab = np.full((5, 3), 1.0)
-    assert learn.label_from_table(tab, 10) == (4, 2)
+    assert learn.label_from_table(tab, 10, 1e-3) == (4, 2)
     tab = np.full((5, 3), 0.0)
-    assert learn.label_from_table(tab, 10) == (0, 0)
+    assert learn.label_from_table(tab, 10, 1e-3) == (0, 0)
     # (q=1, p=5): cost 4 * 15 = 60; (q=0, p=20): cost 2 * 30 = 60 -> the smaller q wins
     tab = np.full((5, 3), 1.0)
     tab[1, 0] = 0.0
     tab[0, 2] = 0.0
-    assert learn.label_from_table(tab, 10) == (0, 2)
+    assert learn.label_from_table(tab, 10, 1e-3) == (0, 2)
 
 
 def test_fold_standardisation():
@@ -63,16 +63,41 @@ def test_draw_problem_tail_window():
         assert 0.003 <= tail <= 0.30
 
 
-def test_rows_and_labels():
+def test_rows_and_targets():
     feats = np.arange(24, dtype=float).reshape(2, 12)
     tab = np.full((5, 3), np.inf)
-    tab[3, 0] = 5e-3        # feasible for requests >= 5e-3
-    tab[4, 2] = 5e-4        # feasible for requests >= 5e-4
-    tabs = np.array([tab, tab])
-    X, yq, yp, idx, ts = learn.rows(feats, np.array([20, 40]), tabs, [[1e-2, 1e-3], [1e-4]], margin=1.0)
-    assert X.shape == (3, 13) and list(idx) == [0, 0, 1]
-    np.testing.assert_allclose(X[:, 12], np.log10([1e-2, 1e-3, 1e-4]))
-    assert (yq[0], yp[0]) == (3, 0) and (yq[1], yp[1]) == (4, 2) and (yq[2], yp[2]) == (4, 2)
+    tab[3, 0] = 5e-3
+    tab[4, 2] = 5e-5
+    X, Y = learn.rows(feats, np.array([tab, tab]))
+    assert X.shape == (2, 12) and Y.shape == (2, 15)
+    np.testing.assert_allclose(Y[0], mo.error_target(tab)[0])
+    assert Y[0, 3 * 3 + 0] == np.log10(5e-3) and Y[0, 4 * 3 + 2] == -4.0 and Y[0, 0] == 1.0
+
+
+def test_choose_and_targets_match_reference():
+    g = inputs.rng(13)
+    for trial in range(300):
+        k = int(g.integers(1, 200))
+        est = g.uniform(-4, 0.5, mo.N_OUT)
+        t = 10.0 ** g.uniform(-3, -1)
+        delta = float(g.uniform(0, 0.5))
+        assert learn.choose_from_estimates(est, k, t, delta) == mo.choose(est, k, t, delta)
+    tab = 10.0 ** g.uniform(-6, 2, size=(5, 3))
+    tab[0, 1] = np.inf
+    np.testing.assert_array_equal(learn.error_target(tab), mo.error_target(tab))
+
+
+def test_calibrate_is_the_residual_quantile():
+    """delta = the chosen quantile of measured - estimated over the entries
+    within a decade of the request range; estimates off by a constant c give
+    delta = c."""
+    g = inputs.rng(14)
+    tabs = 10.0 ** g.uniform(-3.5, -0.5, size=(40, 5, 3))
+    Y = np.concatenate([mo.error_target(t) for t in tabs])
+    assert abs(learn.calibrate(Y - 0.25, tabs) - 0.25) < 1e-12
+    r = g.standard_normal(Y.shape) * 0.1
+    d = learn.calibrate(Y - r, tabs, quantile=0.9)
+    assert abs(d - np.quantile(r, 0.9)) < 1e-12
 
 
 def test_evaluate_at_counts():
@@ -88,15 +113,3 @@ def test_evaluate_at_counts():
     assert r["default_success"] == 0.5 and r["matched_fixed"] is None
     r = learn.evaluate_at(np.array([0, 0]), np.array([0, 0]), tabs, ks, 1e-2)
     assert r["learned_success"] == 0.5 and r["matched_fixed"] == [0, 5]
-
-
-def test_rows_margin_tightens_labels():
-    feats = np.zeros((1, 12))
-    tab = np.full((5, 3), np.inf)
-    tab[1, 0] = 8e-3        # reaches 1e-2, not 1e-2 / 2
-    tab[3, 0] = 4e-3        # reaches both
-    tabs = np.array([tab])
-    _, yq, yp, _, _ = learn.rows(feats, np.array([20]), tabs, [[1e-2]], margin=1.0)
-    assert (yq[0], yp[0]) == (1, 0)
-    _, yq, yp, _, _ = learn.rows(feats, np.array([20]), tabs, [[1e-2]], margin=2.0)
-    assert (yq[0], yp[0]) == (3, 0)

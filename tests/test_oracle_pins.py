@@ -349,3 +349,31 @@ def test_omega_ratio_closed_form():
     assert abs(float(np.linalg.norm((U @ Om[:, :k])[k:] @ np.linalg.inv((U @ Om[:, :k])[:k]), 2)) - want) > 1e-3
     assert abs(float(np.linalg.norm(Ot[k:, :k] @ Ot[:k, :k], 2)) - want) > 1e-3
     assert abs(float(np.linalg.norm(Ot[k:, :k], 2)) - want) > 1e-3
+
+
+@pytest.mark.parametrize("a,b", [(0.3, 1.1), (1.2, 0.2), (0.0, 0.5)])
+def test_subspace_sines_and_cosines_closed_form(a, b):
+    """All canonical angles of the two rotated planes: sines {sin a, sin b},
+    cosines {cos a, cos b}, largest first; the largest sine is subspace_sin."""
+    from oracle.bounds import subspace_cosines, subspace_sines
+    X, Y = _planes(a, b, inputs.rng(321))
+    np.testing.assert_allclose(subspace_sines(X, Y), sorted([np.sin(a), np.sin(b)], reverse=True), atol=1e-13)
+    np.testing.assert_allclose(subspace_cosines(X, Y), sorted([np.cos(a), np.cos(b)], reverse=True), atol=1e-13)
+    assert abs(subspace_sines(X, Y)[0] - subspace_sin(X, Y)) < 1e-13
+
+
+def test_rank_r_errors_identity():
+    """The identity against the explicit residual of A_r = Q L(:, 1:r) P(:, 1:r)^T
+    (section 5.2) for every r, and against the tail of an exact low-rank A
+    (rank 6, d = 10: from r = 6 on the error is 0 up to rounding)."""
+    m, n = 80, 60
+    A = _matrix(m, n, inputs.exp_spectrum(n, 5.0), seed=131, noise=1e-3)
+    Om = inputs.omega(m, 12, 132).astype(np.float64)
+    Q, L, P = orc.rand_qlp(A, Om, 1)
+    errs = orc.rank_r_errors(A, L)
+    for r in range(1, 13):
+        assert abs(errs[r - 1] - orc.rank_r_error_fro(A, Q, L, P, r)) < 1e-10 * np.linalg.norm(A)
+    B = _matrix(m, n, np.linspace(2.0, 1.0, 6), seed=133)
+    Q, L, P = orc.rand_qlp(B, inputs.omega(m, 10, 134).astype(np.float64), 0)
+    e = orc.rank_r_errors(B, L)
+    assert np.all(e[5:] < 1e-6 * np.linalg.norm(B)) and e[4] > 0.5
