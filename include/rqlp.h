@@ -363,6 +363,35 @@ rqlp_status rqlp_factor_batched(int count, const rqlp_problem* probs, int q, voi
                                 size_t ws_bytes, int* d_info, double* d_diag, const rqlp_opts* opts,
                                 void* stream);
 
+/* ---- Sparse A (section 5.1 factors sparse matrices; Algorithm 1 touches A
+ * only through products with A and A^T).
+ *
+ * rqlp_factor_sparse: the chain of rqlp_factor for A in CSR form (device
+ * arrays: row_ptr (m + 1 int64, row_ptr[0] = 0, non-decreasing, row_ptr[m] =
+ * nnz), col_idx (nnz int32 in [0, n)), vals (nnz float)); the passes over A
+ * are sparse-times-dense products (a warp per row, the nonzeros of a row in
+ * storage order, FP32), and A^T is built on the device in CSR form at the
+ * start of every call (column counts, scan, scatter, each column sorted by
+ * row: every sum runs in a fixed order). Other arguments, outputs and
+ * errors as for rqlp_factor; FP32 only (opts->precision = RQLP_PREC_FP32,
+ * else RQLP_ERR_UNSUPPORTED: the products are gathers, not dense
+ * contractions), step 5 on the d x d R. A column index outside [0, n) or a
+ * decreasing row pointer is skipped and reported as RQLP_ERR_ARG in d_info.
+ * workspace: rqlp_sparse_workspace_bytes(A, k, p, q, opts) bytes, 256-byte
+ * aligned (the chain's workspace plus A^T: 8 (n + 1) + 8 nnz + 4 n bytes). */
+typedef struct {
+  int64_t m, n, nnz;
+  const int64_t* row_ptr;
+  const int* col_idx;
+  const float* vals;
+} rqlp_csr;
+size_t rqlp_sparse_workspace_bytes(const rqlp_csr* A, int k, int p, int q, const rqlp_opts* opts);
+rqlp_status rqlp_factor_sparse(const rqlp_csr* A, int k, int p, int q,
+                               const float* Omega, int64_t ldo,
+                               float* Q, int64_t ldq, float* L, int64_t ldl, float* P, int64_t ldp,
+                               void* workspace, size_t ws_bytes, int* d_info, double* d_diag,
+                               const rqlp_opts* opts, void* stream);
+
 /* ---- Evaluation utilities on the device (section 5.2: rank-r
  * approximations; section 4.1, Theorem 2: distances between subspaces).
  *

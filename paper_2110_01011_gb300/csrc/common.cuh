@@ -142,6 +142,20 @@ cudaError_t add_matrix(int64_t rows, int64_t cols, const float* X, int64_t ldx, 
 cudaError_t copy_matrix(int64_t rows, int64_t cols, const float* X, int64_t ldx, float* Y, int64_t ldy,
                         cudaStream_t st, const int* gate = nullptr);
 
+// ---------------------------------------------------------------- sparse A (CSR, device arrays)
+struct SparseA {
+  int64_t m, n, nnz;
+  const int64_t* row_ptr;   // m + 1
+  const int* col_idx;       // nnz
+  const float* vals;        // nnz
+};
+// Device bytes for A's transpose in CSR form (built by sparse_build_csc).
+size_t sparse_csc_bytes(int64_t n, int64_t nnz);
+cudaError_t sparse_build_csc(const SparseA& a, void* ws, SparseA* t, int* info, cudaStream_t st);
+// Y (s.m x d) = S X (X s.n x d); sumsq += sum of S's squared values (optional).
+cudaError_t sparse_spmm(const SparseA& s, const float* X, int64_t ldx, int d, float* Y, int64_t ldy, double* sumsq,
+                        int* info, cudaStream_t st);
+
 // ---------------------------------------------------------------- learned (q, p)
 size_t mlp_workspace_floats(int batch);
 cudaError_t mlp_forward(const float* prm, const float* X, int batch, float* est, cudaStream_t st);

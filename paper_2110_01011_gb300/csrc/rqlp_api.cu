@@ -33,6 +33,11 @@ class Ops {
 
   // Three BF16 parts per pass operand (six products) instead of two.
   void set_three_part(bool on) { three_ = on; }
+  // Sparse A (CSR) and its transpose: the passes become sparse products.
+  void set_sparse(const SparseA* a, const SparseA* at) {
+    sp_ = a;
+    spt_ = at;
+  }
   bool three_part() const { return three_; }
 
   // part_floats: largest split-K partial buffer any product of the caller needs.
@@ -92,6 +97,13 @@ class Ops {
   // transA: out (n x d) = A^T X (X m x d); else out (m x d) = A X (X n x d).
   cudaError_t pass(bool transA, const float* A, int64_t m, int64_t n, int64_t lda, const float* X,
                    int64_t ldx, float* out, int64_t ldout, double* sumsq) {
+    if (sp_ != nullptr) {
+      const bool prof = profiling_on();
+      if (prof) profile_mark_begin(st_);
+      cudaError_t e = sparse_spmm(transA ? *spt_ : *sp_, X, ldx, d_, out, ldout, sumsq, info_, st_);
+      if (prof) profile_mark_end(st_, transA ? 1 : 0);
+      return e;
+    }
     if (o_.precision == RQLP_PREC_BF16X3)   // the engine brackets its MMA kernel when profiling
       return tc_.pass(transA, A, m, n, lda, X, ldx, d_, out, ldout, sumsq, info_, st_, three_);
     const bool prof = profiling_on();
@@ -230,6 +242,8 @@ class Ops {
   TcEngine tc_, tcs_;
   bool tc_on_ = false;
   bool three_ = false;
+  const SparseA* sp_ = nullptr;
+  const SparseA* spt_ = nullptr;
 };
 
 struct Dims {
@@ -332,6 +346,25 @@ class Plan {
       CK(ops_.pass(true, A, d_.m, d_.n, d_.lda, Om, d_.ldo, Y_, ops_.ld(), &ops_.scal[0]));
     }
     return chain(A, d_.q, out, info, diag, st);
+  }
+
+  // The chain for a sparse A: its transpose (CSR) is built into csc_ws
+  // first, then every pass is a sparse product.
+  cudaError_t run_sparse(const SparseA& a, void* csc_ws, const float* Om, const Out& out, int* info, double* diag,
+                         cudaStream_t st) {
+    ops_.bind(st, info);
+    CK(ops_.init());
+    {
+      Range r("rqlp: sparse transpose");
+      CK(sparse_build_csc(a, csc_ws, &at_, info, st));
+    }
+    a_ = a;
+    ops_.set_sparse(&a_, &at_);
+    {
+      Range r("rqlp: sketch Y = A^T Omega (sparse)");
+      CK(ops_.pass(true, nullptr, d_.m, d_.n, d_.n, Om, d_.ldo, Y_, ops_.ld(), &ops_.scal[0]));
+    }
+    return chain(nullptr, d_.q, out, info, diag, st);
   }
 
   // Probe sketch of the full width, its R factor, features, the network's
@@ -456,6 +489,7 @@ class Plan {
   Dims d_;
   Ops ops_;
   rqlp_opts o_;
+  SparseA a_{}, at_{};
   float *Y_ = nullptr, *Z_ = nullptr, *Pt_ = nullptr, *T1_ = nullptr;
   float *Rb_ = nullptr, *Rh_ = nullptr, *Ts_ = nullptr, *Ts2_ = nullptr, *Ph_ = nullptr;
   float *feat_ = nullptr, *logits_ = nullptr;
@@ -884,6 +918,45 @@ rqlp_status rqlp_factor_learned_host(const float* hA, int64_t m, int64_t n, int6
            cudaSuccess))
     return fail(RQLP_ERR_CUDA);
   return cudaStreamSynchronize(st) == cudaSuccess ? RQLP_OK : fail(RQLP_ERR_CUDA);
+}
+
+namespace {
+bool valid_csr(const rqlp_csr* A) {
+  return A != nullptr && A->m > 0 && A->n > 0 && A->nnz >= 0 && A->row_ptr != nullptr &&
+         (A->nnz == 0 || (A->col_idx != nullptr && A->vals != nullptr)) && A->nnz < (int64_t(1) << 31);
+}
+}  // namespace
+
+size_t rqlp_sparse_workspace_bytes(const rqlp_csr* A, int k, int p, int q, const rqlp_opts* opts) {
+  rqlp_opts o = resolve(opts);
+  if (!valid_csr(A) || !valid_opts(o) || o.precision != RQLP_PREC_FP32 || o.literal_step5 != 0 ||
+      !valid_sizes(A->m, A->n, k, p, q))
+    return 0;
+  return round_up((int64_t)plan_bytes(make_dims(A->m, A->n, A->n, k, p, q, k + p), o), 256) +
+         sparse_csc_bytes(A->n, A->nnz);
+}
+
+rqlp_status rqlp_factor_sparse(const rqlp_csr* A, int k, int p, int q, const float* Omega, int64_t ldo, float* Q,
+                               int64_t ldq, float* L, int64_t ldl, float* P, int64_t ldp, void* workspace,
+                               size_t ws_bytes, int* d_info, double* d_diag, const rqlp_opts* opts, void* stream) {
+  rqlp_opts o = resolve(opts);
+  if (!valid_csr(A) || !valid_opts(o) || !valid_sizes(A->m, A->n, k, p, q)) return RQLP_ERR_ARG;
+  if (o.precision != RQLP_PREC_FP32 || o.literal_step5 != 0) return RQLP_ERR_UNSUPPORTED;
+  const int d = k + p;
+  if (Omega == nullptr || Q == nullptr || L == nullptr || P == nullptr || d_info == nullptr) return RQLP_ERR_ARG;
+  if (ldo < d || ldq < d || ldl < d || ldp < d) return RQLP_ERR_ARG;
+  const size_t need = rqlp_sparse_workspace_bytes(A, k, p, q, &o);
+  if (workspace == nullptr || ws_bytes < need || !aligned(workspace, 256)) return RQLP_ERR_WORKSPACE;
+  Dims dm = make_dims(A->m, A->n, A->n, k, p, q, ldo);
+  const size_t core = (size_t)round_up((int64_t)plan_bytes(dm, o), 256);
+  Arena ar = arena_over(workspace, core);
+  Plan pl(dm, o);
+  pl.layout(ar);
+  SparseA a{A->m, A->n, A->nnz, A->row_ptr, A->col_idx, A->vals};
+  Out out{Q, ldq, L, ldl, P, ldp};
+  cudaError_t e = pl.run_sparse(a, static_cast<char*>(workspace) + core, Omega, out, d_info, d_diag,
+                                static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? RQLP_OK : RQLP_ERR_CUDA;
 }
 
 const char* rqlp_status_string(int status) {

@@ -29,7 +29,8 @@ import numpy as np
 __all__ = [
     "rng", "omega", "round_to_bf16", "haar_columns", "step_spectrum",
     "exp_spectrum", "poly_spectrum", "low_rank_matrix", "low_rank_matrix_torch",
-    "omega_torch", "Problem", "random_batch", "e3_spectrum",
+    "omega_torch", "Problem", "random_batch", "e3_spectrum", "SPARSE_SIZES", "sparse_matrix",
+    "csr_to_dense",
 ]
 
 
@@ -245,3 +246,38 @@ def random_batch(count: int, seed: int, m_range=(256, 4096), n_range=(256, 2048)
             kind, par = "poly", float(g.uniform(0.5, 3.0))
         out.append(Problem(m, n, k, p, q, kind, par, seed * 100003 + t))
     return out
+
+
+# Square sizes of the sparse test matrices of section 5.1 (Table 1); the
+# matrices themselves are not available here, so seeded stand-ins of those
+# sizes take their place (``sparse_matrix``).
+SPARSE_SIZES = (1856, 2904, 4929, 6747, 7320)
+
+
+def sparse_matrix(m: int, n: int, seed: int, band: int = 2, extra: int = 8):
+    """Seeded sparse stand-in in CSR form: a band |i - j| <= band (clipped to
+    the matrix) plus ``extra`` uniformly random columns per row, standard
+    normal values, rows sorted by column, no duplicates. Returns (row_ptr
+    int64 (m + 1), col_idx int32, vals float32)."""
+    g = rng(seed)
+    rows, cols = [], []
+    for i in range(m):
+        c = set(range(max(0, i - band), min(n, i + band + 1)))
+        c.update(int(x) for x in g.integers(0, n, size=extra))
+        c = sorted(c)
+        rows.append(len(c))
+        cols.extend(c)
+    row_ptr = np.zeros(m + 1, dtype=np.int64)
+    row_ptr[1:] = np.cumsum(rows)
+    col_idx = np.asarray(cols, dtype=np.int32)
+    vals = g.standard_normal(col_idx.size).astype(np.float32)
+    return row_ptr, col_idx, vals
+
+
+def csr_to_dense(m: int, n: int, row_ptr, col_idx, vals) -> np.ndarray:
+    """The dense m x n FP64 matrix of a CSR triple (for the oracle)."""
+    A = np.zeros((m, n), dtype=np.float64)
+    for i in range(m):
+        s, e = int(row_ptr[i]), int(row_ptr[i + 1])
+        A[i, col_idx[s:e]] = vals[s:e]
+    return A

@@ -40,7 +40,8 @@ EXPORTED = ["rqlp_default_opts", "rqlp_workspace_bytes", "rqlp_factor", "rqlp_ho
             "rqlp_orth_workspace_bytes", "rqlp_orth", "rqlp_mlp_forward", "rqlp_mlp_workspace_bytes",
             "rqlp_mlp_grad", "rqlp_mlp_adam", "rqlp_learned_workspace_bytes", "rqlp_probe_features",
             "rqlp_predict_qp", "rqlp_factor_learned", "rqlp_learned_host_workspace_bytes",
-            "rqlp_factor_learned_host", "rqlp_rank_errors", "rqlp_rank_residual_workspace_bytes",
+            "rqlp_factor_learned_host", "rqlp_sparse_workspace_bytes", "rqlp_factor_sparse",
+            "rqlp_rank_errors", "rqlp_rank_residual_workspace_bytes",
             "rqlp_rank_residual", "rqlp_subspace_workspace_bytes", "rqlp_subspace_angles",
             "rqlp_batch_workspace_bytes", "rqlp_batch_create",
             "rqlp_batch_autotune", "rqlp_batch_tuning", "rqlp_batch_run", "rqlp_batch_launch",
@@ -60,6 +61,12 @@ class Problem(ctypes.Structure):
                 ("Omega", ctypes.c_void_p), ("ldo", ctypes.c_int64), ("k", ctypes.c_int), ("p", ctypes.c_int),
                 ("Q", ctypes.c_void_p), ("ldq", ctypes.c_int64), ("L", ctypes.c_void_p), ("ldl", ctypes.c_int64),
                 ("P", ctypes.c_void_p), ("ldp", ctypes.c_int64)]
+
+
+class Csr(ctypes.Structure):
+    """rqlp_csr: a sparse A in CSR form (device arrays)."""
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("row_ptr", ctypes.c_void_p),
+                ("col_idx", ctypes.c_void_p), ("vals", ctypes.c_void_p)]
 
 
 class RqlpError(RuntimeError):
@@ -123,6 +130,11 @@ def _declare(lib):
     lib.rqlp_factor_learned_host.argtypes = [_vp, _i64, _i64, _i64, _int, _vp, _i64, _d, _vp, _vp, _i64, _vp,
                                              _i64, _vp, _i64, _vp, _sz, _vp, _vp, _vp, ctypes.POINTER(Opts), _vp]
     lib.rqlp_factor_learned_host.restype = _int
+    lib.rqlp_sparse_workspace_bytes.argtypes = [ctypes.POINTER(Csr), _int, _int, _int, ctypes.POINTER(Opts)]
+    lib.rqlp_sparse_workspace_bytes.restype = _sz
+    lib.rqlp_factor_sparse.argtypes = [ctypes.POINTER(Csr), _int, _int, _int, _vp, _i64, _vp, _i64, _vp, _i64, _vp,
+                                       _i64, _vp, _sz, _vp, _vp, ctypes.POINTER(Opts), _vp]
+    lib.rqlp_factor_sparse.restype = _int
     lib.rqlp_rank_errors.argtypes = [_vp, _i64, _int, _vp, _vp, _vp]
     lib.rqlp_rank_errors.restype = _int
     lib.rqlp_rank_residual_workspace_bytes.argtypes = [_i64, _int]
@@ -547,6 +559,38 @@ def factor_learned_host(A, k, Omega, params, target, precision=PREC_BF16X3, work
         raise RqlpError(st, "rqlp_factor_learned_host")
     d = k + qp[1]
     return Q[:, :d], L[:d, :d], P[:, :d], info, diag, (qp[0], qp[1])
+
+
+def rqlp_sparse_workspace_bytes(csr, k, p, q, opts=None):
+    return int(load().rqlp_sparse_workspace_bytes(ctypes.byref(csr), k, p, q, ctypes.byref(opts or _opts())))
+
+
+def factor_sparse(row_ptr, col_idx, vals, m, n, k, p, q, Omega, workspace=None):
+    """Rand-QLP of a sparse A in CSR form (CUDA int64 row_ptr, int32 col_idx,
+    float32 vals) with Omega (CUDA float32, m x (k+p)). Returns (Q, L, P,
+    info, diag) as CUDA tensors (asynchronous)."""
+    import torch
+    d = k + p
+    csr = Csr(m, n, int(col_idx.numel()), row_ptr.data_ptr(), col_idx.data_ptr(), vals.data_ptr())
+    opts = _opts(PREC_FP32)
+    nb = rqlp_sparse_workspace_bytes(csr, k, p, q, opts)
+    if nb == 0:
+        raise RqlpError(1, "rqlp_sparse_workspace_bytes")
+    dev = Omega.device
+    if workspace is None or workspace.numel() < nb + 256:
+        workspace = torch.empty(nb + 256, dtype=torch.uint8, device=dev)
+    ws = (workspace.data_ptr() + 255) // 256 * 256
+    Q = torch.empty(m, d, device=dev)
+    L = torch.empty(d, d, device=dev)
+    P = torch.empty(n, d, device=dev)
+    info = torch.empty(2, dtype=torch.int32, device=dev)
+    diag = torch.empty(4, dtype=torch.float64, device=dev)
+    st = int(load().rqlp_factor_sparse(ctypes.byref(csr), k, p, q, Omega.data_ptr(), Omega.stride(0), Q.data_ptr(),
+                                       Q.stride(0), L.data_ptr(), L.stride(0), P.data_ptr(), P.stride(0), ws, nb,
+                                       info.data_ptr(), diag.data_ptr(), ctypes.byref(opts), _stream()))
+    if st != 0:
+        raise RqlpError(st, "rqlp_factor_sparse")
+    return Q, L, P, info, diag
 
 
 def rank_errors(L, diag):

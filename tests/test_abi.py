@@ -112,3 +112,21 @@ def test_factor_argument_errors_without_device_work(lib):
     assert call(k=78, p=5) == 1       # d > min(m, n)
     assert call(ws_bytes=10) == 6     # workspace too small
     assert call(workspace=fake + 8) == 6   # misaligned
+
+
+def test_sparse_workspace_rules(lib):
+    """Sizing of the sparse path: the chain's workspace plus A^T in CSR form;
+    FP32 only; invalid descriptors size to 0 (no device pointer is read)."""
+    fake = 0x1000
+    m, n, nnz = 1000, 800, 12000
+    csr = rqlp.Csr(m, n, nnz, fake, fake, fake)
+    o = rqlp.rqlp_default_opts()
+    nb = rqlp.rqlp_sparse_workspace_bytes(csr, 20, 5, 1, o)
+    dense = rqlp.rqlp_workspace_bytes(m, n, 20, 5, 1, o)
+    assert nb >= dense + 8 * (n + 1) + 8 * nnz + 4 * n
+    o.precision = rqlp.PREC_BF16X3
+    assert rqlp.rqlp_sparse_workspace_bytes(csr, 20, 5, 1, o) == 0
+    o = rqlp.rqlp_default_opts()
+    assert rqlp.rqlp_sparse_workspace_bytes(rqlp.Csr(m, n, nnz, None, fake, fake), 20, 5, 1, o) == 0
+    assert rqlp.rqlp_sparse_workspace_bytes(rqlp.Csr(0, n, nnz, fake, fake, fake), 20, 5, 1, o) == 0
+    assert rqlp.rqlp_sparse_workspace_bytes(csr, 790, 20, 1, o) == 0     # d > min(m, n)
