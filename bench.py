@@ -304,20 +304,21 @@ def time_steps(ctx, fn, steps):
     return ctx.max_over_ranks(e0.elapsed_time(e1) / steps)
 
 
-def fixed_runner(a, A, Om, q, p, prec, dev, small_fp64=False):
+def fixed_runner(a, A, Om, q, p, prec, dev, small_fp64=False, fused=False):
     import torch
 
     from paper_2110_01011_gb300 import rqlp
     d = a.k + p
     parts = a.parts if prec == rqlp.PREC_BF16X3 else 0
-    opts = rqlp._opts(prec, small_fp64, parts=parts)
+    opts = rqlp._opts(prec, small_fp64, parts=parts, fused=fused)
     ws = torch.empty(rqlp.rqlp_workspace_bytes(a.m, a.n, a.k, p, q, opts) + 256, dtype=torch.uint8, device=dev)
     out = (torch.empty(a.m, d, device=dev), torch.empty(d, d, device=dev), torch.empty(a.n, d, device=dev),
            torch.empty(2, dtype=torch.int32, device=dev), torch.empty(4, dtype=torch.float64, device=dev))
     Omp = Om[:, :d]
 
     def step():
-        rqlp.factor(A, a.k, p, q, Omp, precision=prec, small_fp64=small_fp64, workspace=ws, out=out, parts=parts)
+        rqlp.factor(A, a.k, p, q, Omp, precision=prec, small_fp64=small_fp64, workspace=ws, out=out, parts=parts,
+                    fused=fused)
     return step, out
 
 
@@ -660,6 +661,14 @@ def main():
         ctx.barrier()
         compare["bf16x3_fixed_small_fp64_ms_per_step"] = time_steps(ctx, s64, 3)
         del s64, o64
+        torch.cuda.empty_cache()
+        # power passes fused as A^T (A P~) over L2-sized row panels
+        sfu, ofu = fixed_runner(a, A, Om, 2, 10, rqlp.PREC_BF16X3, dev, fused=True)
+        sfu()
+        ctx.barrier()
+        compare["bf16x3_fixed_fused_power_ms_per_step"] = time_steps(ctx, sfu, 3)
+        compare["bf16x3_fixed_fused_power_excess_error"] = acc(ofu[2])["excess_error"]
+        del sfu, ofu
         torch.cuda.empty_cache()
         # the bench matrix's excess errors for every (q, p) (one width-(k + 20)
         # FP32 chain, FP64 residuals) and the network's picks across requests

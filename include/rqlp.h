@@ -86,7 +86,13 @@ typedef struct {
                    /* agree when rank(A) <= d or d = n; with d = n, q = 0   */
                    /* and 1 the chain is Algorithm 1 as printed. Single-    */
                    /* matrix entry points only (0 for the batched form)     */
-  int reserved[3]; /* must be zero                                            */
+  int fused_power; /* 1: each power pass as Y = A^T (A P~) by row panels of A */
+                   /* small enough to stay in L2, Z = A P~ not              */
+                   /* orthonormalised (its span is all the next product     */
+                   /* needs): one pass over A from HBM per power pass       */
+                   /* instead of two; 0: the two passes with qf(Z) between   */
+                   /* (default). Dense single-matrix entry points only       */
+  int reserved[2]; /* must be zero                                            */
 } rqlp_opts;
 
 /* d_info layout written by rqlp_factor (2 ints): [0] = rqlp_status of the

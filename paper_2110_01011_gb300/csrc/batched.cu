@@ -734,8 +734,8 @@ bool valid_batch(int count, const rqlp_problem* probs, int q, const rqlp_opts& o
   if (o.test_stall != 0 && (o.test_stall != 1 || o.precision != RQLP_PREC_BF16X3)) return false;
   if (o.bf16_parts != 0 && (o.precision != RQLP_PREC_BF16X3 || (o.bf16_parts != 2 && o.bf16_parts != 3)))
     return false;
-  if (o.literal_step5 != 0) return false;
-  for (int i = 0; i < 3; ++i)
+  if (o.literal_step5 != 0 || o.fused_power != 0) return false;
+  for (int i = 0; i < 2; ++i)
     if (o.reserved[i] != 0) return false;
   for (int i = 0; i < count; ++i)
     if (!valid_problem(probs[i])) return false;

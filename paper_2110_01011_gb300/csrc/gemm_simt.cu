@@ -222,6 +222,193 @@ gemm_grouped_kernel(const GroupGemm* __restrict__ jobs, const int* __restrict__ 
   }
 }
 
+// Wide tile for the passes over A and the tall products with N >= 96: one
+// 128 x 128 tile of C per CTA of 256 threads, 8 x 8 outputs per thread in two
+// 4-wide row groups (ty * 4 .., 64 + ty * 4 ..) and two 4-wide column groups
+// (tx * 4 .., 64 + tx * 4 ..), so that four conflict-free 128-bit shared loads
+// feed 64 FMAs (the 128 x 64 tile needs three per 32). VEC: A and B are
+// 16-byte aligned with row strides that are multiples of 4 floats, and tiles
+// are fetched with 128-bit global loads. Same K slicing, gates, sum of
+// squares and two-level accumulation as gemm_tile.
+constexpr int kWideBM = 128, kWideBN = 128, kWideBK = 16, kWideThreads = 256;
+
+template <bool TRANS_A, bool VEC>
+__global__ void __launch_bounds__(kWideThreads, 1) gemm_f32_wide_kernel(GemmArgs g) {
+  constexpr int BM = kWideBM, BN = kWideBN, BK = kWideBK, NT = kWideThreads;
+  __shared__ __align__(16) float As[2][BK][BM + 4];
+  __shared__ __align__(16) float Bs[2][BK][BN];
+  const int tid = threadIdx.x;
+  const int tx = tid % 16, ty = tid / 16;
+  const int64_t m0 = (int64_t)blockIdx.y * BM, n0 = (int64_t)blockIdx.x * BN;
+  const int slice = blockIdx.z;
+  float* C = g.C + (int64_t)slice * g.c_slice;
+
+  if (g.gate != nullptr && *g.gate == 0) {
+    if (g.gate_mode == kGateSkip) return;
+    for (int idx = tid; idx < BM * BN; idx += NT) {   // B taken as the identity (see gemm_tile)
+      const int64_t gm = m0 + idx / BN, gn = n0 + idx % BN;
+      if (gm < g.M && gn < g.N) C[gm * g.ldc + gn] = g.A[gm * g.lda + gn];
+    }
+    return;
+  }
+
+  const int64_t kbeg = (int64_t)slice * g.kchunk;
+  int64_t kend = kbeg + g.kchunk < g.K ? kbeg + g.kchunk : g.K;
+  if (g.b_upper && kend > n0 + BN) kend = n0 + BN;
+  const int64_t ntiles = kend > kbeg ? cdiv(kend - kbeg, BK) : 0;
+  const bool want_sq = g.sumsq != nullptr && n0 == 0;
+  float sq = 0.f, sq_c = 0.f;
+
+  // Per thread and K tile: two float4 of A and two of B (512 of each per tile).
+  float4 ra[2], rb[2];
+  auto load = [&](int64_t k0) {
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int f = tid + r * NT;
+      float v[4];
+      if (TRANS_A) {   // A stored K x M: tile row kk, columns mq * 4 .. + 3
+        const int kk = f / 32, mq = f % 32;
+        const int64_t gk = k0 + kk, gm = m0 + mq * 4;
+        const float* src = g.A + gk * g.lda + gm;
+        if (VEC && gk < kend && gm + 3 < g.M) {
+          const float4 t = *reinterpret_cast<const float4*>(src);
+          v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+        } else {
+#pragma unroll
+          for (int i = 0; i < 4; ++i) v[i] = (gk < kend && gm + i < g.M) ? src[i] : 0.f;
+        }
+      } else {         // A stored M x K: row, k columns kq * 4 .. + 3
+        const int row = f / 4, kq = f % 4;
+        const int64_t gm = m0 + row, gk = k0 + kq * 4;
+        const float* src = g.A + gm * g.lda + gk;
+        if (VEC && gm < g.M && gk + 3 < kend) {
+          const float4 t = *reinterpret_cast<const float4*>(src);
+          v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+        } else {
+#pragma unroll
+          for (int i = 0; i < 4; ++i) v[i] = (gm < g.M && gk + i < kend) ? src[i] : 0.f;
+        }
+      }
+      ra[r] = make_float4(v[0], v[1], v[2], v[3]);
+      {
+        const int kk = f / 32, nq = f % 32;
+        const int64_t gk = k0 + kk, gn = n0 + nq * 4;
+        const float* src = g.B + gk * g.ldb + gn;
+        float w[4];
+        if (VEC && gk < kend && gn + 3 < g.N) {
+          const float4 t = *reinterpret_cast<const float4*>(src);
+          w[0] = t.x; w[1] = t.y; w[2] = t.z; w[3] = t.w;
+        } else {
+#pragma unroll
+          for (int i = 0; i < 4; ++i) w[i] = (gk < kend && gn + i < g.N) ? src[i] : 0.f;
+        }
+        rb[r] = make_float4(w[0], w[1], w[2], w[3]);
+      }
+    }
+    if (want_sq) {
+      float s = 0.f;
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        s = fmaf(ra[r].x, ra[r].x, s); s = fmaf(ra[r].y, ra[r].y, s);
+        s = fmaf(ra[r].z, ra[r].z, s); s = fmaf(ra[r].w, ra[r].w, s);
+      }
+      const float y = s - sq_c, t = sq + y;
+      sq_c = (t - sq) - y;
+      sq = t;
+    }
+  };
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int f = tid + r * NT;
+      if (TRANS_A) {
+        *reinterpret_cast<float4*>(&As[buf][f / 32][(f % 32) * 4]) = ra[r];
+      } else {
+        const int row = f / 4, k = (f % 4) * 4;
+        As[buf][k][row] = ra[r].x; As[buf][k + 1][row] = ra[r].y;
+        As[buf][k + 2][row] = ra[r].z; As[buf][k + 3][row] = ra[r].w;
+      }
+      *reinterpret_cast<float4*>(&Bs[buf][f / 32][(f % 32) * 4]) = rb[r];
+    }
+  };
+
+  constexpr int kPromoteTiles = 256 / BK;
+  float acc[8][8], tot[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = tot[i][j] = 0.f;
+
+  if (ntiles > 0) {
+    load(kbeg);
+    store(0);
+    __syncthreads();
+    for (int64_t t = 0; t < ntiles; ++t) {
+      const int buf = (int)(t & 1);
+      if (t + 1 < ntiles) load(kbeg + (t + 1) * BK);
+#pragma unroll
+      for (int kk = 0; kk < BK; ++kk) {
+        const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 4]);
+        const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][kk][64 + ty * 4]);
+        const float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * 4]);
+        const float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][kk][64 + tx * 4]);
+        const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+        const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+      }
+      if (t + 1 < ntiles) store(buf ^ 1);
+      if ((t + 1) % kPromoteTiles == 0) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            tot[i][j] += acc[i][j];
+            acc[i][j] = 0.f;
+          }
+      }
+      __syncthreads();
+    }
+  }
+
+  const bool cvec = (reinterpret_cast<uintptr_t>(C) % 16 == 0) && (g.ldc % 4 == 0);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int64_t gm = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + i - 4);
+    if (gm >= g.M) continue;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int64_t gn = n0 + h * 64 + tx * 4;
+      float v[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) v[j] = acc[i][h * 4 + j] + tot[i][h * 4 + j];
+      float* dst = C + gm * g.ldc + gn;
+      if (cvec && gn + 3 < g.N) {
+        *reinterpret_cast<float4*>(dst) = make_float4(v[0], v[1], v[2], v[3]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (gn + j < g.N) dst[j] = v[j];
+      }
+    }
+  }
+
+  if (want_sq) {
+    __shared__ double red[NT / 32];
+    double v = (double)sq - (double)sq_c;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((tid & 31) == 0) red[tid >> 5] = v;
+    __syncthreads();
+    if (tid == 0) {
+      double s = 0.0;
+      for (int w = 0; w < NT / 32; ++w) s += red[w];
+      atomicAdd(g.sumsq, s);
+    }
+  }
+}
+
 // C[m, n] = sum_z part[z][m][n] (fixed order, Kahan-compensated FP32).
 __global__ void splitk_reduce_kernel(int64_t M, int64_t N, int splits, const float* __restrict__ part,
                                      float* __restrict__ C, int64_t ldc) {
@@ -239,8 +426,10 @@ __global__ void splitk_reduce_kernel(int64_t M, int64_t N, int splits, const flo
   }
 }
 
-// Tile configuration: a large 128 x 64 tile for the passes over A and the
-// tall products, a small 32 x 32 tile for d x d work.
+// Tile configuration: the wide 128 x 128 tile for the passes over A and the
+// tall products of width N >= 96, a 128 x 64 tile for narrower ones, a small
+// 32 x 32 tile for d x d work.
+bool use_wide(int64_t M, int64_t N) { return M >= 1024 && N >= 96; }
 bool use_big(int64_t M, int64_t N) { return M >= 1024 && N >= 48; }
 
 }  // namespace
@@ -259,9 +448,28 @@ int sm_count() {
 }
 
 int gemm_f32_splits(int64_t M, int64_t N, int64_t K) {
-  const bool big = use_big(M, N);
-  const int64_t BM = big ? 128 : 32, BN = big ? 64 : 32;
+  const bool wide = use_wide(M, N), big = use_big(M, N);
+  const int64_t BM = big ? 128 : 32, BN = wide ? 128 : big ? 64 : 32;
   const int64_t tiles = cdiv(M, BM) * cdiv(N, BN);
+  if (wide) {
+    // One CTA per SM: the fewest K slices (1..8, >= 512 of K per slice) whose
+    // CTAs fill at least 90 % of their waves, else the fullest (314 tiles of
+    // a 20000 x 210 pass fill 69 % of three waves unsplit, 92 % of nine in
+    // four slices).
+    const int64_t nsm = sm_count();
+    int best = 1;
+    double best_eff = 0.0;
+    for (int s = 1; s <= 8 && (s == 1 || K / s >= 512); ++s) {
+      const int64_t ctas = tiles * s;
+      const double eff = (double)ctas / (double)(cdiv(ctas, nsm) * nsm);
+      if (eff > best_eff) {
+        best_eff = eff;
+        best = s;
+      }
+      if (eff >= 0.9) break;
+    }
+    return best;
+  }
   const int64_t resident = (int64_t)sm_count() * (big ? 2 : 8);
   int64_t s = cdiv(resident * 2, tiles);            // about two waves of CTAs
   int64_t maxs = K / 256;                           // keep >= 256 K per slice
@@ -278,7 +486,19 @@ size_t gemm_f32_part_floats(int64_t M, int64_t N, int64_t K) {
 
 static cudaError_t launch_gemm(bool transA, const GemmArgs& g, int splits, cudaStream_t st) {
   const bool big = use_big(g.M, g.N);
-  if (big) {
+  if (use_wide(g.M, g.N)) {
+    const bool vec = reinterpret_cast<uintptr_t>(g.A) % 16 == 0 && reinterpret_cast<uintptr_t>(g.B) % 16 == 0 &&
+                     g.lda % 4 == 0 && g.ldb % 4 == 0;
+    dim3 grid((unsigned)cdiv(g.N, kWideBN), (unsigned)cdiv(g.M, kWideBM), (unsigned)splits);
+    if (transA) {
+      if (vec) gemm_f32_wide_kernel<true, true><<<grid, kWideThreads, 0, st>>>(g);
+      else     gemm_f32_wide_kernel<true, false><<<grid, kWideThreads, 0, st>>>(g);
+    } else {
+      if (vec) gemm_f32_wide_kernel<false, true><<<grid, kWideThreads, 0, st>>>(g);
+      else     gemm_f32_wide_kernel<false, false><<<grid, kWideThreads, 0, st>>>(g);
+    }
+    note_launch();
+  } else if (big) {
     dim3 grid((unsigned)cdiv(g.N, 64), (unsigned)cdiv(g.M, 128), (unsigned)splits);
     if (transA) gemm_f32_kernel<128, 64, 16, 8, 4, true><<<grid, 256, 0, st>>>(g);
     else        gemm_f32_kernel<128, 64, 16, 8, 4, false><<<grid, 256, 0, st>>>(g);

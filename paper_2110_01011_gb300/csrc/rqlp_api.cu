@@ -131,6 +131,46 @@ class Ops {
     if (prof) profile_mark_end(st_, 1);
     return e;
   }
+  // Y (n x d) = A^T (A X) by row panels of A: Z_b = A_b X, then Y += A_b^T Z_b
+  // while A_b is still in L2 (panels of at most ~48 MB of A's pass operands).
+  // Z (m x d, ld_) receives A X, T (n x d, ld_) is scratch. Z is not
+  // orthonormalised: R(A^T A X) = R(A^T qf(A X)), and any triangular right
+  // factor leaves the qf of the product unchanged (reading C3).
+  cudaError_t power_fused(const float* A, int64_t m, int64_t n, int64_t lda, const float* X, int64_t ldx, float* Y,
+                          int64_t ldy, float* Z, float* T) {
+    const bool tc = o_.precision == RQLP_PREC_BF16X3;
+    const int64_t h = fused_rows(m, n, tc ? (three_ ? 6 : 4) : 4);
+    for (int64_t r0 = 0; r0 < m; r0 += h) {   // (in the BF16x3 form A's split is current: the sketch made it)
+      const int64_t rows = std::min(h, m - r0);
+      float* zb = Z + r0 * ld_;
+      float* dst = r0 == 0 ? Y : T;
+      const int64_t ldd = r0 == 0 ? ldy : ld_;
+      if (tc) {
+        CK(tc_.pass_k(false, 0, n, X, ldx, d_, zb, ld_, info_, st_, three_, r0, rows));
+        CK(tc_.pass_k(true, r0, rows, zb, ld_, d_, dst, ldd, info_, st_, three_));
+      } else {
+        CK(gemm_f32_ex(false, rows, d_, n, A + r0 * lda, lda, X, ldx, zb, ld_, gemm_f32_splits(rows, d_, n), part_,
+                       nullptr, nullptr, kGateNone, false, st_));
+        CK(gemm_f32_ex(true, n, d_, rows, A + r0 * lda, lda, zb, ld_, dst, ldd, gemm_f32_splits(n, d_, rows), part_,
+                       nullptr, nullptr, kGateNone, false, st_));
+      }
+      if (r0 > 0) CK(add_matrix(n, d_, T, ld_, Y, ldy, st_));
+    }
+    return cudaSuccess;
+  }
+  // Row-panel height of power_fused: at most ~48 MB of A's pass operands
+  // (bpe bytes per element of A), a multiple of 128 rows.
+  static int64_t fused_rows(int64_t m, int64_t n, int64_t bpe) {
+    return std::min<int64_t>(m, std::max<int64_t>(128, (48ll << 20) / (n * bpe) / 128 * 128));
+  }
+  // Largest split-K partial buffer of power_fused in the FP32 form: a panel's
+  // A_b X has fewer rows than A X, so it may take more K slices.
+  static size_t fused_part_floats(int64_t m, int64_t n, int d) {
+    const int64_t h = fused_rows(m, n, 4), tail = m % h;
+    size_t p = std::max(gemm_f32_part_floats(h, d, n), gemm_f32_part_floats(n, d, h));
+    if (tail > 0) p = std::max({p, gemm_f32_part_floats(tail, d, n), gemm_f32_part_floats(n, d, tail)});
+    return p;
+  }
   static size_t pass_part_floats(int64_t m, int64_t n, int d) {
     return std::max(gemm_f32_part_floats(n, d, m), gemm_f32_part_floats(m, d, n));
   }
@@ -333,6 +373,8 @@ class Plan {
     for (int d = lo; d <= d_.d; ++d)
       part = std::max({part, Ops::pass_part_floats(d_.m, d_.n, d), Ops::orth_part_floats(d_.m, d),
                        Ops::orth_part_floats(d_.n, d), Ops::orth_part_floats(d, d)});
+    if (o_.fused_power != 0 && o_.precision == RQLP_PREC_FP32)
+      for (int d = lo; d <= d_.d; ++d) part = std::max(part, Ops::fused_part_floats(d_.m, d_.n, d));
     ops_.layout(ar, part, o_.precision == RQLP_PREC_BF16X3, d_.m, d_.n);
     return ar.off;
   }
@@ -453,9 +495,13 @@ class Plan {
     }
     for (int i = 1; i <= q; ++i) {
       Range r("rqlp: power pass");
-      CK(ops_.pass(false, A, m, n, lda, Pt_, ld, Z_, ld, nullptr));   // Z = A P~
-      CK(ops_.orth_inter(Z_, ld, m, T1_, ld));                        // Z = qf(Z), one pass
-      CK(ops_.pass(true, A, m, n, lda, T1_, ld, Y_, ld, nullptr));    // Y = A^T Z
+      if (o_.fused_power != 0) {
+        CK(ops_.power_fused(A, m, n, lda, Pt_, ld, Y_, ld, Z_, T1_));   // Y = A^T (A P~)
+      } else {
+        CK(ops_.pass(false, A, m, n, lda, Pt_, ld, Z_, ld, nullptr));   // Z = A P~
+        CK(ops_.orth_inter(Z_, ld, m, T1_, ld));                        // Z = qf(Z), one pass
+        CK(ops_.pass(true, A, m, n, lda, T1_, ld, Y_, ld, nullptr));    // Y = A^T Z
+      }
       if (i == q) CK(ops_.orth_final(Y_, ld, n, Pt_, ld, T1_, nullptr, 0));
       else CK(ops_.orth_inter(Y_, ld, n, Pt_, ld));
     }
@@ -510,7 +556,8 @@ bool valid_opts(const rqlp_opts& o) {
   if (o.bf16_parts != 0 && (o.precision != RQLP_PREC_BF16X3 || (o.bf16_parts != 2 && o.bf16_parts != 3)))
     return false;
   if (o.literal_step5 != 0 && o.literal_step5 != 1) return false;
-  for (int i = 0; i < 3; ++i)
+  if (o.fused_power != 0 && o.fused_power != 1) return false;
+  for (int i = 0; i < 2; ++i)
     if (o.reserved[i] != 0) return false;
   return true;
 }
@@ -930,7 +977,7 @@ bool valid_csr(const rqlp_csr* A) {
 size_t rqlp_sparse_workspace_bytes(const rqlp_csr* A, int k, int p, int q, const rqlp_opts* opts) {
   rqlp_opts o = resolve(opts);
   if (!valid_csr(A) || !valid_opts(o) || o.precision != RQLP_PREC_FP32 || o.literal_step5 != 0 ||
-      !valid_sizes(A->m, A->n, k, p, q))
+      o.fused_power != 0 || !valid_sizes(A->m, A->n, k, p, q))
     return 0;
   return round_up((int64_t)plan_bytes(make_dims(A->m, A->n, A->n, k, p, q, k + p), o), 256) +
          sparse_csc_bytes(A->n, A->nnz);
@@ -941,7 +988,7 @@ rqlp_status rqlp_factor_sparse(const rqlp_csr* A, int k, int p, int q, const flo
                                size_t ws_bytes, int* d_info, double* d_diag, const rqlp_opts* opts, void* stream) {
   rqlp_opts o = resolve(opts);
   if (!valid_csr(A) || !valid_opts(o) || !valid_sizes(A->m, A->n, k, p, q)) return RQLP_ERR_ARG;
-  if (o.precision != RQLP_PREC_FP32 || o.literal_step5 != 0) return RQLP_ERR_UNSUPPORTED;
+  if (o.precision != RQLP_PREC_FP32 || o.literal_step5 != 0 || o.fused_power != 0) return RQLP_ERR_UNSUPPORTED;
   const int d = k + p;
   if (Omega == nullptr || Q == nullptr || L == nullptr || P == nullptr || d_info == nullptr) return RQLP_ERR_ARG;
   if (ldo < d || ldq < d || ldl < d || ldp < d) return RQLP_ERR_ARG;

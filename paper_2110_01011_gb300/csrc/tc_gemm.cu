@@ -74,6 +74,7 @@ constexpr int kChunkK = 4096;
 struct TcArgs {
   int M, K, d, npad, kblocks, tiles, G, stages;
   int k0;                    // A^T X over A's rows k0 .. k0 + K - 1 (X holds those rows); 0 otherwise
+  int m0;                    // A X over A's rows m0 .. m0 + M - 1 (out row 0 = A's row m0); 0 otherwise
   int tpc;                   // > 0: whole tiles per CTA (no split tiles); 0: stream-K
   int vec_out;               // out rows are 16-byte aligned (float4 stores)
   long long units;
@@ -202,10 +203,10 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant_
         tc::tma_load_3d(base + kAP, &tmAlo, &full[stage], 0, kr, 2 * t);
         if (ex) tc::tma_load_3d(base + 2 * kAP, &tmAlo2, &full[stage], 0, kr, 2 * t);
       } else {      // 128 rows (M) x BKP columns (K) of panel kb BKP / 64
-        const int kx = (kb * BKP) & 63, kp = (kb * BKP) >> 6;
-        tc::tma_load_3d(base, &tmAhi, &full[stage], kx, t * BM, kp);
-        tc::tma_load_3d(base + kAP, &tmAlo, &full[stage], kx, t * BM, kp);
-        if (ex) tc::tma_load_3d(base + 2 * kAP, &tmAlo2, &full[stage], kx, t * BM, kp);
+        const int kx = (kb * BKP) & 63, kp = (kb * BKP) >> 6, mr = a.m0 + t * BM;
+        tc::tma_load_3d(base, &tmAhi, &full[stage], kx, mr, kp);
+        tc::tma_load_3d(base + kAP, &tmAlo, &full[stage], kx, mr, kp);
+        if (ex) tc::tma_load_3d(base + 2 * kAP, &tmAlo2, &full[stage], kx, mr, kp);
       }
       tc::tma_load_2d(base + xoff, &tmXhi, &full[stage], kb * BKP, 0);
       if (nx >= 2) tc::tma_load_2d(base + xoff + xbytes, &tmXlo, &full[stage], kb * BKP, 0);
@@ -839,14 +840,16 @@ cudaError_t TcEngine::pass(bool transA, const float* A, int64_t m, int64_t n, in
 }
 
 cudaError_t TcEngine::pass_k(bool transA, int64_t k0, int64_t K, const float* X, int64_t ldx, int d, float* out,
-                             int64_t ldout, int* info, cudaStream_t st, bool exact) {
+                             int64_t ldout, int* info, cudaStream_t st, bool exact, int64_t m0, int64_t Mrows) {
   if (d > d_cap_ || split_of_ == nullptr) return cudaErrorInvalidValue;
   if (exact && (Alo2_ == nullptr || Xlo2_ == nullptr)) return cudaErrorInvalidValue;
   if (k0 < 0 || (!transA && k0 != 0) || k0 + K > (transA ? m_ : n_) || K <= 0) return cudaErrorInvalidValue;
+  if (m0 < 0 || (transA && (m0 != 0 || Mrows >= 0)) || (!transA && Mrows >= 0 && m0 + Mrows > m_))
+    return cudaErrorInvalidValue;
   cudaError_t e;
   const int64_t m = m_, n = n_;
   const int npad_ = npad_of(d);
-  const long long M = transA ? n : m;
+  const long long M = transA ? n : (Mrows >= 0 ? Mrows : m);
   if (K > k_cap_) return cudaErrorInvalidValue;
   if ((e = cudaMemsetAsync(flag_, 0, sizeof(int), st)) != cudaSuccess) return e;
   {
@@ -886,6 +889,7 @@ cudaError_t TcEngine::pass_k(bool transA, int64_t k0, int64_t K, const float* X,
   a.M = (int)M;
   a.K = (int)K;
   a.k0 = (int)k0;
+  a.m0 = (int)m0;
   a.d = d;
   a.npad = npad_;
   a.kblocks = (int)cdiv(K, bkp);

@@ -40,9 +40,11 @@ class TcEngine {
   cudaError_t split_rows(const float* Ablock, int64_t row0, int64_t rows, int64_t lda, double* sumsq,
                          cudaStream_t st);
   // out = op(A_cur) X over K rows k0 .. k0 + K - 1 of the current split
-  // (transA only for k0 > 0; X holds those K rows).
+  // (transA only for k0 > 0; X holds those K rows). Without transA, Mrows >= 0
+  // restricts the product to A's rows m0 .. m0 + Mrows - 1 (out row 0 = row m0).
   cudaError_t pass_k(bool transA, int64_t k0, int64_t K, const float* X, int64_t ldx, int d, float* out,
-                     int64_t ldout, int* info, cudaStream_t st, bool exact = false);
+                     int64_t ldout, int* info, cudaStream_t st, bool exact = false, int64_t m0 = 0,
+                     int64_t Mrows = -1);
   // G (cols x cols, ldg) = A^T A of the current split (cols <= 256).
   cudaError_t gram(float* G, int64_t ldg, int* info, cudaStream_t st);
 

@@ -52,7 +52,7 @@ EXPORTED = ["rqlp_default_opts", "rqlp_workspace_bytes", "rqlp_factor", "rqlp_ho
 class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("small_fp64", ctypes.c_int),
                 ("test_stall", ctypes.c_int), ("bf16_parts", ctypes.c_int),
-                ("literal_step5", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+                ("literal_step5", ctypes.c_int), ("fused_power", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
 
 
 class Problem(ctypes.Structure):
@@ -192,13 +192,14 @@ def load(build_if_missing: bool = True):
     return lib
 
 
-def _opts(precision=PREC_FP32, small_fp64=False, parts=0, literal=False):
+def _opts(precision=PREC_FP32, small_fp64=False, parts=0, literal=False, fused=False):
     o = Opts()
     load().rqlp_default_opts(ctypes.byref(o))
     o.precision = int(precision)
     o.small_fp64 = 1 if small_fp64 else 0
     o.bf16_parts = int(parts)
     o.literal_step5 = 1 if literal else 0
+    o.fused_power = 1 if fused else 0
     return o
 
 
@@ -391,13 +392,14 @@ def _stream():
 
 
 def factor(A, k, p, q, Omega, precision=PREC_FP32, small_fp64=False, workspace=None, out=None, parts=0,
-           literal=False):
+           literal=False, fused=False):
     """Factor a CUDA FP32 row-major A (m x n) with Omega (m x (k+p)).
 
     Returns (Q, L, P, info, diag) as CUDA tensors; info (int32[2]) and diag
     (float64[4]) are filled asynchronously on the current stream. parts:
     BF16 parts per pass operand in the BF16X3 form (0 = automatic, 2, 3).
     literal: step 5 as Algorithm 1 prints it (QR of A^T Q, a third pass).
+    fused: each power pass as A^T (A P~) over L2-sized row panels.
     """
     import torch
     m, n = A.shape
@@ -406,7 +408,7 @@ def factor(A, k, p, q, Omega, precision=PREC_FP32, small_fp64=False, workspace=N
         raise TypeError("A and Omega must be CUDA float32 tensors")
     if A.stride(1) != 1 or Omega.stride(1) != 1:
         raise ValueError("A and Omega must be row-major (unit column stride)")
-    opts = _opts(precision, small_fp64, parts, literal)
+    opts = _opts(precision, small_fp64, parts, literal, fused)
     ws_bytes = rqlp_workspace_bytes(m, n, k, p, q, opts)
     if ws_bytes == 0:
         raise RqlpError(1, "rqlp_workspace_bytes")

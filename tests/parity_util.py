@@ -14,14 +14,14 @@ TOL_ORTH = 1e-5
 TOL_RES = 1e-3
 
 
-def run_gpu(A, Om, k, p, q, precision=0, small_fp64=False, parts=0, literal=False):
+def run_gpu(A, Om, k, p, q, precision=0, small_fp64=False, parts=0, literal=False, fused=False):
     import torch
 
     from paper_2110_01011_gb300 import rqlp
     dA = torch.from_numpy(np.ascontiguousarray(A, dtype=np.float32)).cuda()
     dO = torch.from_numpy(np.ascontiguousarray(Om, dtype=np.float32)).cuda()
     Q, L, P, info, diag = rqlp.factor(dA, k, p, q, dO, precision=precision, small_fp64=small_fp64, parts=parts,
-                                      literal=literal)
+                                      literal=literal, fused=fused)
     torch.cuda.synchronize()
     return (Q.double().cpu().numpy(), L.double().cpu().numpy(), P.double().cpu().numpy(),
             info.cpu().numpy(), diag.cpu().numpy())

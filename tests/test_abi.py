@@ -42,7 +42,8 @@ def test_host_only_calls(lib):
     assert "breakdown" in rqlp.rqlp_status_string(3).lower()
     o = rqlp.rqlp_default_opts()
     assert o.precision == rqlp.PREC_FP32 and o.small_fp64 == 0
-    assert o.test_stall == 0 and o.bf16_parts == 0 and o.literal_step5 == 0 and list(o.reserved) == [0] * 3
+    assert o.test_stall == 0 and o.bf16_parts == 0 and o.literal_step5 == 0 and o.fused_power == 0
+    assert list(o.reserved) == [0] * 2
 
 
 @pytest.mark.parametrize("m,n,k,p,q", [(0, 10, 1, 0, 0), (10, 10, 0, 1, 0), (10, 10, 8, 3, 0),
@@ -76,6 +77,11 @@ def test_bad_opts_rejected(lib):
     for parts, ok in ((0, True), (1, False), (2, True), (3, True), (4, False)):
         o.bf16_parts = parts
         assert (rqlp.rqlp_workspace_bytes(100, 100, 5, 5, 0, o) > 0) == ok, parts
+    o = rqlp.rqlp_default_opts()
+    o.fused_power = 2
+    assert rqlp.rqlp_workspace_bytes(100, 100, 5, 5, 0, o) == 0
+    o.fused_power = 1
+    assert rqlp.rqlp_workspace_bytes(100, 100, 5, 5, 2, o) > 0
     o = rqlp.rqlp_default_opts()
     o.literal_step5 = 2
     assert rqlp.rqlp_workspace_bytes(100, 100, 5, 5, 0, o) == 0

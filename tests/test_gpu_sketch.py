@@ -15,9 +15,12 @@ pytestmark = pytest.mark.gpu
 
 # d = 160 and 161 sit on either side of the tensor-core pass's switch from
 # K = 64 to K = 32 per pipeline stage (three K = 64 stages fit up to d = 160).
+# In FP32, outputs of >= 1024 rows and >= 96 columns take the 128 x 128 tile:
+# 1025 x 1031 with d = 130 has odd row strides (scalar loads), ragged tiles in
+# both directions and split K; 3000 x 2000 with d = 100 the 128-bit loads.
 SHAPES = [(300, 200, 13), (129, 257, 16), (1000, 777, 25), (777, 1000, 37),
           (2500, 1300, 210), (4100, 300, 64), (640, 512, 256), (97, 53, 1),
-          (1500, 900, 160), (900, 1500, 161)]
+          (1500, 900, 160), (900, 1500, 161), (1025, 1031, 130), (3000, 2000, 100)]
 
 
 def _run(A, X, trans, prec):
