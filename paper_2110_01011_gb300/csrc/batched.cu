@@ -335,6 +335,7 @@ struct Builder {
     std::vector<GroupGemm> js;
     for (int i = 0; i < n(); ++i) {
       GroupGemm j = job(X(i), bf[i].ld, X(i), bf[i].ld, bf[i].G, bf[i].ld, d(i), d(i), rows(i));
+      j.lower_only = 1;   // the Cholesky reads G(i, j) for j <= i
       if (gate_slot >= 0) {
         j.gate = &bf[i].gates[gate_slot];
         j.gate_mode = kGateSkip;

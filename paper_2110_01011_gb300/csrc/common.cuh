@@ -64,10 +64,14 @@ void profile_mark_end(cudaStream_t st, int tag);
 // gate (optional) with gate_mode 1: *gate == 0 -> C = A (B taken as identity,
 // needs !transA, K == N, one slice); gate_mode 2: *gate == 0 -> no work.
 // b_upper: B is upper triangular (k-tiles beyond the column tile are skipped).
+// lower_only (M == N, a Gram matrix whose reader takes its lower triangle):
+// tiles whose entries all lie above the diagonal are skipped and C's strict
+// upper triangle is left undefined.
 enum GateMode { kGateNone = 0, kGateCopy = 1, kGateSkip = 2 };
 cudaError_t gemm_f32_ex(bool transA, int64_t M, int64_t N, int64_t K, const float* A, int64_t lda,
                         const float* B, int64_t ldb, float* C, int64_t ldc, int splits, float* part,
-                        double* sumsq, const int* gate, int gate_mode, bool b_upper, cudaStream_t st);
+                        double* sumsq, const int* gate, int gate_mode, bool b_upper, cudaStream_t st,
+                        bool lower_only = false);
 int gemm_f32_splits(int64_t M, int64_t N, int64_t K);
 size_t gemm_f32_part_floats(int64_t M, int64_t N, int64_t K);
 
@@ -83,6 +87,7 @@ struct GroupGemm {
   const int* gate;
   int gate_mode;
   int b_upper;
+  int lower_only;   // a Gram read by its lower triangle: tiles above the diagonal are skipped
 };
 // Tile shapes (kGroupCfgs) times grid modes: choice < kGroupCfgs is a
 // persistent grid, choice - kGroupCfgs the same tile with one CTA per tile.

@@ -25,7 +25,50 @@ struct GemmArgs {
   const int* gate;                          // optional gate word (see GateMode)
   int gate_mode;
   int b_upper;                              // B upper triangular: skip k >= n-tile end
+  int lower_only;                           // only tiles with entries on or below the diagonal
 };
+
+// Gated off (kGateCopy): C = A on this tile (B taken as the identity). All
+// loads of the thread are issued before its stores (C and A are distinct
+// buffers, which the compiler cannot assume), 128-bit where aligned.
+template <int BM, int BN, int NT>
+__device__ __forceinline__ void copy_tile(const GemmArgs& g, int64_t m0, int64_t n0, float* C) {
+  constexpr int Q = BN / 4;            // float4 per tile row
+  constexpr int PER = BM * Q / NT;     // float4 per thread
+  static_assert(PER * NT == BM * Q, "copy tiling");
+  const bool vec = ((reinterpret_cast<uintptr_t>(g.A) | reinterpret_cast<uintptr_t>(C)) % 16 == 0) &&
+                   g.lda % 4 == 0 && g.ldc % 4 == 0;
+  float4 v[PER];
+#pragma unroll
+  for (int r = 0; r < PER; ++r) {
+    const int f = threadIdx.x + r * NT;
+    const int64_t gm = m0 + f / Q, gn = n0 + (f % Q) * 4;
+    const float* src = g.A + gm * g.lda + gn;
+    if (gm < g.M && vec && gn + 3 < g.N) {
+      v[r] = *reinterpret_cast<const float4*>(src);
+    } else {
+      float t[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) t[i] = (gm < g.M && gn + i < g.N) ? src[i] : 0.f;
+      v[r] = make_float4(t[0], t[1], t[2], t[3]);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < PER; ++r) {
+    const int f = threadIdx.x + r * NT;
+    const int64_t gm = m0 + f / Q, gn = n0 + (f % Q) * 4;
+    if (gm >= g.M) continue;
+    float* dst = C + gm * g.ldc + gn;
+    if (vec && gn + 3 < g.N) {
+      *reinterpret_cast<float4*>(dst) = v[r];
+    } else {
+      const float t[4] = {v[r].x, v[r].y, v[r].z, v[r].w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (gn + i < g.N) dst[i] = t[i];
+    }
+  }
+}
 
 // One BM x BN tile of C (rows m0.., columns n0..) over K-slice `slice`, by the
 // whole CTA.
@@ -42,14 +85,12 @@ __device__ __forceinline__ void gemm_tile(const GemmArgs& g, int64_t m0, int64_t
   const int tid = threadIdx.x;
   const int tx = tid % TX, ty = tid / TX;
   float* C = g.C + (int64_t)slice * g.c_slice;
+  if (g.lower_only && n0 > m0 + BM - 1) return;   // every entry of the tile has j > i
 
   if (g.gate != nullptr && *g.gate == 0) {
     if (g.gate_mode == kGateSkip) return;
     // Gated off: B is taken as the identity (requires !TRANS_A, K == N, one slice).
-    for (int idx = tid; idx < BM * BN; idx += NT) {
-      int64_t gm = m0 + idx / BN, gn = n0 + idx % BN;
-      if (gm < g.M && gn < g.N) C[gm * g.ldc + gn] = g.A[gm * g.lda + gn];
-    }
+    copy_tile<BM, BN, NT>(g, m0, n0, C);
     return;
   }
 
@@ -217,6 +258,7 @@ gemm_grouped_kernel(const GroupGemm* __restrict__ jobs, const int* __restrict__ 
     g.gate = j.gate;
     g.gate_mode = j.gate_mode;
     g.b_upper = j.b_upper;
+    g.lower_only = j.lower_only;
     __syncthreads();   // the previous tile's shared-memory reads are done
     gemm_tile<BM, BN, BK, TM, TN, TRANS_A>(g, (int64_t)(local / tn) * BM, (int64_t)(local % tn) * BN, 0);
   }
@@ -245,10 +287,7 @@ __global__ void __launch_bounds__(kWideThreads, 1) gemm_f32_wide_kernel(GemmArgs
 
   if (g.gate != nullptr && *g.gate == 0) {
     if (g.gate_mode == kGateSkip) return;
-    for (int idx = tid; idx < BM * BN; idx += NT) {   // B taken as the identity (see gemm_tile)
-      const int64_t gm = m0 + idx / BN, gn = n0 + idx % BN;
-      if (gm < g.M && gn < g.N) C[gm * g.ldc + gn] = g.A[gm * g.lda + gn];
-    }
+    copy_tile<BM, BN, NT>(g, m0, n0, C);   // B taken as the identity (see gemm_tile)
     return;
   }
 
@@ -426,10 +465,12 @@ __global__ void splitk_reduce_kernel(int64_t M, int64_t N, int splits, const flo
   }
 }
 
-// Tile configuration: the wide 128 x 128 tile for the passes over A and the
-// tall products of width N >= 96, a 128 x 64 tile for narrower ones, a small
+// Tile configuration: the wide 128 x 128 tile (one CTA per SM) for the
+// passes over A of width N >= 96, a 128 x 64 tile (two CTAs per SM) for
+// narrower passes and for the tall products with a short K (X R^{-1}, P~ P^:
+// K = d, too few k-tiles to hide the wide tile's first loads), a small
 // 32 x 32 tile for d x d work.
-bool use_wide(int64_t M, int64_t N) { return M >= 1024 && N >= 96; }
+bool use_wide(int64_t M, int64_t N, int64_t K) { return M >= 1024 && N >= 96 && K >= 1024; }
 bool use_big(int64_t M, int64_t N) { return M >= 1024 && N >= 48; }
 
 }  // namespace
@@ -448,7 +489,7 @@ int sm_count() {
 }
 
 int gemm_f32_splits(int64_t M, int64_t N, int64_t K) {
-  const bool wide = use_wide(M, N), big = use_big(M, N);
+  const bool wide = use_wide(M, N, K), big = use_big(M, N);
   const int64_t BM = big ? 128 : 32, BN = wide ? 128 : big ? 64 : 32;
   const int64_t tiles = cdiv(M, BM) * cdiv(N, BN);
   if (wide) {
@@ -472,7 +513,10 @@ int gemm_f32_splits(int64_t M, int64_t N, int64_t K) {
   }
   const int64_t resident = (int64_t)sm_count() * (big ? 2 : 8);
   int64_t s = cdiv(resident * 2, tiles);            // about two waves of CTAs
-  int64_t maxs = K / 256;                           // keep >= 256 K per slice
+  // keep >= 256 K per slice on the large tile; the d x d products of the
+  // small tile (K = d) split down to 64 K per slice, as they would otherwise
+  // run 49 CTAs at d = 210
+  int64_t maxs = big ? K / 256 : K / 64;
   if (s > maxs) s = maxs;
   if (s > 64) s = 64;
   if (s < 1) s = 1;
@@ -486,7 +530,7 @@ size_t gemm_f32_part_floats(int64_t M, int64_t N, int64_t K) {
 
 static cudaError_t launch_gemm(bool transA, const GemmArgs& g, int splits, cudaStream_t st) {
   const bool big = use_big(g.M, g.N);
-  if (use_wide(g.M, g.N)) {
+  if (use_wide(g.M, g.N, g.K)) {
     const bool vec = reinterpret_cast<uintptr_t>(g.A) % 16 == 0 && reinterpret_cast<uintptr_t>(g.B) % 16 == 0 &&
                      g.lda % 4 == 0 && g.ldb % 4 == 0;
     dim3 grid((unsigned)cdiv(g.N, kWideBN), (unsigned)cdiv(g.M, kWideBM), (unsigned)splits);
@@ -514,13 +558,16 @@ static cudaError_t launch_gemm(bool transA, const GemmArgs& g, int splits, cudaS
 
 cudaError_t gemm_f32_ex(bool transA, int64_t M, int64_t N, int64_t K, const float* A, int64_t lda,
                         const float* B, int64_t ldb, float* C, int64_t ldc, int splits, float* part,
-                        double* sumsq, const int* gate, int gate_mode, bool b_upper, cudaStream_t st) {
+                        double* sumsq, const int* gate, int gate_mode, bool b_upper, cudaStream_t st,
+                        bool lower_only) {
   if (M <= 0 || N <= 0) return cudaSuccess;
+  if (lower_only && (M != N || use_wide(M, N, K))) return cudaErrorInvalidValue;
   if (gate != nullptr && gate_mode == kGateCopy && (transA || K != N)) return cudaErrorInvalidValue;
   if (gate != nullptr && gate_mode == kGateCopy) splits = 1;
   GemmArgs g;
   g.M = M; g.N = N; g.K = K; g.A = A; g.lda = lda; g.B = B; g.ldb = ldb;
   g.sumsq = sumsq; g.gate = gate; g.gate_mode = gate_mode; g.b_upper = b_upper ? 1 : 0;
+  g.lower_only = lower_only ? 1 : 0;
   if (splits <= 1 || part == nullptr) {
     g.C = C; g.ldc = ldc; g.c_slice = 0; g.kchunk = round_up(K > 0 ? K : 1, 16);
     return launch_gemm(transA, g, 1, st);

@@ -176,10 +176,10 @@ class Ops {
   }
   static size_t orth_part_floats(int64_t rows, int d) { return gemm_f32_part_floats(d, d, rows); }
 
-  // G = X^T X.
+  // G = X^T X, lower triangle (the Cholesky kernel reads G(i, j) for j <= i).
   cudaError_t gram(const float* X, int64_t ldx, int64_t rows, const int* gate) {
     return gemm_f32_ex(true, d_, d_, rows, X, ldx, X, ldx, G_, ld_, gemm_f32_splits(d_, d_, rows), part_,
-                       nullptr, gate, kGateSkip, false, st_);
+                       nullptr, gate, kGateSkip, false, st_, /*lower_only=*/true);
   }
   // out = X Rinv (Rinv upper triangular); gate == 0 -> out = X.
   cudaError_t trmm(const float* X, int64_t ldx, int64_t rows, const float* Rinv, float* out, int64_t ldout,
@@ -260,9 +260,11 @@ class Ops {
     CK(chol(2, nullptr, g, want_r));
     CK(trmm(X, ldx, rows, Ri_[2], out, ldout, g));
     if (Racc != nullptr) {
-      CK(gemm_f32_ex(false, d_, d_, d_, R_[1], ld_, R_[0], ld_, Ra_, ld_, 1, nullptr, nullptr, nullptr,
+      // d x d products, split along K (their partials fit the Gram's buffer)
+      const int sk = gemm_f32_splits(d_, d_, d_);
+      CK(gemm_f32_ex(false, d_, d_, d_, R_[1], ld_, R_[0], ld_, Ra_, ld_, sk, part_, nullptr, nullptr,
                      kGateNone, true, st_));
-      CK(gemm_f32_ex(false, d_, d_, d_, R_[2], ld_, Ra_, ld_, Racc, ld_, 1, nullptr, nullptr, nullptr,
+      CK(gemm_f32_ex(false, d_, d_, d_, R_[2], ld_, Ra_, ld_, Racc, ld_, sk, part_, nullptr, nullptr,
                      kGateNone, true, st_));
     }
     return cudaSuccess;

@@ -314,30 +314,59 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant_
         ncols = a.npad;
       }
       const bool vec = whole ? (a.vec_out != 0) : true;   // partial slots are 64-byte aligned
-      for (int c0 = 0; c0 < a.npad; c0 += 16) {
-        float v[16];
-        tc::tmem_ld16(taddr + (uint32_t)c0, v);
-        if (a.split_acc) {
-          float w[16];
-          tc::tmem_ld16(taddr + (uint32_t)(a.npad + c0), w);
+      // 32 columns per step: the row's earlier sums (this thread wrote them)
+      // are all loaded before the step's stores, so the loads of a step
+      // overlap instead of queueing behind stores to the same array.
+      for (int c0 = 0; c0 < a.npad; c0 += 32) {
+        float v[2][16];
+        float4 o[2][4];
+        float os[2][16];
 #pragma unroll
-          for (int i = 0; i < 16; ++i) v[i] += w[i];
-        }
-        if (vec && c0 + 16 <= ncols) {
-          float4* d4 = reinterpret_cast<float4*>(dst + c0);
-          if (!first_chunk) {   // this thread wrote the row's earlier chunks
+        for (int h = 0; h < 2; ++h) {
+          const int cc = c0 + 16 * h;
+          if (cc >= a.npad || first_chunk) continue;
+          if (vec && cc + 16 <= ncols) {
+            const float4* d4 = reinterpret_cast<const float4*>(dst + cc);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              const float4 o = d4[q];
-              v[4 * q] += o.x; v[4 * q + 1] += o.y; v[4 * q + 2] += o.z; v[4 * q + 3] += o.w;
-            }
+            for (int q = 0; q < 4; ++q) o[h][q] = d4[q];
+          } else {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) os[h][i] = cc + i < ncols ? dst[cc + i] : 0.f;
           }
+        }
 #pragma unroll
-          for (int q = 0; q < 4; ++q) d4[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-        } else {
+        for (int h = 0; h < 2; ++h) {
+          const int cc = c0 + 16 * h;
+          if (cc >= a.npad) continue;   // uniform across the warp
+          tc::tmem_ld16(taddr + (uint32_t)cc, v[h]);
+          if (a.split_acc) {
+            float w[16];
+            tc::tmem_ld16(taddr + (uint32_t)(a.npad + cc), w);
 #pragma unroll
-          for (int i = 0; i < 16; ++i)
-            if (c0 + i < ncols) dst[c0 + i] = first_chunk ? v[i] : dst[c0 + i] + v[i];
+            for (int i = 0; i < 16; ++i) v[h][i] += w[i];
+          }
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int cc = c0 + 16 * h;
+          if (cc >= a.npad) continue;
+          float* vv = v[h];
+          if (vec && cc + 16 <= ncols) {
+            float4* d4 = reinterpret_cast<float4*>(dst + cc);
+            if (!first_chunk) {
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {
+                vv[4 * q] += o[h][q].x; vv[4 * q + 1] += o[h][q].y;
+                vv[4 * q + 2] += o[h][q].z; vv[4 * q + 3] += o[h][q].w;
+              }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) d4[q] = make_float4(vv[4 * q], vv[4 * q + 1], vv[4 * q + 2], vv[4 * q + 3]);
+          } else {
+#pragma unroll
+            for (int i = 0; i < 16; ++i)
+              if (cc + i < ncols) dst[cc + i] = first_chunk ? vv[i] : os[h][i] + vv[i];
+          }
         }
       }
       tc::tc_fence_before();
@@ -364,7 +393,49 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant_
           last_lo[1] = chi;
         }
         asm volatile("bar.sync 1, 128;" ::: "memory");
-        if (*last_flag) {
+        if (*last_flag && *nslots <= kMaxSlots) {
+          // Sum the slots in CTA order, the four warps over consecutive
+          // float4 of the tile (coalesced), eight float4 per thread in flight.
+          __threadfence();
+          const int n = *nslots;
+          const int Q = a.npad / 4, total = BM * Q;
+          for (int f0 = threadIdx.x; f0 < total; f0 += 128 * 8) {
+            float4 acc[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int s2 = 0; s2 < n; ++s2) {
+              const float4* src = reinterpret_cast<const float4*>(a.part + (long long)slots[s2] * BM * a.npad);
+              float4 v[8];
+#pragma unroll
+              for (int j = 0; j < 8; ++j) {
+                const int f = f0 + 128 * j;
+                v[j] = f < total ? __ldcg(src + f) : make_float4(0.f, 0.f, 0.f, 0.f);
+              }
+#pragma unroll
+              for (int j = 0; j < 8; ++j) {
+                acc[j].x += v[j].x; acc[j].y += v[j].y; acc[j].z += v[j].z; acc[j].w += v[j].w;
+              }
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              const int f = f0 + 128 * j;
+              if (f >= total) continue;
+              const int r = f / Q, c = (f % Q) * 4;
+              const long long gr = (long long)t * BM + r;
+              if (gr >= a.M || c >= a.d) continue;
+              float* o = a.out + gr * a.ldo + c;
+              if (a.vec_out && c + 3 < a.d) {
+                *reinterpret_cast<float4*>(o) = acc[j];
+              } else {
+                const float w[4] = {acc[j].x, acc[j].y, acc[j].z, acc[j].w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                  if (c + i < a.d) o[i] = w[i];
+              }
+            }
+          }
+          if (threadIdx.x == 0) a.tile_cnt[t] = 0;
+        } else if (*last_flag) {
           __threadfence();
           if (gm < a.M) {
             float* o = a.out + gm * a.ldo;
@@ -373,17 +444,7 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant_
               float acc[16];
 #pragma unroll
               for (int i = 0; i < 16; ++i) acc[i] = 0.f;
-              if (n <= kMaxSlots) {
-                for (int s2 = 0; s2 < n; ++s2) {
-                  const float4* src =
-                      reinterpret_cast<const float4*>(a.part + ((long long)slots[s2] * BM + row) * a.npad + c0);
-#pragma unroll
-                  for (int q = 0; q < 4; ++q) {
-                    const float4 v = __ldcg(src + q);
-                    acc[4 * q] += v.x; acc[4 * q + 1] += v.y; acc[4 * q + 2] += v.z; acc[4 * q + 3] += v.w;
-                  }
-                }
-              } else {   // many contributors (tiny problems): recompute the slots
+              {   // many contributors (tiny problems): recompute the slots
                 for (int c = last_lo[0]; c <= last_lo[1]; ++c) {
                   const long long cb = unit_begin(c, a.units, a.G);
                   if (cb == unit_begin(c + 1, a.units, a.G)) continue;

@@ -19,8 +19,12 @@ ELEM_TOL = 2e-4   # max |difference| of Q, L, P entries, as in the parity tests
 
 
 def _problem(m, n, k, p, seed):
-    A = inputs.low_rank_matrix(m, n, inputs.exp_spectrum(min(m, n), 8.0), 1e-5, seed=seed)
-    Om = inputs.omega(m, k + p, seed=seed + 1)
+    """A and Omega on the device. Rank 64 with sigma_i = exp(-i / 8) and a
+    1e-5 noise floor: the largest FP32 case is ~37000^2, whose full-rank Haar
+    factors would take many minutes to draw on the host."""
+    import torch
+    A = inputs.low_rank_matrix_torch(m, n, inputs.exp_spectrum(64, 8.0), 1e-5, seed=seed, rank=64)
+    Om = torch.from_numpy(inputs.omega(m, k + p, seed=seed + 1)).cuda()
     return A, Om
 
 
@@ -61,9 +65,7 @@ def test_noalloc_matches_rqlp_factor_twice_in_a_row(precision):
     nmax = _largest_square_within_bound(12, 4, 2, precision)
     cases = [(600, 500, 16, 4, 1, 11), (nmax, nmax, 12, 4, 2, 23)]
     for (m, n, k, p, q, seed) in cases:
-        A, Om = _problem(m, n, k, p, seed)
-        dA = torch.from_numpy(A).cuda()
-        dO = torch.from_numpy(Om).cuda()
+        dA, dO = _problem(m, n, k, p, seed)
         Qn, Ln, Pn, info_n = _noalloc(dA, dO, k, p, q, precision)
         torch.cuda.synchronize()
         Qn, Ln, Pn = (x.double().cpu().numpy() for x in (Qn, Ln, Pn))
