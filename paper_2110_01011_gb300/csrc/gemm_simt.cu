@@ -465,20 +465,36 @@ __global__ void __launch_bounds__(kWideThreads, 1) gemm_f32_wide_kernel(GemmArgs
   }
 }
 
-// C[m, n] = sum_z part[z][m][n] (fixed order, Kahan-compensated FP32).
+// C[m, n] = sum_z part[z][m][n] (fixed order, Kahan-compensated FP32); the
+// slices' values are loaded four at a time ahead of the sums. lower_only:
+// entries above the diagonal are not summed (the caller reads the lower
+// triangle; their partial tiles were never written).
 __global__ void splitk_reduce_kernel(int64_t M, int64_t N, int splits, const float* __restrict__ part,
-                                     float* __restrict__ C, int64_t ldc) {
+                                     float* __restrict__ C, int64_t ldc, int lower_only) {
   const int64_t total = M * N;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = i / N, col = i % N;
+    if (lower_only && col > row) continue;
     float s = 0.f, c = 0.f;
-    for (int z = 0; z < splits; ++z) {
-      float y = part[(int64_t)z * total + i] - c;
-      float t = s + y;
+    int z = 0;
+    for (; z + 4 <= splits; z += 4) {
+      float v[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) v[j] = part[(int64_t)(z + j) * total + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float y = v[j] - c, t = s + y;
+        c = (t - s) - y;
+        s = t;
+      }
+    }
+    for (; z < splits; ++z) {
+      const float y = part[(int64_t)z * total + i] - c, t = s + y;
       c = (t - s) - y;
       s = t;
     }
-    C[(i / N) * ldc + (i % N)] = s;
+    C[row * ldc + col] = s;
   }
 }
 
@@ -596,7 +612,7 @@ cudaError_t gemm_f32_ex(bool transA, int64_t M, int64_t N, int64_t K, const floa
   if (e != cudaSuccess) return e;
   int64_t total = M * N;
   int blocks = (int)std::min<int64_t>(cdiv(total, 256), (int64_t)sm_count() * 8);
-  splitk_reduce_kernel<<<blocks, 256, 0, st>>>(M, N, used, part, C, ldc);
+  splitk_reduce_kernel<<<blocks, 256, 0, st>>>(M, N, used, part, C, ldc, lower_only ? 1 : 0);
   note_launch();
   return cudaGetLastError();
 }

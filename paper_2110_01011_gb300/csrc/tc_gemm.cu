@@ -678,33 +678,42 @@ __global__ void split_a_kernel(const float* __restrict__ A, long long m, long lo
 }
 
 // X (rows x d FP32) -> X_hi^T, X_lo^T (d x ldk BF16, K-major); flags a nonzero low part.
-// tl2 (optional) receives bf16(X - X_hi - X_lo).
+// tl2 (optional) receives bf16(X - X_hi - X_lo). A block of 32 x 8 threads
+// transposes a 64 (K) x 32 (d) tile through shared memory; each thread then
+// writes two consecutive K entries of a column as one 32-bit pair, so a warp
+// stores 128 contiguous bytes of a row of X^T (ldk is a multiple of 8).
+constexpr int kPrepRows = 64;
 __global__ void prep_x_kernel(const float* __restrict__ X, long long rows, int d, long long ldx,
                               bf16* __restrict__ th, bf16* __restrict__ tl, bf16* __restrict__ tl2, long long ldk,
                               int* nonzero_lo) {
-  __shared__ float tile[32][33];
-  const long long r0 = (long long)blockIdx.x * 32;
+  __shared__ float tile[kPrepRows][33];
+  const long long r0 = (long long)blockIdx.x * kPrepRows;
   const int c0 = blockIdx.y * 32;
-  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+  for (int i = threadIdx.y; i < kPrepRows; i += blockDim.y) {
     const long long r = r0 + i;
     const int c = c0 + threadIdx.x;
     tile[i][threadIdx.x] = (r < rows && c < d) ? X[r * ldx + c] : 0.f;
   }
   __syncthreads();
   bool any = false;
+  const long long r = r0 + 2 * threadIdx.x;   // this thread's pair of K entries
   for (int i = threadIdx.y; i < 32; i += blockDim.y) {
     const int c = c0 + i;
-    const long long r = r0 + threadIdx.x;
-    if (c < d && r < ldk) {
-      const float x = tile[threadIdx.x][i];
-      const bf16 h = __float2bfloat16_rn(x);
-      const float r1 = x - __bfloat162float(h);
-      const bf16 l = __float2bfloat16_rn(r1);
-      th[(long long)c * ldk + r] = h;
-      tl[(long long)c * ldk + r] = l;
-      if (tl2 != nullptr) tl2[(long long)c * ldk + r] = __float2bfloat16_rn(r1 - __bfloat162float(l));
-      any |= __bfloat162float(l) != 0.f;
+    if (c >= d || r >= ldk) continue;
+    bf16 h[2], l[2], l2[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const float x = tile[2 * threadIdx.x + e][i];
+      h[e] = __float2bfloat16_rn(x);
+      const float r1 = x - __bfloat162float(h[e]);
+      l[e] = __float2bfloat16_rn(r1);
+      l2[e] = __float2bfloat16_rn(r1 - __bfloat162float(l[e]));
+      any |= __bfloat162float(l[e]) != 0.f;
     }
+    const long long o = (long long)c * ldk + r;
+    *reinterpret_cast<__nv_bfloat162*>(th + o) = __halves2bfloat162(h[0], h[1]);
+    *reinterpret_cast<__nv_bfloat162*>(tl + o) = __halves2bfloat162(l[0], l[1]);
+    if (tl2 != nullptr) *reinterpret_cast<__nv_bfloat162*>(tl2 + o) = __halves2bfloat162(l2[0], l2[1]);
   }
   // One vote per block, and none once another block has raised the flag.
   if (__syncthreads_or(any) && threadIdx.x == 0 && threadIdx.y == 0 && *(volatile int*)nonzero_lo == 0)
@@ -914,7 +923,7 @@ cudaError_t TcEngine::pass_k(bool transA, int64_t k0, int64_t K, const float* X,
   if (K > k_cap_) return cudaErrorInvalidValue;
   if ((e = cudaMemsetAsync(flag_, 0, sizeof(int), st)) != cudaSuccess) return e;
   {
-    dim3 grid((unsigned)cdiv(round_up(K, 8), 32), (unsigned)cdiv(d, 32));
+    dim3 grid((unsigned)cdiv(round_up(K, 8), kPrepRows), (unsigned)cdiv(d, 32));
     prep_x_kernel<<<grid, dim3(32, 8), 0, st>>>(X, K, d, ldx, reinterpret_cast<bf16*>(Xhi_),
                                                  reinterpret_cast<bf16*>(Xlo_),
                                                  exact ? reinterpret_cast<bf16*>(Xlo2_) : nullptr, round_up(K, 8),
