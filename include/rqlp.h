@@ -90,8 +90,11 @@ typedef struct {
                    /* small enough to stay in L2, Z = A P~ not              */
                    /* orthonormalised (its span is all the next product     */
                    /* needs): one pass over A from HBM per power pass       */
-                   /* instead of two; 0: the two passes with qf(Z) between   */
-                   /* (default). Dense single-matrix entry points only       */
+                   /* instead of two. It pays off for narrow A only (a      */
+                   /* 48 MB panel must span the SMs' worth of 128-row       */
+                   /* tiles, n <~ 600); at n = 20000 it is ~10x slower.     */
+                   /* 0: the two passes with qf(Z) between (default).       */
+                   /* Dense single-matrix entry points only                 */
   int reserved[2]; /* must be zero                                            */
 } rqlp_opts;
 
