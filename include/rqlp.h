@@ -90,9 +90,11 @@ typedef struct {
                    /* small enough to stay in L2, Z = A P~ not              */
                    /* orthonormalised (its span is all the next product     */
                    /* needs): one pass over A from HBM per power pass       */
-                   /* instead of two. It pays off for narrow A only (a      */
-                   /* 48 MB panel must span the SMs' worth of 128-row       */
-                   /* tiles, n <~ 600); at n = 20000 it is ~10x slower.     */
+                   /* instead of two. Measured slower than the two passes   */
+                   /* at every shape tried (200000 x 500: 6.2 vs 5.8 ms;    */
+                   /* 20000 x 20000: 12.8 vs 5.3 ms): an L2-sized panel     */
+                   /* holds few 128-row tiles, and each panel writes a      */
+                   /* full n x d partial of Y.                              */
                    /* 0: the two passes with qf(Z) between (default).       */
                    /* Dense single-matrix entry points only                 */
   int reserved[2]; /* must be zero                                            */

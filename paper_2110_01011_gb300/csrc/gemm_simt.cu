@@ -36,7 +36,7 @@ __device__ __forceinline__ void copy_tile(const GemmArgs& g, int64_t m0, int64_t
   constexpr int Q = BN / 4;            // float4 per tile row
   constexpr int PER = BM * Q / NT;     // float4 per thread
   constexpr int CH = 4;                // float4 loaded before their stores (bounded registers)
-  static_assert(PER * NT == BM * Q && PER % CH == 0, "copy tiling");
+  static_assert(PER * NT == BM * Q, "copy tiling");
   const bool vec = ((reinterpret_cast<uintptr_t>(g.A) | reinterpret_cast<uintptr_t>(C)) % 16 == 0) &&
                    g.lda % 4 == 0 && g.ldc % 4 == 0;
 #pragma unroll 1
@@ -44,6 +44,7 @@ __device__ __forceinline__ void copy_tile(const GemmArgs& g, int64_t m0, int64_t
     float4 v[CH];
 #pragma unroll
     for (int r = 0; r < CH; ++r) {
+      if (r0 + r >= PER) break;
       const int f = threadIdx.x + (r0 + r) * NT;
       const int64_t gm = m0 + f / Q, gn = n0 + (f % Q) * 4;
       const float* src = g.A + gm * g.lda + gn;
@@ -58,6 +59,7 @@ __device__ __forceinline__ void copy_tile(const GemmArgs& g, int64_t m0, int64_t
     }
 #pragma unroll
     for (int r = 0; r < CH; ++r) {
+      if (r0 + r >= PER) break;
       const int f = threadIdx.x + (r0 + r) * NT;
       const int64_t gm = m0 + f / Q, gn = n0 + (f % Q) * 4;
       if (gm >= g.M) continue;
@@ -282,18 +284,23 @@ gemm_grouped_kernel(const GroupGemm* __restrict__ jobs, const int* __restrict__ 
 }
 
 // Wide tile for the passes over A and the tall products with N >= 96: one
-// 128 x 128 tile of C per CTA of 256 threads, 8 x 8 outputs per thread in two
-// 4-wide row groups (ty * 4 .., 64 + ty * 4 ..) and two 4-wide column groups
-// (tx * 4 .., 64 + tx * 4 ..), so that four conflict-free 128-bit shared loads
-// feed 64 FMAs (the 128 x 64 tile needs three per 32). VEC: A and B are
-// 16-byte aligned with row strides that are multiples of 4 floats, and tiles
-// are fetched with 128-bit global loads. Same K slicing, gates, sum of
-// squares and two-level accumulation as gemm_tile.
-constexpr int kWideBM = 128, kWideBN = 128, kWideBK = 16, kWideThreads = 256;
+// 128 x BN tile of C per CTA of 256 threads, 8 x (4 + TN2) outputs per thread
+// in two 4-wide row groups (ty * 4 .., 64 + ty * 4 ..) and two column groups
+// (tx * 4 .. + 3 and 64 + tx * TN2 .., TN2 = (BN - 64) / 16), so that four
+// conflict-free 128-bit shared loads feed 64 FMAs at BN = 128 (the 128 x 64
+// tile needs three per 32). BN = 112 (TN2 = 3, the second group read by three
+// conflict-free 32-bit loads) covers N = 210 in 224 columns instead of 256.
+// VEC: A and B are 16-byte aligned with row strides that are multiples of 4
+// floats, and tiles are fetched with 128-bit global loads. Same K slicing,
+// gates, sum of squares and two-level accumulation as gemm_tile.
+constexpr int kWideBM = 128, kWideBK = 16, kWideThreads = 256;
 
-template <bool TRANS_A, bool VEC>
+template <bool TRANS_A, bool VEC, int BN>
 __global__ void __launch_bounds__(kWideThreads, 1) gemm_f32_wide_kernel(GemmArgs g) {
-  constexpr int BM = kWideBM, BN = kWideBN, BK = kWideBK, NT = kWideThreads;
+  constexpr int BM = kWideBM, BK = kWideBK, NT = kWideThreads;
+  constexpr int TN2 = (BN - 64) / 16, TN = 4 + TN2;
+  constexpr int QB = BN / 4;                 // float4 per row of a B tile
+  static_assert(BN == 112 || BN == 128, "wide tile widths");
   __shared__ __align__(16) float As[2][BK][BM + 4];
   __shared__ __align__(16) float Bs[2][BK][BN];
   const int tid = threadIdx.x;
@@ -346,8 +353,8 @@ __global__ void __launch_bounds__(kWideThreads, 1) gemm_f32_wide_kernel(GemmArgs
         }
       }
       ra[r] = make_float4(v[0], v[1], v[2], v[3]);
-      {
-        const int kk = f / 32, nq = f % 32;
+      if (f < BK * QB) {
+        const int kk = f / QB, nq = f % QB;
         const int64_t gk = k0 + kk, gn = n0 + nq * 4;
         const float* src = g.B + gk * g.ldb + gn;
         float w[4];
@@ -384,16 +391,16 @@ __global__ void __launch_bounds__(kWideThreads, 1) gemm_f32_wide_kernel(GemmArgs
         As[buf][k][row] = ra[r].x; As[buf][k + 1][row] = ra[r].y;
         As[buf][k + 2][row] = ra[r].z; As[buf][k + 3][row] = ra[r].w;
       }
-      *reinterpret_cast<float4*>(&Bs[buf][f / 32][(f % 32) * 4]) = rb[r];
+      if (f < BK * QB) *reinterpret_cast<float4*>(&Bs[buf][f / QB][(f % QB) * 4]) = rb[r];
     }
   };
 
   constexpr int kPromoteTiles = 256 / BK;
-  float acc[8][8], tot[8][8];
+  float acc[8][TN], tot[8][TN];
 #pragma unroll
   for (int i = 0; i < 8; ++i)
 #pragma unroll
-    for (int j = 0; j < 8; ++j) acc[i][j] = tot[i][j] = 0.f;
+    for (int j = 0; j < TN; ++j) acc[i][j] = tot[i][j] = 0.f;
 
   if (ntiles > 0) {
     load(kbeg);
@@ -407,20 +414,26 @@ __global__ void __launch_bounds__(kWideThreads, 1) gemm_f32_wide_kernel(GemmArgs
         const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 4]);
         const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][kk][64 + ty * 4]);
         const float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * 4]);
-        const float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][kk][64 + tx * 4]);
+        float b[TN] = {b0.x, b0.y, b0.z, b0.w};
+        if (TN2 == 4) {
+          const float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][kk][64 + tx * 4]);
+          b[4] = b1.x; b[5] = b1.y; b[6] = b1.z; b[TN - 1] = b1.w;
+        } else {
+#pragma unroll
+          for (int j = 0; j < TN2; ++j) b[4 + j] = Bs[buf][kk][64 + tx * TN2 + j];
+        }
         const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-        const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
         for (int i = 0; i < 8; ++i)
 #pragma unroll
-          for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+          for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
       }
       if (t + 1 < ntiles) store(buf ^ 1);
       if ((t + 1) % kPromoteTiles == 0) {
 #pragma unroll
         for (int i = 0; i < 8; ++i)
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
+          for (int j = 0; j < TN; ++j) {
             tot[i][j] += acc[i][j];
             acc[i][j] = 0.f;
           }
@@ -436,17 +449,18 @@ __global__ void __launch_bounds__(kWideThreads, 1) gemm_f32_wide_kernel(GemmArgs
     if (gm >= g.M) continue;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      const int64_t gn = n0 + h * 64 + tx * 4;
+      const int w = h == 0 ? 4 : TN2;   // columns of this group
+      const int64_t gn = n0 + (h == 0 ? tx * 4 : 64 + tx * TN2);
       float v[4];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) v[j] = acc[i][h * 4 + j] + tot[i][h * 4 + j];
+      for (int j = 0; j < 4; ++j) v[j] = j < w ? acc[i][h * 4 + j] + tot[i][h * 4 + j] : 0.f;
       float* dst = C + gm * g.ldc + gn;
-      if (cvec && gn + 3 < g.N) {
+      if (w == 4 && cvec && gn + 3 < g.N) {
         *reinterpret_cast<float4*>(dst) = make_float4(v[0], v[1], v[2], v[3]);
       } else {
 #pragma unroll
         for (int j = 0; j < 4; ++j)
-          if (gn + j < g.N) dst[j] = v[j];
+          if (j < w && gn + j < g.N) dst[j] = v[j];
       }
     }
   }
@@ -504,6 +518,8 @@ __global__ void splitk_reduce_kernel(int64_t M, int64_t N, int splits, const flo
 // K = d, too few k-tiles to hide the wide tile's first loads), a small
 // 32 x 32 tile for d x d work.
 bool use_wide(int64_t M, int64_t N, int64_t K) { return M >= 1024 && N >= 96 && K >= 1024; }
+// Column tile of the wide kernel: 112 where it pads N less than 128 does.
+int wide_bn(int64_t N) { return cdiv(N, 112) * 112 < cdiv(N, 128) * 128 ? 112 : 128; }
 bool use_big(int64_t M, int64_t N) { return M >= 1024 && N >= 48; }
 
 }  // namespace
@@ -523,7 +539,7 @@ int sm_count() {
 
 int gemm_f32_splits(int64_t M, int64_t N, int64_t K) {
   const bool wide = use_wide(M, N, K), big = use_big(M, N);
-  const int64_t BM = big ? 128 : 32, BN = wide ? 128 : big ? 64 : 32;
+  const int64_t BM = big ? 128 : 32, BN = wide ? wide_bn(N) : big ? 64 : 32;
   const int64_t tiles = cdiv(M, BM) * cdiv(N, BN);
   if (wide) {
     // One CTA per SM: the fewest K slices (1..8, >= 512 of K per slice) whose
@@ -566,14 +582,17 @@ static cudaError_t launch_gemm(bool transA, const GemmArgs& g, int splits, cudaS
   if (use_wide(g.M, g.N, g.K)) {
     const bool vec = reinterpret_cast<uintptr_t>(g.A) % 16 == 0 && reinterpret_cast<uintptr_t>(g.B) % 16 == 0 &&
                      g.lda % 4 == 0 && g.ldb % 4 == 0;
-    dim3 grid((unsigned)cdiv(g.N, kWideBN), (unsigned)cdiv(g.M, kWideBM), (unsigned)splits);
-    if (transA) {
-      if (vec) gemm_f32_wide_kernel<true, true><<<grid, kWideThreads, 0, st>>>(g);
-      else     gemm_f32_wide_kernel<true, false><<<grid, kWideThreads, 0, st>>>(g);
+    const int bn = wide_bn(g.N);
+    dim3 grid((unsigned)cdiv(g.N, bn), (unsigned)cdiv(g.M, kWideBM), (unsigned)splits);
+#define RQLP_WIDE(T, V, W) gemm_f32_wide_kernel<T, V, W><<<grid, kWideThreads, 0, st>>>(g)
+    if (bn == 112) {
+      if (transA) { if (vec) RQLP_WIDE(true, true, 112); else RQLP_WIDE(true, false, 112); }
+      else        { if (vec) RQLP_WIDE(false, true, 112); else RQLP_WIDE(false, false, 112); }
     } else {
-      if (vec) gemm_f32_wide_kernel<false, true><<<grid, kWideThreads, 0, st>>>(g);
-      else     gemm_f32_wide_kernel<false, false><<<grid, kWideThreads, 0, st>>>(g);
+      if (transA) { if (vec) RQLP_WIDE(true, true, 128); else RQLP_WIDE(true, false, 128); }
+      else        { if (vec) RQLP_WIDE(false, true, 128); else RQLP_WIDE(false, false, 128); }
     }
+#undef RQLP_WIDE
     note_launch();
   } else if (big) {
     dim3 grid((unsigned)cdiv(g.N, 64), (unsigned)cdiv(g.M, 128), (unsigned)splits);

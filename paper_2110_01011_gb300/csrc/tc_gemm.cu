@@ -90,6 +90,7 @@ struct TcArgs {
   int bufcols;               // TMEM columns of one buffer (npad, or 2 npad when split_acc)
   int* info;                 // status word (may be null)
   uint32_t idesc, stage_bytes, tmem_cols;
+  int fixup;                 // 1: split tiles are summed by tc_fixup_kernel after the pass
 };
 
 __host__ __device__ inline long long unit_begin(int c, long long units, int G) {
@@ -371,7 +372,7 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant_
       }
       tc::tc_fence_before();
       tc::mbar_arrive(&acce[ab]);
-      if (!whole && last_chunk) {
+      if (!whole && last_chunk && !a.fixup) {
         // Publish the partial tile; the last CTA to arrive on the tile sums them.
         __threadfence();
         asm volatile("bar.sync 1, 128;" ::: "memory");
@@ -476,6 +477,44 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant_
   __syncthreads();
   tc::tc_fence_after();
   if (warp == 5) tc::tmem_dealloc(tmem_base, a.tmem_cols);
+}
+
+// Sums of the split tiles when a tile has more contributors than the last
+// arriver's slot list holds (few output tiles, e.g. A^T X with n <= ~1300):
+// every split tile's partials are summed here by all SMs, one float4 of the
+// output per thread, over the tile's contributors in CTA order (the order
+// and the values of the last-arriver reduction).
+__global__ void tc_fixup_kernel(const TcArgs a) {
+  const int Q = a.npad / 4, KB = a.kblocks;
+  const long long total = (long long)a.tiles * BM * Q;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int t = (int)(idx / ((long long)BM * Q));
+    const int rem = (int)(idx % ((long long)BM * Q));
+    const int r = rem / Q, c = (rem % Q) * 4;
+    const long long gr = (long long)t * BM + r;
+    if (gr >= a.M || c >= a.d) continue;
+    const long long ub = (long long)t * KB, ue = ub + KB;
+    const int clo = unit_owner(ub, a.units, a.G), chi = unit_owner(ue - 1, a.units, a.G);
+    if (clo == chi) continue;   // one contributor: the tile was written whole
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int cc = clo; cc <= chi; ++cc) {
+      const long long cb = unit_begin(cc, a.units, a.G);
+      if (cb == unit_begin(cc + 1, a.units, a.G)) continue;
+      const int slot = (cb / KB == t) ? 2 * cc : 2 * cc + 1;
+      const float4 v = __ldcg(reinterpret_cast<const float4*>(a.part + ((long long)slot * BM + r) * a.npad + c));
+      acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
+    }
+    float* o = a.out + gr * a.ldo + c;
+    if (a.vec_out && c + 3 < a.d) {
+      *reinterpret_cast<float4*>(o) = acc;
+    } else {
+      const float w[4] = {acc.x, acc.y, acc.z, acc.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (c + i < a.d) o[i] = w[i];
+    }
+  }
 }
 
 // Gram matrix of a split tall matrix on the tensor cores: G = X^T X for
@@ -973,6 +1012,9 @@ cudaError_t TcEngine::pass_k(bool transA, int64_t k0, int64_t K, const float* X,
     a.tpc = (int)cdiv(a.tiles, G_);
     a.G = (int)cdiv(a.tiles, a.tpc);
   }
+  // A tile spans at most G / tiles + 2 CTAs; past the last arriver's slot
+  // list the split tiles are summed by tc_fixup_kernel instead.
+  a.fixup = (a.tpc == 0 && (long long)a.G / a.tiles + 2 > kMaxSlots) ? 1 : 0;
   a.vec_out = ((reinterpret_cast<uintptr_t>(out) % 16) == 0 && ldout % 4 == 0) ? 1 : 0;
   a.exact = exact ? 1 : 0;
   a.chunk = kChunkK / bkp;
@@ -1001,6 +1043,13 @@ cudaError_t TcEngine::pass_k(bool transA, int64_t k0, int64_t K, const float* X,
   else
     e = transA ? launch_pass<true, 32>(ah, al, xh, xl, al2, xl2, a, st)
                : launch_pass<false, 32>(ah, al, xh, xl, al2, xl2, a, st);
+  if (e == cudaSuccess && a.fixup) {
+    const long long total = (long long)a.tiles * BM * (npad_ / 4);
+    const int blocks = (int)std::min<long long>(cdiv(total, 256), (long long)G_ * 8);
+    tc_fixup_kernel<<<blocks, 256, 0, st>>>(a);
+    note_launch();
+    e = cudaGetLastError();
+  }
   if (prof) profile_mark_end(st, transA ? 1 : 0);
   return e;
 }

@@ -29,6 +29,7 @@ def test_config1(prec):
     (257, 131, 10, 3, 0), (257, 131, 10, 3, 2), (131, 257, 10, 3, 1),   # ragged tails, m < n
     (1500, 700, 40, 9, 1), (700, 1500, 48, 16, 1),                     # several big tiles
     (64, 64, 64, 0, 0), (300, 200, 1, 0, 3), (2049, 1025, 60, 4, 2),
+    (12000, 600, 40, 10, 1),   # five output tiles of A^T X over 188 k-blocks: split tiles summed after the pass
 ])
 @pytest.mark.parametrize("prec", [0, 1], ids=["fp32", "bf16x3"])
 def test_shapes(m, n, k, p, q, prec):

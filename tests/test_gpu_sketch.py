@@ -15,12 +15,17 @@ pytestmark = pytest.mark.gpu
 
 # d = 160 and 161 sit on either side of the tensor-core pass's switch from
 # K = 64 to K = 32 per pipeline stage (three K = 64 stages fit up to d = 160).
-# In FP32, outputs of >= 1024 rows and >= 96 columns take the 128 x 128 tile:
-# 1025 x 1031 with d = 130 has odd row strides (scalar loads), ragged tiles in
-# both directions and split K; 3000 x 2000 with d = 100 the 128-bit loads.
+# In FP32, outputs of >= 1024 rows and >= 96 columns over K >= 1024 take the
+# wide tile, 128 x 112 where that pads d less than 128 x 128 does (d = 100,
+# 130, 160, 161, 210) and 128 x 128 otherwise (d = 128, 240): 1025 x 1031 with
+# d = 130 has odd row strides (scalar loads), ragged tiles in both directions
+# and split K; 3000 x 2000 with d = 100 the 128-bit loads. In BF16x3, A^T X of
+# 9000 x 500 (four output tiles, ~38 CTAs each) and of 4100 x 300 sum their
+# split tiles in a separate kernel after the pass.
 SHAPES = [(300, 200, 13), (129, 257, 16), (1000, 777, 25), (777, 1000, 37),
           (2500, 1300, 210), (4100, 300, 64), (640, 512, 256), (97, 53, 1),
-          (1500, 900, 160), (900, 1500, 161), (1025, 1031, 130), (3000, 2000, 100)]
+          (1500, 900, 160), (900, 1500, 161), (1025, 1031, 130), (3000, 2000, 100),
+          (2048, 1100, 128), (1200, 1300, 240), (9000, 500, 205)]
 
 
 def _run(A, X, trans, prec):
