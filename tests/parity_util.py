@@ -6,9 +6,15 @@ import numpy as np
 
 from oracle import rqlp_oracle as orc
 
-# Tolerances (FP32 path vs FP64 oracle); the derivation is in the design notes:
-# leading-k |L_ii| relative 1e-4, ||Q^T Q - I||_F <= 1e-5, relative residual
-# within 1e-3 (relative) of the oracle's.
+# Tolerances, FP32 or BF16x3 path vs the FP64 oracle: leading-k |L_ii|
+# relative 1e-4 (the target; both arithmetic forms meet it without widening),
+# ||Q^T Q - I||_F <= 1e-5 (CholeskyQR2 in FP32 leaves ~1e-6), relative residual
+# within 1e-3 (relative) of the oracle's or within RES_FLOOR of it when the
+# residual is at the pass arithmetic's rounding level. Entries of the leading
+# k columns of Q, P and of L's leading block differ by <= elem_atol (default
+# 2e-4): an entry error of qf(X) is about kappa(X(:, 1:k)) times the unit
+# roundoff of the passes (6e-8 in FP32, ~2^-16 with two BF16 parts), and
+# kappa <= ~1e2 on the leading blocks of these workloads.
 TOL_LII = 1e-4
 TOL_ORTH = 1e-5
 TOL_RES = 1e-3
