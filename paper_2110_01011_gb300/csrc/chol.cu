@@ -5,7 +5,8 @@
 // Blocked right-looking elimination on the augmented matrix [G | I] with
 // 16-column panels J:
 //   (1) warp 0 factors the 16 x 16 diagonal block L_JJ (row per lane,
-//       right-looking, column t's entries broadcast by shuffles);
+//       right-looking, column t's entries broadcast by shuffles; each pivot
+//       broadcast straight from its own lane's update);
 //   (2) forward substitutions o = L_JJ^{-1} v, a thread per vector: the
 //       panel L_IJ = G_IJ L_JJ^{-T} for the rows below, the block row of W
 //       (W_J,: = L_JJ^{-1} X_J,:, X = the eliminated identity) and its
@@ -17,7 +18,9 @@
 // Step (3) gives each warp 32 x 16 tiles and each lane 4 x 4 blocks, with the
 // panel operands in transposed shared-memory buffers. L lives in the lower
 // triangle of one square buffer and W^T in its strict upper triangle (W's
-// diagonal in a side array).
+// diagonal in a side array). The Gram's lower triangle reaches shared memory
+// by 16-byte asynchronous copies (FP32 factor, aligned rows), all of them in
+// flight at once.
 //
 // A pivot that is not clearly positive restarts the elimination on G + s I
 // (shifted CholeskyQR, Fukaya et al. 2020) and raises the caller's gate flag.
@@ -68,6 +71,9 @@ template <> struct Eps<double> { static constexpr double u = 1.1102230246251565e
 // 4 banks off a multiple of 32, so consecutive rows start in different banks.
 __host__ __device__ inline int lds_of(int d) { return (int)round_up(d, 32) + 4; }
 __host__ __device__ inline int ptld_of(int d) { return (int)round_up(d, 16); }
+
+template <typename T> struct IsF32 { static constexpr bool value = false; };
+template <> struct IsF32<float> { static constexpr bool value = true; };
 
 __device__ void post_error(int* info, int code, int detail) {
   if (info != nullptr && atomicCAS(info, 0, code) == 0) info[1] = detail;
@@ -184,10 +190,41 @@ __device__ __forceinline__ void chol_body(int d, const float* __restrict__ G, in
     // succeeds reduces kappa(X R^{-1}) the most
     if (attempt > 1) shift *= (T)10;
     const T sh = attempt == 0 ? (T)0 : shift;
-    // Lower triangle of G (+ sh I) into S, zeros above: a warp per group of
-    // four rows, lanes over columns, all of a group's loads issued before
-    // its stores.
-    for (int i0 = 4 * warp; i0 < d; i0 += 4 * nwarps) {
+    // Lower triangle of G (+ sh I) into S, zeros above.
+    bool loaded = false;
+    if constexpr (kShared && IsF32<T>::value) {
+      if ((reinterpret_cast<uintptr_t>(G) & 15) == 0 && (ldg & 3) == 0) {
+        // 16-byte chunks: those that reach the diagonal are copied
+        // asynchronously (all in flight at once), the others cleared; then
+        // the diagonal chunk's entries above the diagonal are cleared and
+        // the shift added. Chunk c of row i ends at 4 c + 3 < round_up(d, 4)
+        // <= ldg, and S's rows hold LDS > 4 c + 3 entries.
+        const int nch = (d + 3) >> 2;
+        for (int e = tid; e < d * nch; e += blockDim.x) {
+          const int i = e / nch, c4 = 4 * (e - i * nch);
+          T* dst = &S[(size_t)i * LDS + c4];
+          if (c4 <= i) {
+            cp_async16(dst, &G[(int64_t)i * ldg + c4]);
+          } else {
+            const T z[4] = {(T)0, (T)0, (T)0, (T)0};
+            st4(dst, z);
+          }
+        }
+        cp_async_wait_all();
+        __syncthreads();
+        for (int i = tid; i < d; i += blockDim.x) {
+          const int ce = min(d, (i & ~3) + 4);
+          for (int j = i + 1; j < ce; ++j) S[(size_t)i * LDS + j] = (T)0;
+          const T x = S[(size_t)i * LDS + i] + sh;
+          S[(size_t)i * LDS + i] = x;
+          gdiag[i] = x;
+        }
+        loaded = true;
+      }
+    }
+    // Otherwise a warp per group of four rows, lanes over columns, all of a
+    // group's loads issued before its stores.
+    for (int i0 = 4 * warp; !loaded && i0 < d; i0 += 4 * nwarps) {
       T v[4][kMaxD / 32];
 #pragma unroll
       for (int r = 0; r < 4; ++r)
@@ -241,15 +278,19 @@ __device__ __forceinline__ void chol_body(int d, const float* __restrict__ G, in
           ld4(&gdiag[j0 + k], &gd[k]);
         }
         int f = -1;
+        T piv = __shfl_sync(0xffffffffu, l[0], 0);
 #pragma unroll
         for (int t = 0; t < NB; ++t) {
-          const T piv = __shfl_sync(0xffffffffu, l[t], t);
           const bool live = t < jb;
           const bool ok = piv > rel_tol * gd[t] && isfinite(piv);
           f = (f < 0 && live && !ok) ? j0 + t : f;
           const T rl = rsqrt(ok ? piv : (T)1);
           if (lane == 0) rdiag[t] = rl;
           l[t] = lane == t ? piv * rl : (lane > t ? l[t] * rl : (T)0);
+          // The next pivot is lane t + 1's own update of its diagonal entry
+          // (the operation the column loop below performs there, so the same
+          // value), broadcast without waiting on the shuffle of column t.
+          if (t + 1 < NB) piv = __shfl_sync(0xffffffffu, l[t + 1] - l[t] * l[t], t + 1);
 #pragma unroll
           for (int c = t + 1; c < NB; ++c) l[c] -= l[t] * __shfl_sync(0xffffffffu, l[t], c);
         }

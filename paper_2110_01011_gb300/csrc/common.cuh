@@ -47,6 +47,24 @@ struct Arena {
 
 int sm_count();
 
+// Asynchronous global -> shared copies (cp.async): `bytes` of the copy are
+// read from src, the rest of the 4- or 16-byte destination is zero-filled
+// (bytes == 0 reads nothing). The 16-byte form needs both addresses 16-byte
+// aligned. Completion is tracked per thread in commit groups.
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem, int bytes) {
+  const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(s), "l"(gmem), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int bytes = 16) {
+  const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(s), "l"(gmem), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// Wait until at most N of this thread's committed groups are still in flight.
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Cumulative count of kernels this library has launched in the process
 // (reported by rqlp_kernel_launches). Every launch site calls note_launch().
 void note_launch(int n = 1);

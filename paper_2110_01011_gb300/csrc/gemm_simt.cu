@@ -5,8 +5,11 @@
 // C = op(A) B with op(A) = A^T (transA) or A, row-major operands. Each CTA
 // owns a BM x BN tile of C and one slice of the K range (split-K); slices
 // write partial tiles that a second kernel sums in a fixed order (Kahan), so
-// results are deterministic. Tiles are staged through double-buffered shared
-// memory; each thread accumulates a TM x TN block in registers.
+// results are deterministic. Tiles reach shared memory by asynchronous copies
+// (cp.async) through a ring of three or four stages, so a CTA pays the global
+// latency about once per K range rather than once per 16-wide K tile (the
+// d x d products of CholeskyQR have K = d and only a handful of tiles); each
+// thread accumulates a TM x TN block in registers.
 #include <algorithm>
 
 #include "common.cuh"
@@ -87,9 +90,13 @@ __device__ __forceinline__ void gemm_tile(const GemmArgs& g, int64_t m0, int64_t
   constexpr int TX = BN / TN;
   constexpr int AL = BM * BK / NT;
   constexpr int BL = BN * BK / NT;
+  constexpr int QA = BM / 4, QB = BN / 4;          // 16-byte chunks per tile row
+  constexpr int AV = BK * QA / NT, BV = BK * QB / NT;
   static_assert(AL * NT == BM * BK && BL * NT == BN * BK, "tile/thread mismatch");
-  __shared__ __align__(16) float As[2][BK][BM + 4];
-  __shared__ __align__(16) float Bs[2][BK][BN + 4];
+  static_assert(AV * NT == BK * QA && BV * NT == BK * QB, "chunk/thread mismatch");
+  constexpr int S = BM * BN <= 2048 ? 4 : 3;       // stages in the ring
+  __shared__ __align__(16) float As[S][BK][BM + 4];
+  __shared__ __align__(16) float Bs[S][BK][BN + 4];
 
   const int tid = threadIdx.x;
   const int tx = tid % TX, ty = tid / TX;
@@ -115,50 +122,82 @@ __device__ __forceinline__ void gemm_tile(const GemmArgs& g, int64_t m0, int64_t
   if (g.b_upper && kend > n0 + BN) kend = n0 + BN;
   const int64_t ntiles = kend > kbeg ? cdiv(kend - kbeg, BK) : 0;
 
-  float ra[AL], rb[BL];
   float sq = 0.f, sq_c = 0.f;   // Kahan sum of squares of the A tiles read
   const bool want_sq = g.sumsq != nullptr && n0 == 0;   // each element of A once
 
-  auto load = [&](int64_t k0) {
+  // A tile: As[kk][mm] = op(A)(m0 + mm, k0 + kk); B tile: Bs[kk][nn] =
+  // B(k0 + kk, n0 + nn); zeros outside [0, M) x [k0, kend) x [0, N). A smem
+  // row that is contiguous in global memory (B's rows; A^T's rows) goes as
+  // 16-byte chunks when the operand is 16-byte aligned with a row stride that
+  // is a multiple of 4; A (not transposed) is transposed element by element.
+  const bool vecA = TRANS_A && (reinterpret_cast<uintptr_t>(g.A) & 15) == 0 && (g.lda & 3) == 0;
+  const bool vecB = (reinterpret_cast<uintptr_t>(g.B) & 15) == 0 && (g.ldb & 3) == 0;
+  auto issue = [&](int64_t k0, int buf) {
+    if (vecA) {
 #pragma unroll
-    for (int r = 0; r < AL; ++r) {
-      int idx = tid + r * NT;
-      int kk = TRANS_A ? idx / BM : idx % BK;
-      int mm = TRANS_A ? idx % BM : idx / BK;
-      int64_t gk = k0 + kk, gm = m0 + mm;
-      float v = 0.f;
-      if (gk < kend && gm < g.M) v = TRANS_A ? g.A[gk * g.lda + gm] : g.A[gm * g.lda + gk];
-      ra[r] = v;
+      for (int r = 0; r < AV; ++r) {
+        const int idx = tid + r * NT, kk = idx / QA, mq = idx % QA;
+        const int64_t gk = k0 + kk, gm = m0 + 4 * mq;
+        const int64_t left = g.M - gm;
+        const int valid = gk < kend && left > 0 ? (left < 4 ? (int)left : 4) : 0;
+        cp_async16(&As[buf][kk][4 * mq], valid > 0 ? g.A + gk * g.lda + gm : g.A, 4 * valid);
+      }
+    } else {
+#pragma unroll
+      for (int r = 0; r < AL; ++r) {
+        const int idx = tid + r * NT;
+        const int kk = TRANS_A ? idx / BM : idx % BK;
+        const int mm = TRANS_A ? idx % BM : idx / BK;
+        const int64_t gk = k0 + kk, gm = m0 + mm;
+        const bool ok = gk < kend && gm < g.M;
+        const float* src = !ok ? g.A : (TRANS_A ? g.A + gk * g.lda + gm : g.A + gm * g.lda + gk);
+        cp_async4(&As[buf][kk][mm], src, ok ? 4 : 0);
+      }
     }
+    if (vecB) {
 #pragma unroll
-    for (int r = 0; r < BL; ++r) {
-      int idx = tid + r * NT;
-      int kk = idx / BN, nn = idx % BN;
-      int64_t gk = k0 + kk, gn = n0 + nn;
-      rb[r] = (gk < kend && gn < g.N) ? g.B[gk * g.ldb + gn] : 0.f;
-    }
-    if (want_sq) {
-      float s = 0.f;
+      for (int r = 0; r < BV; ++r) {
+        const int idx = tid + r * NT, kk = idx / QB, nq = idx % QB;
+        const int64_t gk = k0 + kk, gn = n0 + 4 * nq;
+        const int64_t left = g.N - gn;
+        const int valid = gk < kend && left > 0 ? (left < 4 ? (int)left : 4) : 0;
+        cp_async16(&Bs[buf][kk][4 * nq], valid > 0 ? g.B + gk * g.ldb + gn : g.B, 4 * valid);
+      }
+    } else {
 #pragma unroll
-      for (int r = 0; r < AL; ++r) s = fmaf(ra[r], ra[r], s);
-      float y = s - sq_c, t = sq + y;
-      sq_c = (t - sq) - y;
-      sq = t;
+      for (int r = 0; r < BL; ++r) {
+        const int idx = tid + r * NT, kk = idx / BN, nn = idx % BN;
+        const int64_t gk = k0 + kk, gn = n0 + nn;
+        const bool ok = gk < kend && gn < g.N;
+        cp_async4(&Bs[buf][kk][nn], ok ? g.B + gk * g.ldb + gn : g.B, ok ? 4 : 0);
+      }
     }
   };
-  auto store = [&](int buf) {
+  // Squares of the A entries this thread copied into stage buf (zeros past
+  // the edges), Kahan-summed.
+  auto add_squares = [&](int buf) {
+    float sacc = 0.f;
+    if (vecA) {
 #pragma unroll
-    for (int r = 0; r < AL; ++r) {
-      int idx = tid + r * NT;
-      int kk = TRANS_A ? idx / BM : idx % BK;
-      int mm = TRANS_A ? idx % BM : idx / BK;
-      As[buf][kk][mm] = ra[r];
-    }
+      for (int r = 0; r < AV; ++r) {
+        const int idx = tid + r * NT, kk = idx / QA, mq = idx % QA;
+        const float4 v = *reinterpret_cast<const float4*>(&As[buf][kk][4 * mq]);
+        sacc = fmaf(v.x, v.x, sacc); sacc = fmaf(v.y, v.y, sacc);
+        sacc = fmaf(v.z, v.z, sacc); sacc = fmaf(v.w, v.w, sacc);
+      }
+    } else {
 #pragma unroll
-    for (int r = 0; r < BL; ++r) {
-      int idx = tid + r * NT;
-      Bs[buf][idx / BN][idx % BN] = rb[r];
+      for (int r = 0; r < AL; ++r) {
+        const int idx = tid + r * NT;
+        const int kk = TRANS_A ? idx / BM : idx % BK;
+        const int mm = TRANS_A ? idx % BM : idx / BK;
+        const float v = As[buf][kk][mm];
+        sacc = fmaf(v, v, sacc);
+      }
     }
+    const float y = sacc - sq_c, t = sq + y;
+    sq_c = (t - sq) - y;
+    sq = t;
   };
 
   // Two-level accumulation: acc runs over kPromoteTiles K-tiles (256 of K)
@@ -173,12 +212,21 @@ __device__ __forceinline__ void gemm_tile(const GemmArgs& g, int64_t m0, int64_t
     for (int j = 0; j < TN; ++j) acc[i][j] = tot[i][j] = 0.f;
 
   if (ntiles > 0) {
-    load(kbeg);
-    store(0);
-    __syncthreads();
+    // Ring: tile t lives in stage t % S; S - 1 tiles are in flight ahead of
+    // the one being multiplied. The barrier at the top of iteration t also
+    // ends every thread's reads of stage (t - 1) % S, which iteration t refills.
+#pragma unroll
+    for (int st = 0; st < S - 1; ++st) {
+      if (st < ntiles) issue(kbeg + st * BK, st);
+      cp_async_commit();
+    }
     for (int64_t t = 0; t < ntiles; ++t) {
-      const int buf = (int)(t & 1);
-      if (t + 1 < ntiles) load(kbeg + (t + 1) * BK);
+      const int buf = (int)(t % S);
+      cp_async_wait<S - 2>();   // this thread's copies of tile t have landed
+      __syncthreads();
+      if (t + S - 1 < ntiles) issue(kbeg + (t + S - 1) * BK, (int)((t + S - 1) % S));
+      cp_async_commit();
+      if (want_sq) add_squares(buf);
 #pragma unroll
       for (int kk = 0; kk < BK; ++kk) {
         float a[TM], b[TN];
@@ -197,7 +245,6 @@ __device__ __forceinline__ void gemm_tile(const GemmArgs& g, int64_t m0, int64_t
 #pragma unroll
           for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
       }
-      if (t + 1 < ntiles) store(buf ^ 1);
       if ((t + 1) % kPromoteTiles == 0) {
 #pragma unroll
         for (int i = 0; i < TM; ++i)
@@ -207,8 +254,8 @@ __device__ __forceinline__ void gemm_tile(const GemmArgs& g, int64_t m0, int64_t
             acc[i][j] = 0.f;
           }
       }
-      __syncthreads();
     }
+    cp_async_wait_all();   // only empty groups can remain; the stages are free
   }
 #pragma unroll
   for (int i = 0; i < TM; ++i)
@@ -241,8 +288,10 @@ __device__ __forceinline__ void gemm_tile(const GemmArgs& g, int64_t m0, int64_t
   }
 }
 
+// Registers: 512 threads' worth per CTA count, as in the grouped form (at
+// most 128 per thread).
 template <int BM, int BN, int BK, int TM, int TN, bool TRANS_A>
-__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+__global__ void __launch_bounds__((BM / TM) * (BN / TN), 512 / ((BM / TM) * (BN / TN)))
 gemm_f32_kernel(GemmArgs g) {
   gemm_tile<BM, BN, BK, TM, TN, TRANS_A>(g, (int64_t)blockIdx.y * BM, (int64_t)blockIdx.x * BN, blockIdx.z);
 }
