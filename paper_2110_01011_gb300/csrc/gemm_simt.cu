@@ -341,11 +341,15 @@ gemm_grouped_kernel(const GroupGemm* __restrict__ jobs, const int* __restrict__ 
 // conflict-free 32-bit loads) covers N = 210 in 224 columns instead of 256.
 // VEC: A and B are 16-byte aligned with row strides that are multiples of 4
 // floats, and tiles are fetched with 128-bit global loads. Same K slicing,
-// gates, sum of squares and two-level accumulation as gemm_tile.
-constexpr int kWideBM = 128, kWideBK = 16, kWideThreads = 256;
+// gates, sum of squares and two-level accumulation as gemm_tile; the second
+// level (8 x TN per thread) lives in dynamic shared memory, so that a thread
+// fits in 128 registers and two CTAs share an SM.
+constexpr int kWideBM = 128, kWideBK = 16, kWideThreads = 256, kWidePerSm = 2;
+template <int BN>
+constexpr size_t wide_tot_bytes() { return (size_t)8 * (4 + (BN - 64) / 16) * kWideThreads * sizeof(float); }
 
 template <bool TRANS_A, bool VEC, int BN>
-__global__ void __launch_bounds__(kWideThreads, 1) gemm_f32_wide_kernel(GemmArgs g) {
+__global__ void __launch_bounds__(kWideThreads, kWidePerSm) gemm_f32_wide_kernel(GemmArgs g) {
   constexpr int BM = kWideBM, BK = kWideBK, NT = kWideThreads;
   constexpr int TN2 = (BN - 64) / 16, TN = 4 + TN2;
   constexpr int QB = BN / 4;                 // float4 per row of a B tile
@@ -445,11 +449,15 @@ __global__ void __launch_bounds__(kWideThreads, 1) gemm_f32_wide_kernel(GemmArgs
   };
 
   constexpr int kPromoteTiles = 256 / BK;
-  float acc[8][TN], tot[8][TN];
+  extern __shared__ __align__(16) float tot_s[];   // [8][TN][NT]: entry (i, j) of thread tid
+  float acc[8][TN];
 #pragma unroll
   for (int i = 0; i < 8; ++i)
 #pragma unroll
-    for (int j = 0; j < TN; ++j) acc[i][j] = tot[i][j] = 0.f;
+    for (int j = 0; j < TN; ++j) {
+      acc[i][j] = 0.f;
+      tot_s[(i * TN + j) * NT + tid] = 0.f;
+    }
 
   if (ntiles > 0) {
     load(kbeg);
@@ -483,7 +491,7 @@ __global__ void __launch_bounds__(kWideThreads, 1) gemm_f32_wide_kernel(GemmArgs
         for (int i = 0; i < 8; ++i)
 #pragma unroll
           for (int j = 0; j < TN; ++j) {
-            tot[i][j] += acc[i][j];
+            tot_s[(i * TN + j) * NT + tid] += acc[i][j];
             acc[i][j] = 0.f;
           }
       }
@@ -502,7 +510,7 @@ __global__ void __launch_bounds__(kWideThreads, 1) gemm_f32_wide_kernel(GemmArgs
       const int64_t gn = n0 + (h == 0 ? tx * 4 : 64 + tx * TN2);
       float v[4];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) v[j] = j < w ? acc[i][h * 4 + j] + tot[i][h * 4 + j] : 0.f;
+      for (int j = 0; j < 4; ++j) v[j] = j < w ? acc[i][h * 4 + j] + tot_s[(i * TN + h * 4 + j) * NT + tid] : 0.f;
       float* dst = C + gm * g.ldc + gn;
       if (w == 4 && cvec && gn + 3 < g.N) {
         *reinterpret_cast<float4*>(dst) = make_float4(v[0], v[1], v[2], v[3]);
@@ -591,11 +599,9 @@ int gemm_f32_splits(int64_t M, int64_t N, int64_t K) {
   const int64_t BM = big ? 128 : 32, BN = wide ? wide_bn(N) : big ? 64 : 32;
   const int64_t tiles = cdiv(M, BM) * cdiv(N, BN);
   if (wide) {
-    // One CTA per SM: the fewest K slices (1..8, >= 512 of K per slice) whose
-    // CTAs fill at least 90 % of their waves, else the fullest (314 tiles of
-    // a 20000 x 210 pass fill 69 % of three waves unsplit, 92 % of nine in
-    // four slices).
-    const int64_t nsm = sm_count();
+    // kWidePerSm CTAs per SM: the fewest K slices (1..8, >= 512 of K per
+    // slice) whose CTAs fill at least 90 % of their waves, else the fullest.
+    const int64_t nsm = (int64_t)sm_count() * kWidePerSm;
     int best = 1;
     double best_eff = 0.0;
     for (int s = 1; s <= 8 && (s == 1 || K / s >= 512); ++s) {
@@ -633,7 +639,18 @@ static cudaError_t launch_gemm(bool transA, const GemmArgs& g, int splits, cudaS
                      g.lda % 4 == 0 && g.ldb % 4 == 0;
     const int bn = wide_bn(g.N);
     dim3 grid((unsigned)cdiv(g.N, bn), (unsigned)cdiv(g.M, kWideBM), (unsigned)splits);
-#define RQLP_WIDE(T, V, W) gemm_f32_wide_kernel<T, V, W><<<grid, kWideThreads, 0, st>>>(g)
+#define RQLP_WIDE(T, V, W)                                                                              \
+  do {                                                                                                  \
+    static bool set_ = false;                                                                           \
+    if (!set_) {                                                                                        \
+      const cudaError_t e_ = cudaFuncSetAttribute(gemm_f32_wide_kernel<T, V, W>,                       \
+                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,          \
+                                                  (int)wide_tot_bytes<W>());                            \
+      if (e_ != cudaSuccess) return e_;                                                                 \
+      set_ = true;                                                                                      \
+    }                                                                                                   \
+    gemm_f32_wide_kernel<T, V, W><<<grid, kWideThreads, wide_tot_bytes<W>(), st>>>(g);                 \
+  } while (0)
     if (bn == 112) {
       if (transA) { if (vec) RQLP_WIDE(true, true, 112); else RQLP_WIDE(true, false, 112); }
       else        { if (vec) RQLP_WIDE(false, true, 112); else RQLP_WIDE(false, false, 112); }
