@@ -578,6 +578,11 @@ bool use_wide(int64_t M, int64_t N, int64_t K) { return M >= 1024 && N >= 96 && 
 // Column tile of the wide kernel: 112 where it pads N less than 128 does.
 int wide_bn(int64_t N) { return cdiv(N, 112) * 112 < cdiv(N, 128) * 128 ? 112 : 128; }
 bool use_big(int64_t M, int64_t N) { return M >= 1024 && N >= 48; }
+// Column tile of the large tile: 32 where it pads N less than 64 does and K
+// is short (the d-wide products X R^{-1}, P~ P^ with K = d: more, smaller
+// CTAs also fill the last wave better); 64 otherwise (a long-K pass reads
+// its A once per column tile).
+int big_bn(int64_t N, int64_t K) { return K <= 256 && cdiv(N, 32) * 32 < cdiv(N, 64) * 64 ? 32 : 64; }
 
 }  // namespace
 
@@ -596,7 +601,7 @@ int sm_count() {
 
 int gemm_f32_splits(int64_t M, int64_t N, int64_t K) {
   const bool wide = use_wide(M, N, K), big = use_big(M, N);
-  const int64_t BM = big ? 128 : 32, BN = wide ? wide_bn(N) : big ? 64 : 32;
+  const int64_t BM = big ? 128 : 32, BN = wide ? wide_bn(N) : big ? big_bn(N, K) : 32;
   const int64_t tiles = cdiv(M, BM) * cdiv(N, BN);
   if (wide) {
     // kWidePerSm CTAs per SM: the fewest K slices (1..8, >= 512 of K per
@@ -615,7 +620,7 @@ int gemm_f32_splits(int64_t M, int64_t N, int64_t K) {
     }
     return best;
   }
-  const int64_t resident = (int64_t)sm_count() * (big ? 2 : 8);
+  const int64_t resident = (int64_t)sm_count() * (512 / ((BM / (big ? 8 : 4)) * (BN / 4)));   // CTAs per SM
   int64_t s = cdiv(resident * 2, tiles);            // about two waves of CTAs
   // keep >= 256 K per slice on the large tile; the d x d products of the
   // small tile (K = d) split down to 64 K per slice, as they would otherwise
@@ -659,6 +664,11 @@ static cudaError_t launch_gemm(bool transA, const GemmArgs& g, int splits, cudaS
       else        { if (vec) RQLP_WIDE(false, true, 128); else RQLP_WIDE(false, false, 128); }
     }
 #undef RQLP_WIDE
+    note_launch();
+  } else if (big && big_bn(g.N, g.K) == 32) {
+    dim3 grid((unsigned)cdiv(g.N, 32), (unsigned)cdiv(g.M, 128), (unsigned)splits);
+    if (transA) gemm_f32_kernel<128, 32, 16, 8, 4, true><<<grid, 128, 0, st>>>(g);
+    else        gemm_f32_kernel<128, 32, 16, 8, 4, false><<<grid, 128, 0, st>>>(g);
     note_launch();
   } else if (big) {
     dim3 grid((unsigned)cdiv(g.N, 64), (unsigned)cdiv(g.M, 128), (unsigned)splits);

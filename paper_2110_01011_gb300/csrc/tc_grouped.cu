@@ -327,19 +327,23 @@ split_grouped_kernel(const SplitJob* __restrict__ jobs, const int* __restrict__ 
 
 // Every problem's X (K x d FP32) -> X_hi^T, X_lo^T (d x ldk BF16, K-major);
 // the problem's flag is raised when the low part is nonzero. One block per
-// 32 x 32 tile: tiles of problem b are numbered from start[b], row tiles
-// fastest.
+// 64 (K) x 32 (d) tile, transposed through shared memory: tiles of problem b
+// are numbered from start[b], row tiles fastest. Each thread writes two
+// consecutive K entries of a column as one 32-bit pair (ldk is a multiple of
+// 8, so a warp stores 128 contiguous bytes of a row of X^T); rows past K are
+// read as zeros by the TMA.
+constexpr int kPrepRows = 64;
 __global__ void __launch_bounds__(256)
 prep_grouped_kernel(const PrepJob* __restrict__ jobs, const int* __restrict__ start, int count) {
-  __shared__ float tile[32][33];
+  __shared__ float tile[kPrepRows][33];
   const int b = problem_of(start, count, blockIdx.x);
   const PrepJob j = jobs[b];
   const int local = blockIdx.x - start[b];
-  const int rtiles = (int)((j.K + 31) / 32);   // rows past K are read as zeros by the TMA
-  const long long r0 = (long long)(local % rtiles) * 32;
+  const int rtiles = (int)((j.K + kPrepRows - 1) / kPrepRows);
+  const long long r0 = (long long)(local % rtiles) * kPrepRows;
   const int c0 = (local / rtiles) * 32;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  for (int i = ty; i < 32; i += 8) {
+  for (int i = ty; i < kPrepRows; i += 8) {
     const long long r = r0 + i;
     const int c = c0 + tx;
     tile[i][tx] = (r < j.K && c < j.d) ? j.X[r * j.ldx + c] : 0.f;
@@ -349,19 +353,24 @@ prep_grouped_kernel(const PrepJob* __restrict__ jobs, const int* __restrict__ st
   bf16* th = reinterpret_cast<bf16*>(j.th);
   bf16* tl = reinterpret_cast<bf16*>(j.tl);
   bf16* tl2 = reinterpret_cast<bf16*>(j.tl2);
+  const long long r = r0 + 2 * tx;   // this thread's pair of K entries (r + 1 < ldk when r < K)
   for (int i = ty; i < 32; i += 8) {
     const int c = c0 + i;
-    const long long r = r0 + tx;
-    if (c < j.d && r < j.K) {
-      const float x = tile[tx][i];
-      const bf16 h = __float2bfloat16_rn(x);
-      const float r1 = x - __bfloat162float(h);
-      const bf16 l = __float2bfloat16_rn(r1);
-      th[(long long)c * j.ldk + r] = h;
-      tl[(long long)c * j.ldk + r] = l;
-      if (tl2 != nullptr) tl2[(long long)c * j.ldk + r] = __float2bfloat16_rn(r1 - __bfloat162float(l));
-      any |= __bfloat162float(l) != 0.f;
+    if (c >= j.d || r >= j.K) continue;
+    bf16 h[2], l[2], l2[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const float x = tile[2 * tx + e][i];
+      h[e] = __float2bfloat16_rn(x);
+      const float r1 = x - __bfloat162float(h[e]);
+      l[e] = __float2bfloat16_rn(r1);
+      l2[e] = __float2bfloat16_rn(r1 - __bfloat162float(l[e]));
+      any |= __bfloat162float(l[e]) != 0.f;
     }
+    const long long o = (long long)c * j.ldk + r;
+    *reinterpret_cast<__nv_bfloat162*>(th + o) = __halves2bfloat162(h[0], h[1]);
+    *reinterpret_cast<__nv_bfloat162*>(tl + o) = __halves2bfloat162(l[0], l[1]);
+    if (tl2 != nullptr) *reinterpret_cast<__nv_bfloat162*>(tl2 + o) = __halves2bfloat162(l2[0], l2[1]);
   }
   if (__syncthreads_or(any) && threadIdx.x == 0 && *(volatile int*)j.flag == 0) atomicOr(j.flag, 1);
 }
@@ -460,7 +469,7 @@ int tc_npad(int d) { return (int)round_up(std::max(d, 16), 16); }
 uint32_t tc_idesc(int npad, bool a_mn_major) { return tc::idesc_bf16(BM, npad, a_mn_major, false); }
 
 int tc_split_blocks(long long m, long long n) { return (int)cdiv(m * cdiv(n, 64) * 8, kSplitGroups); }
-int tc_prep_blocks(long long K, int d) { return (int)(cdiv(K, 32) * cdiv(d, 32)); }
+int tc_prep_blocks(long long K, int d) { return (int)(cdiv(K, kPrepRows) * cdiv(d, 32)); }
 
 cudaError_t split_grouped(const SplitJob* jobs, const int* start, int count, int total_blocks, cudaStream_t st) {
   if (count <= 0 || total_blocks <= 0) return cudaSuccess;
