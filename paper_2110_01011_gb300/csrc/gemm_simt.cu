@@ -539,9 +539,11 @@ __global__ void __launch_bounds__(kWideThreads, kWidePerSm) gemm_f32_wide_kernel
 // C[m, n] = sum_z part[z][m][n] (fixed order, Kahan-compensated FP32); the
 // slices' values are loaded four at a time ahead of the sums. lower_only:
 // entries above the diagonal are not summed (the caller reads the lower
-// triangle; their partial tiles were never written).
+// triangle; their partial tiles were never written). A product gated off
+// with kGateSkip wrote no partial tiles, and nothing is summed.
 __global__ void splitk_reduce_kernel(int64_t M, int64_t N, int splits, const float* __restrict__ part,
-                                     float* __restrict__ C, int64_t ldc, int lower_only) {
+                                     float* __restrict__ C, int64_t ldc, int lower_only, const int* skip_gate) {
+  if (skip_gate != nullptr && *skip_gate == 0) return;
   const int64_t total = M * N;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -707,7 +709,8 @@ cudaError_t gemm_f32_ex(bool transA, int64_t M, int64_t N, int64_t K, const floa
   if (e != cudaSuccess) return e;
   int64_t total = M * N;
   int blocks = (int)std::min<int64_t>(cdiv(total, 256), (int64_t)sm_count() * 8);
-  splitk_reduce_kernel<<<blocks, 256, 0, st>>>(M, N, used, part, C, ldc, lower_only ? 1 : 0);
+  splitk_reduce_kernel<<<blocks, 256, 0, st>>>(M, N, used, part, C, ldc, lower_only ? 1 : 0,
+                                                 gate_mode == kGateSkip ? gate : nullptr);
   note_launch();
   return cudaGetLastError();
 }
