@@ -38,7 +38,6 @@ class Ops {
     sp_ = a;
     spt_ = at;
   }
-  bool three_part() const { return three_; }
 
   // part_floats: largest split-K partial buffer any product of the caller needs.
   void layout(Arena& ar, size_t part_floats, bool with_tc, int64_t m, int64_t n) {

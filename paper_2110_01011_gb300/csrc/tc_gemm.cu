@@ -53,7 +53,6 @@ constexpr int BK = 32;               // K per pipeline stage of the Gram kernel 
 constexpr int kThreads = 192;        // 6 warps
 constexpr int kMaxStages = 8;
 constexpr long long kWaitLimit = 4000000000LL;   // cycles (~2 s) before a wait gives up
-constexpr uint32_t kABytes = BM * BK * 2;        // one BF16 A tile of the Gram kernel (8 KB)
 // K per pipeline stage of a pass: 64 (128-byte rows, 128B swizzle) where at
 // least three such stages fit in shared memory, else 32 (64-byte rows, 64B
 // swizzle). Larger TMA boxes stream A faster (measured: 7.1 vs 5.2 TB/s of
@@ -440,7 +439,6 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant_
           __threadfence();
           if (gm < a.M) {
             float* o = a.out + gm * a.ldo;
-            const int n = *nslots;
             for (int c0 = 0; c0 < a.d; c0 += 16) {
               float acc[16];
 #pragma unroll

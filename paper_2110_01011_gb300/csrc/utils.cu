@@ -117,7 +117,6 @@ __global__ void __launch_bounds__(256) jacobi_sqrt_eig_kernel(double* __restrict
   double* sn = cs + nb / 2;                   // [nb / 2] sines
   int* top = reinterpret_cast<int*>(sn + nb / 2);
   int* bot = top + nb / 2;
-  __shared__ double off;
   __shared__ int done;
   const int npairs = nb / 2;
   for (int t = threadIdx.x; t < npairs; t += blockDim.x) {
@@ -127,8 +126,6 @@ __global__ void __launch_bounds__(256) jacobi_sqrt_eig_kernel(double* __restrict
   __syncthreads();
   auto at = [&](int i, int j) -> double& { return S[(int64_t)i * b + j]; };
   for (int sweep = 0; sweep < 30; ++sweep) {
-    if (threadIdx.x == 0) off = 0.0;
-    __syncthreads();
     double part = 0.0, diag = 0.0;
     for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
       const double v = S[e];
@@ -220,8 +217,9 @@ __global__ void __launch_bounds__(256) jacobi_sqrt_eig_kernel(double* __restrict
 }
 
 // R = Y - T (rows x b).
-__global__ void sub_kernel(int64_t rows, int b, const float* __restrict__ Y, int64_t ldy, const float* __restrict__ T,
-                           int64_t ldt, float* __restrict__ R, int64_t ldr) {
+// R = Y - T; R may be T (each entry is read and written by the same thread).
+__global__ void sub_kernel(int64_t rows, int b, const float* __restrict__ Y, int64_t ldy, const float* T,
+                           int64_t ldt, float* R, int64_t ldr) {
   const int64_t total = rows * b;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = e / b, j = e % b;
