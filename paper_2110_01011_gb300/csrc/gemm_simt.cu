@@ -571,11 +571,12 @@ __global__ void splitk_reduce_kernel(int64_t M, int64_t N, int splits, const flo
   }
 }
 
-// Tile configuration: the wide 128 x 128 tile (one CTA per SM) for the
-// passes over A of width N >= 96, a 128 x 64 tile (two CTAs per SM) for
-// narrower passes and for the tall products with a short K (X R^{-1}, P~ P^:
-// K = d, too few k-tiles to hide the wide tile's first loads), a small
-// 32 x 32 tile for d x d work.
+// Tile configuration: the wide 128 x 128 (or 128 x 112) tile, two CTAs per
+// SM, for the passes over A of width N >= 96; a 128 x 64 tile (two CTAs per
+// SM) or 128 x 32 tile (four) for narrower passes and for the tall products
+// with a short K (X R^{-1}, P~ P^: K = d, too few k-tiles for the wide
+// tile's deep K loop); a small 32 x 32 tile (eight) for the Grams and d x d
+// work.
 bool use_wide(int64_t M, int64_t N, int64_t K) { return M >= 1024 && N >= 96 && K >= 1024; }
 // Column tile of the wide kernel: 112 where it pads N less than 128 does.
 int wide_bn(int64_t N) { return cdiv(N, 112) * 112 < cdiv(N, 128) * 128 ? 112 : 128; }
