@@ -484,6 +484,25 @@ def batched_leg(a, ctx):
     return out
 
 
+def h2d_copy_gbs(hA, dev):
+    """Pinned host-to-device copy rate of A alone on this machine (GB/s, CUDA
+    events around three plain copies): the floor that the end-to-end call's
+    copy of A cannot beat, reported beside its time."""
+    import torch
+    dst = torch.empty(hA.shape, dtype=hA.dtype, device=dev)
+    dst.copy_(hA, non_blocking=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(3):
+        dst.copy_(hA, non_blocking=True)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / 3
+    del dst
+    return hA.numel() * hA.element_size() / ms / 1e6
+
+
 def e2e_learned(a, ctx, A, Om, params, target, prec, steps, warmup):
     """End to end through the public C ABI with host buffers:
     rqlp_factor_learned_host takes pinned host A and Omega, copies A by row
@@ -512,7 +531,7 @@ def e2e_learned(a, ctx, A, Om, params, target, prec, steps, warmup):
     d2h = 4 * (a.m * d + d * d + a.n * d) + 8 + 32 + 8
     return {"value": ctx.world * (2 * qp[0] + 2) * a.m * a.n * 4 / dt / 1e9, "unit": "GB/s", "ms_per_step": dt * 1e3,
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "qp": list(qp),
-            "api": "rqlp_factor_learned_host"}
+            "api": "rqlp_factor_learned_host", "h2d_copy_gbs": h2d_copy_gbs(hA, ctx.dev)}
 
 
 def e2e_fixed(a, ctx, A, Om, q, p, prec, steps, warmup):
@@ -536,7 +555,8 @@ def e2e_fixed(a, ctx, A, Om, q, p, prec, steps, warmup):
     dt = ctx.max_over_ranks((time.perf_counter() - t0) / steps)
     return {"value": ctx.world * (2 * q + 2) * a.m * a.n * 4 / dt / 1e9, "unit": "GB/s", "ms_per_step": dt * 1e3,
             "h2d_bytes_per_step": 4 * (a.m * a.n + a.m * d),
-            "d2h_bytes_per_step": 4 * (a.m * d + d * d + a.n * d) + 8 + 32, "api": "rqlp_factor_host"}
+            "d2h_bytes_per_step": 4 * (a.m * d + d * d + a.n * d) + 8 + 32, "api": "rqlp_factor_host",
+            "h2d_copy_gbs": h2d_copy_gbs(hA, ctx.dev)}
 
 
 def main():
