@@ -36,6 +36,27 @@ constexpr int kInterGate = 3;
 
 int bucket_of(int d) { return d <= 32 ? 0 : 1; }
 
+// A tall Gram X^T X (X: K x d) runs as K slices of at most kGramSliceRows
+// rows (four at most), each into its own partial d x d slot, summed by
+// gram_reduce_batched_kernel: one CTA per tile over the whole K left the
+// problems with K near 4096 running long after the others.
+constexpr int64_t kGramSliceRows = 1024;
+constexpr int kGramSlicesMax = 4;
+int gram_slices(int64_t K) {
+  return (int)std::min<int64_t>(kGramSlicesMax, std::max<int64_t>(1, cdiv(K, kGramSliceRows)));
+}
+
+// Sum of a problem's Gram slices into G (lower triangle, slice order,
+// Kahan-compensated FP32); nothing when slices <= 1 (the product wrote G)
+// or when the gate is down (the Gram was skipped, and so is its Cholesky).
+struct GramRedJob {
+  float* G;
+  const float* part;   // slices x d x ld
+  int64_t ld;
+  int d, slices;
+  const int* gate;
+};
+
 // Untuned choice per (shape, bucket): what the tuner picked for the mixed
 // 512-problem workload (tile shape 0..5, + kGroupCfgs = one CTA per tile).
 int default_cfg(int shape, int bucket) {
@@ -54,6 +75,8 @@ int default_cfg(int shape, int bucket) {
 // eight tensor maps (see tc_grouped.cu).
 struct Bufs {
   float *Y, *Z, *Pt, *T1, *G, *R[3], *Ri[3], *Ra, *Rb, *Rh, *Ts, *Ts2, *Ph;
+  float* Gp = nullptr;   // Gram slices (gslices x d x ld) when a tall Gram is split
+  int gslices = 1;
   double* scal;
   int* gates;
   int64_t ld;
@@ -75,8 +98,9 @@ struct GemmStage {
   bool transA;
   int shape;
   size_t jobs_off;                           // GroupGemm[count] (bucket order)
-  size_t tiles_off[kBuckets][kGroupCfgs];    // int[cnt_b + 1] per bucket and cfg
+  size_t tiles_off[kBuckets][kGroupCfgs];    // int[njobs_b + 1] per bucket and cfg
   int total[kBuckets][kGroupCfgs];
+  int njobs[kBuckets];                       // jobs per bucket (the problems', or their slices)
   bool gated;
 };
 
@@ -96,7 +120,7 @@ struct TcStage {
 };
 
 struct Stage {
-  enum Kind { kInit, kGemm, kChol, kTranspose, kWriteL, kFinish, kSplit, kTc, kGateClear, kCopyGated } kind;
+  enum Kind { kInit, kGemm, kChol, kTranspose, kWriteL, kFinish, kSplit, kTc, kGateClear, kCopyGated, kGramReduce } kind;
   int gemm = -1;         // index into gemms / tcs
   size_t jobs_off = 0;   // CholJob[], SmallJob[] or SplitJob[]
   size_t start_off = 0;  // kSplit: int[count + 1] block prefix
@@ -172,7 +196,8 @@ struct Builder {
   int n() const { return (int)pr.size(); }
   int d(int i) const { return pr[i].k + pr[i].p; }
 
-  void gemm(bool transA, int shape, const std::vector<GroupGemm>& jobs, bool gated) {
+  // jobs in bucket order; per_bucket: jobs per bucket (default one per problem)
+  void gemm(bool transA, int shape, const std::vector<GroupGemm>& jobs, bool gated, const int* per_bucket = nullptr) {
     GemmStage g{};
     g.transA = transA;
     g.shape = shape;
@@ -180,7 +205,8 @@ struct Builder {
     g.jobs_off = sg.put(jobs.data(), jobs.size());
     int lo = 0;
     for (int bk = 0; bk < kBuckets; ++bk) {
-      const int c = b->cnt[bk];
+      const int c = per_bucket != nullptr ? per_bucket[bk] : b->cnt[bk];
+      g.njobs[bk] = c;
       for (int cfg = 0; cfg < kGroupCfgs; ++cfg) {
         int bm, bn;
         grouped_tile(cfg, &bm, &bn);
@@ -329,20 +355,50 @@ struct Builder {
     return j;
   }
 
-  // G = X^T X over `rows(i)` rows.
+  // G = X^T X over `rows(i)` rows; a tall Gram (shape kGram) in K slices of
+  // at most kGramSliceRows rows, summed by a reduction stage.
   template <typename XF, typename RF>
   void gram(XF X, RF rows, int shape, int gate_slot) {
     std::vector<GroupGemm> js;
+    std::vector<GramRedJob> rj;
+    int per_bucket[kBuckets] = {0, 0};
+    bool split = false;
     for (int i = 0; i < n(); ++i) {
-      GroupGemm j = job(X(i), bf[i].ld, X(i), bf[i].ld, bf[i].G, bf[i].ld, d(i), d(i), rows(i));
-      j.lower_only = 1;   // the Cholesky reads G(i, j) for j <= i
-      if (gate_slot >= 0) {
-        j.gate = &bf[i].gates[gate_slot];
-        j.gate_mode = kGateSkip;
+      const int bk = i < b->cnt[0] ? 0 : 1;   // problems are in bucket order
+      const int64_t K = rows(i);
+      const int s = shape == kGram ? std::min(bf[i].gslices, gram_slices(K)) : 1;
+      const int64_t kc = s > 1 ? round_up(cdiv(K, s), 16) : K;
+      int used = 0;
+      for (int64_t k0 = 0; k0 < K; k0 += kc, ++used) {
+        const int64_t kl = std::min(kc, K - k0);
+        float* C = s > 1 ? bf[i].Gp + (int64_t)used * d(i) * bf[i].ld : bf[i].G;
+        const float* Xk = X(i) + k0 * bf[i].ld;
+        GroupGemm j = job(Xk, bf[i].ld, Xk, bf[i].ld, C, bf[i].ld, d(i), d(i), kl);
+        j.lower_only = 1;   // the Cholesky reads G(i, j) for j <= i
+        if (gate_slot >= 0) {
+          j.gate = &bf[i].gates[gate_slot];
+          j.gate_mode = kGateSkip;
+        }
+        js.push_back(j);
+        ++per_bucket[bk];
       }
-      js.push_back(j);
+      GramRedJob r{};
+      r.G = bf[i].G;
+      r.part = bf[i].Gp;
+      r.ld = bf[i].ld;
+      r.d = d(i);
+      r.slices = s > 1 ? used : 1;
+      r.gate = gate_slot >= 0 ? &bf[i].gates[gate_slot] : nullptr;
+      rj.push_back(r);
+      split = split || s > 1;
     }
-    gemm(true, shape, js, gate_slot >= 0);
+    gemm(true, shape, js, gate_slot >= 0, per_bucket);
+    if (split) {
+      Stage st;
+      st.kind = Stage::kGramReduce;
+      st.jobs_off = sg.put(rj.data(), rj.size());
+      b->stages.push_back(st);
+    }
   }
   void cholesky(int slot, int gate_out, int gate_in) {
     std::vector<CholJob> js;
@@ -542,6 +598,8 @@ Bufs take_bufs(Arena& ar, const rqlp_problem& p, bool tc, bool exact) {
   f.Pt = ar.take<float>(p.n * f.ld);
   f.T1 = ar.take<float>(tall * f.ld);
   f.G = ar.take<float>(dd);
+  f.gslices = gram_slices(tall);
+  if (f.gslices > 1) f.Gp = ar.take<float>((size_t)f.gslices * dd);
   for (int s = 0; s < 3; ++s) {
     f.R[s] = ar.take<float>(dd);
     f.Ri[s] = ar.take<float>(dd);
@@ -669,12 +727,32 @@ const T* at(const rqlp_batch_s* b, size_t off) {
   return reinterpret_cast<const T*>(b->dev + off);
 }
 
+// One CTA per problem (see GramRedJob).
+__global__ void __launch_bounds__(256) gram_reduce_batched_kernel(const GramRedJob* __restrict__ jobs, int count) {
+  if ((int)blockIdx.x >= count) return;
+  const GramRedJob j = jobs[blockIdx.x];
+  if (j.slices <= 1 || (j.gate != nullptr && *j.gate == 0)) return;
+  const int64_t slot = (int64_t)j.d * j.ld;
+  for (int e = threadIdx.x; e < j.d * j.d; e += blockDim.x) {
+    const int r = e / j.d, c = e % j.d;
+    if (c > r) continue;
+    const float* p = j.part + (int64_t)r * j.ld + c;
+    float s = 0.f, comp = 0.f;
+    for (int z = 0; z < j.slices; ++z) {
+      const float y = p[z * slot] - comp, t = s + y;
+      comp = (t - s) - y;
+      s = t;
+    }
+    j.G[(int64_t)r * j.ld + c] = s;
+  }
+}
+
 cudaError_t run_gemm(const rqlp_batch_s* b, const GemmStage& g, cudaStream_t st, int only_bucket = -1,
                      int force_cfg = -1) {
   const GroupGemm* jobs = at<GroupGemm>(b, g.jobs_off);
   int lo = 0;
   for (int bk = 0; bk < kBuckets; ++bk) {
-    const int c = b->cnt[bk];
+    const int c = g.njobs[bk];
     if (c > 0 && (only_bucket < 0 || only_bucket == bk)) {
       const int choice = force_cfg >= 0 ? force_cfg : b->cfg[g.shape][bk];
       const int cfg = choice % kGroupCfgs;   // tile shape; the choice also fixes the grid mode
@@ -701,6 +779,11 @@ cudaError_t run_stages(const rqlp_batch_s* b, cudaStream_t st) {
         break;
       case Stage::kGateClear: CK(gate_clear_batched(at<SmallJob>(b, s.jobs_off), b->count, st)); break;
       case Stage::kCopyGated: CK(copy_gated_batched(at<SmallJob>(b, s.jobs_off), b->count, st)); break;
+      case Stage::kGramReduce:
+        gram_reduce_batched_kernel<<<b->count, 256, 0, st>>>(at<GramRedJob>(b, s.jobs_off), b->count);
+        note_launch();
+        CK(cudaGetLastError());
+        break;
       case Stage::kTc: {
         const TcStage& t = b->tcs[s.gemm];
         CK(cudaMemsetAsync(b->flags, 0, sizeof(int) * b->count, st));
